@@ -1,0 +1,262 @@
+/*
+ * smc.h - C ABI of libsmc.so, a GB300 (sm_103a) implementation of the adaptive
+ * sequential posterior simulator of Durham & Geweke, "Adaptive Sequential
+ * Posterior Simulators for Massively Parallel Computing Environments" (2013).
+ *
+ * The simulator (Algorithm 2 with the specifics of Section 3.3) moves J groups
+ * of N particles from the prior to the posterior in cycles of three phases:
+ *   C (correction):  reweight by the next slice of likelihood; the slice ends
+ *                    when the relative sample size RSS = ESS / (J N) drops
+ *                    below D1 (Section 3.3, "C phase termination").  Two forms:
+ *                    SMC_DATA adds observations one at a time (Algorithm 1,
+ *                    (C_phase_compute)); SMC_POWER raises the full-sample
+ *                    likelihood to the next power phi, found by a k-ary
+ *                    bisection so that RSS reaches D1.
+ *   S (selection):   residual (default) or multinomial resampling within each
+ *                    group (Section 3.3, "Resampling method").
+ *   M (mutation):    Gaussian random-walk Metropolis with Sigma = h^2 V,
+ *                    V the pooled particle covariance, h adapted toward an
+ *                    acceptance target (Section 3.3, "Metropolis steps"); the
+ *                    number of iterations follows the deterministic or the
+ *                    RNE-based rule ("M phase Termination").
+ * The log marginal likelihood and its numerical standard error come from the
+ * per-group products of mean weights (Section 4.2, (ML_se)); posterior moments
+ * with NSE and RNE from the between-group variance (Section 2.3, (NSE_def)).
+ *
+ * Conventions for every function below:
+ *   - Return value: SMC_OK or an error code; nothing is thrown across the ABI.
+ *     The context-taking calls keep a message for smc_last_error().
+ *   - "device" pointers are CUDA device addresses on the current device; "host"
+ *     pointers are ordinary memory.  Inputs are copied in; the caller keeps
+ *     ownership of everything it passes.  A context owns all device memory it
+ *     allocates and releases it in smc_free().
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is enqueued on it; functions that return host values
+ *     synchronise that stream before returning.
+ *   - Particle arrays on the device are structure-of-arrays: theta is [d][P]
+ *     (parameter-major, P = J N), state is [K+1][P].  Host particle arrays
+ *     are particle-major [P][d].
+ *   - There is no CPU fallback: without a usable GPU every call that computes
+ *     returns SMC_ECUDA.
+ */
+#ifndef SMC_H
+#define SMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SMC_MAX_D 32      /* free parameters per particle */
+#define SMC_MAX_FORCE 64  /* dates of interest */
+#define SMC_MAX_N 8192    /* particles per group */
+
+typedef enum {
+    SMC_OK = 0,
+    SMC_EINVAL = 1,       /* invalid argument (message in smc_last_error) */
+    SMC_ENOMEM = 2,       /* device or host allocation failed */
+    SMC_ECUDA = 3,        /* CUDA runtime error, or no usable GPU */
+    SMC_EDEGENERATE = 4,  /* a group has zero total weight */
+    SMC_ENONFINITE = 5,   /* non-finite input data */
+    SMC_ETIMEOUT = 6,     /* a bounded device wait ran out */
+    SMC_EDONE = 7         /* the run has already reached the full posterior */
+} smc_status;
+
+enum { SMC_EGARCH = 0, SMC_LINREG = 1 };
+enum { SMC_FP64 = 0, SMC_FP32 = 1 };
+enum { SMC_DATA = 0, SMC_POWER = 1 };
+enum { SMC_RW = 0, SMC_MALA = 1 };
+enum { SMC_RESIDUAL = 0, SMC_MULTINOMIAL = 1 };
+enum { SMC_STOP_DET = 0, SMC_STOP_RNE = 1 };
+
+/* Model description (plain data).
+ * EGARCH(K, I) of Section 5.1, (EGARCH_mod1)-(EGARCH_mod2) with the normal
+ * mixture (normal_mixture); parameters are the transformed theta of Table 1,
+ * laid out as theta_1, theta_2, theta_3k (k = 1..K), theta_4k, [theta_5k if
+ * gamma], [theta_6i, theta_7i, theta_8i (i = 1..I) if I >= 2].  With I = 1 the
+ * normalisation (EGARCH_normalization) fixes the mixture, so it carries no
+ * parameters.  eps0_zero selects v_k1 = -beta_k (2/pi)^1/2 instead of the
+ * default v_k1 = 0 (no shock before the first observation).
+ * LINREG: y_t = x_t' beta + e_t, e_t ~ N(0, sigma^2) with sigma known
+ * (a conjugate check model; theta = beta, p <= 7).
+ * Priors are independent Gaussians on the free parameters, truncated below at
+ * prior_lo (-inf for none); the log prior is the density kernel of
+ * Condition 1 (truncation constants omitted).
+ * n_free = 0 means all d_full parameters are free; otherwise only
+ * free_idx[0..n_free) move and the rest stay at theta_fixed. */
+typedef struct {
+    int model;
+    int K, I, gamma, eps0_zero;
+    int p;
+    double sigma;
+    int d_full;                       /* filled by smc_model_egarch/linreg */
+    int n_free;
+    int free_idx[SMC_MAX_D];
+    double theta_fixed[SMC_MAX_D];
+    double prior_mean[SMC_MAX_D];     /* over the free parameters, in order */
+    double prior_sd[SMC_MAX_D];
+    double prior_lo[SMC_MAX_D];
+} smc_model;
+
+/* Fills an EGARCH(K, I) description with the priors of Table 1
+ * (K in 1..4, I in 1..4; gamma = 0 drops theta_5k). */
+smc_status smc_model_egarch(smc_model* m, int K, int I, int gamma);
+/* Fills a LINREG description; prior_mean/prior_sd are host arrays of p. */
+smc_status smc_model_linreg(smc_model* m, int p, double sigma, const double* prior_mean,
+                            const double* prior_sd);
+/* Number of parameters each particle carries. */
+int smc_model_dim(const smc_model* m);
+
+/* Simulator settings.  smc_config_default gives the defaults of Section 3.3:
+ * D1 = 0.5, D2 = 0.2, Rbar = 7, kappa = 3, E1 = 0.35, E2 = 0.90, Rmax = 100,
+ * h0 = 0.5 in steps of 0.1 within [0.1, 1.0], acceptance target 0.25,
+ * residual resampling, random-walk mutation, deterministic stopping rule,
+ * power tempering, FP32 recursion. */
+typedef struct {
+    int J, N;                 /* groups x particles per group (N <= SMC_MAX_N) */
+    int precision;            /* SMC_FP32: recursion in FP32 with FP64 log-likelihood,
+                                 log weights and estimators; SMC_FP64: all FP64 */
+    int tempering;            /* SMC_POWER | SMC_DATA */
+    int mutation;             /* SMC_RW (MALA is not in this build) */
+    int resampler;            /* SMC_RESIDUAL | SMC_MULTINOMIAL */
+    double d1, d2;
+    int stop_rule;            /* SMC_STOP_DET | SMC_STOP_RNE */
+    int rbar, kappa, rmax;
+    double e1, e2;
+    int h0_tenths, hmin_tenths, hmax_tenths;
+    double acc_target;
+    int h_reset_each_cycle;
+    int n_force;              /* data tempering: dates of interest (1-based) */
+    int force_dates[SMC_MAX_FORCE];
+    int search_passes;        /* power tempering: k-ary passes (32 candidates each) */
+    uint64_t seed;
+} smc_config;
+
+void smc_config_default(smc_config* c);
+
+/* Per-cycle report of smc_cycle. */
+typedef struct {
+    int cycle;                /* l, 1-based */
+    int t;                    /* data tempering: t_l; power tempering: T */
+    double phi;               /* power reached after the C phase (1 in data tempering) */
+    double rss;               /* RSS at the end of the C phase */
+    int R;                    /* Metropolis iterations run in the M phase */
+    int h_tenths;             /* step size after the M phase */
+    double acc_rate;          /* mean acceptance rate over the M phase */
+    double evals;             /* particle x observation likelihood evaluations in the M phase */
+    int done;                 /* 1 once the full posterior is reached */
+} smc_cycle_info;
+
+typedef struct smc_ctx smc_ctx;
+
+/* Creates a context and runs step 1 of Algorithm 1: the given prior draws
+ * theta0 (P x d, particle-major, host; or [d][P] device when theta0_on_device)
+ * get their log prior and, in power tempering, their full-sample log
+ * likelihood.  y: host array of T observations (EGARCH); X: host T x p
+ * regressors (LINREG, with y).  Non-finite y or X gives SMC_ENONFINITE. */
+smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, const double* X,
+                    int T, const double* theta0, int theta0_on_device, void* stream,
+                    smc_ctx** out);
+
+/* One C + S + M cycle (Algorithm 2).  Returns SMC_EDONE if the previous cycle
+ * already reached t = T (data) or phi = 1 (power). */
+smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info);
+
+/* Cycles until the full posterior is reached (at most max_cycles, 0 = no cap).
+ * info (nullable) receives the last cycle's report; ncycles (nullable) the
+ * number of cycles run by this call. */
+smc_status smc_run(smc_ctx* ctx, int max_cycles, smc_cycle_info* info, int* ncycles);
+
+/* log wbar^(J,N) with its working NSE from (ML_se), and log wtilde^(J,N)
+ * (Section 4.2).  Host outputs; any may be NULL. */
+smc_status smc_log_ml(smc_ctx* ctx, double* log_ml, double* nse, double* log_ml_tilde);
+
+/* Posterior moments at the current particles: for each free parameter and,
+ * for EGARCH, the test functions g1 (log volatility), g2 (E eps^3) and g3
+ * (P(Y_t+1 < -0.03)) of Section 5.2: mean, s.d., NSE (NSE_def) and RNE.
+ * out: host array of nf x 4 with nf = d (+3 for EGARCH); *nf receives nf. */
+smc_status smc_moments(smc_ctx* ctx, double* out, int* nf);
+
+/* Copies the particles to host arrays (particle-major theta [P][d]; loglik,
+ * logprior [P]; state [P][K+1]).  Any pointer may be NULL. */
+smc_status smc_get_particles(smc_ctx* ctx, double* theta, double* loglik, double* logprior,
+                             double* state);
+
+/* Number of kernel launches this library has issued in this process. */
+uint64_t smc_launch_count(void);
+
+/* Total device time (ms, CUDA events on the context's stream) and launch count
+ * of the M-phase mutation kernel since the context was created or the timer
+ * last reset.  Timing is enabled by smc_profile(ctx, 1). */
+smc_status smc_profile(smc_ctx* ctx, int enable);
+smc_status smc_mutate_time(smc_ctx* ctx, double* ms, uint64_t* launches, int reset);
+
+void smc_free(smc_ctx* ctx);
+const char* smc_last_error(const smc_ctx* ctx);
+const char* smc_status_str(smc_status s);
+
+/* ---------------------------------------------------------------------------
+ * Stateless entry points on caller-owned device memory (for tests, autograd
+ * and custom drivers).  All enqueue on `stream`; temporaries they need are
+ * allocated stream-ordered (cudaMallocAsync) and released before return.
+ * ------------------------------------------------------------------------- */
+
+/* Log likelihood log p(y_1:T | theta) of Section 5.1 (four evaluation steps)
+ * for P particles.  obs: device observations, float[T] for EGARCH with
+ * SMC_FP32, double[T] for EGARCH with SMC_FP64, or double[T][W] records
+ * [x_1..x_p, y, 0...] with W = smc_linreg_width(p) for LINREG; 16-byte
+ * aligned.  theta: device [d][P].  Outputs (device, nullable except ll):
+ * ll[P], lp[P] (log prior), state[K+1][P] (v_kT, eps_T). */
+smc_status smc_loglik(const smc_model* m, int precision, const void* obs, int T,
+                      const double* theta, int P, double* ll, double* lp, double* state,
+                      void* stream);
+int smc_linreg_width(int p);
+
+/* One random-walk Metropolis iteration (Section 3.3) on device particles in
+ * place: proposal theta + L z with z from Philox4x64-10 at counter
+ * (particle, iter, cycle, 1 << 32 | block), acceptance against
+ * lp + phi * ll with log u from counter (particle, iter, cycle, 2 << 32).
+ * L: device [d][d] lower triangular, row-major.  accepted (host, nullable)
+ * receives the number of accepted proposals (synchronises). */
+smc_status smc_mutate_rw(const smc_model* m, int precision, const void* obs, int T,
+                         double* theta, double* ll, double* lp, double* state, int P,
+                         const double* L, double phi, uint64_t seed, uint64_t cycle,
+                         uint64_t iter, uint64_t* accepted, void* stream);
+
+/* Pooled mean and covariance V of theta (device [d][P]) and the lower
+ * Cholesky factor of (h_tenths / 10)^2 V (Section 3.3, Sigma = h^2 V); a
+ * non-positive pivot zeroes its column.  Outputs (device, nullable): mean[d],
+ * cov[d][d], L[d][d]. */
+smc_status smc_cov_chol(const double* theta, int d, int P, int h_tenths, double* mean,
+                        double* cov, double* L, void* stream);
+
+/* Power tempering C phase: the increment dphi in (0, 1 - phi] at which the
+ * pooled RSS of weights exp(dphi * ll) first falls below d1, by `passes`
+ * k-ary passes of 32 candidates; 1 - phi if RSS(1 - phi) >= d1.  ll: device
+ * [P].  Host outputs: dphi, rss (FP64 RSS at dphi).  Synchronises. */
+smc_status smc_power_search(const double* ll, int P, double phi, double d1, int passes,
+                            double* dphi, double* rss, void* stream);
+
+/* S phase within each of J groups of N (Section 3.3): residual
+ * (SMC_RESIDUAL) or multinomial resampling from weights w (device [J*N],
+ * non-negative, any scale per group).  Integer fixed point: q_n =
+ * floor(2^40 w_n / max w), counts floor(N q_n / Q), residual draws by
+ * upper_bound on the integer residual prefix with mulhi64(x, R), x from
+ * Philox4x64-10 at counter (group, draw, cycle, 3 << 32).  idx: device
+ * [J*N] int32, group-local source index of each output slot, in particle
+ * order.  Returns SMC_EDEGENERATE if a group's weights are all zero. */
+smc_status smc_resample(const double* w, int J, int N, int resampler, uint64_t seed,
+                        uint64_t cycle, int32_t* idx, void* stream);
+
+/* Grand mean, s.d., NSE and RNE (Section 2.3) of each of nf functions
+ * g (device [nf][J*N], group-major columns).  out: host [nf][4]. */
+smc_status smc_group_moments(const double* g, int nf, int J, int N, double* out, void* stream);
+
+/* log wbar, its NSE (ML_se) from per-group log products a (device [J]). */
+smc_status smc_ml_from_groups(const double* a, int J, double* log_ml, double* nse, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMC_H */

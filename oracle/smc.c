@@ -17,11 +17,14 @@
  *   - power tempering (an addition to the paper's data tempering): target
  *     p(theta) p(y|theta)^phi; the increment dphi is found by bisection so that
  *     RSS just falls below D1; if RSS(1-phi) >= D1 the increment is 1-phi.
- *   - residual resampling in integer fixed point: q_n = floor(2^40 w_n/max w),
+ *   - residual resampling in integer fixed point: q_n = floor(2^32 w_n/max w),
  *     count_n = floor(N q_n / Q), residuals r_n = N q_n - Q count_n, and the
  *     N - sum count residual draws pick upper_bound(prefix r, mulhi64(x, R)) with
- *     x from Philox.  Multinomial is the same with all counts zero.  The
- *     quantisation changes selection probabilities by at most 2^-40 relative.
+ *     x from Philox.  Multinomial is the same with all counts zero.  With 32
+ *     fractional bits the residual total R = Q (N - sum count) stays below 2^64
+ *     for N up to 2^15 (Q <= N 2^32); a particle whose weight is below 2^-32 of
+ *     the group maximum is never selected, which moves at most N 2^-32 of the
+ *     selection probability.
  *   - RNE stopping rule: arithmetic mean of the RNE of the test functions after
  *     each iteration; E1 normally, E2 at dates of interest and at the end of the
  *     sample; at most Rmax iterations.
@@ -155,7 +158,7 @@ int or_resample(const double *w, int J, int N, int resid, uint64_t seed,
         uint64_t Q = 0;
         for (int n = 0; n < N; ++n) {
             double wn = wj[n] > 0.0 ? wj[n] / wmax : 0.0;
-            q[n] = (uint64_t)floor(ldexp(wn, 40));
+            q[n] = (uint64_t)floor(ldexp(wn, 32));
             Q += q[n];
         }
         uint64_t placed = 0, R = 0;

@@ -1,0 +1,51 @@
+// Instantiation helpers: one translation unit per (precision, K) keeps each
+// compile short and lets the build run them in parallel.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace smc {
+
+inline int mutate_grid(int P) { return (P + kMutThreads - 1) / kMutThreads; }
+
+template <template <int, int> class Pol, int K>
+cudaError_t launch_mutate_k(const MutateArgs& a, cudaStream_t s)
+{
+    const int g = mutate_grid(a.P);
+    switch (a.m.I) {
+    case 1: k_mutate<Pol<K, 1>><<<g, kMutThreads, 0, s>>>(a); break;
+    case 2: k_mutate<Pol<K, 2>><<<g, kMutThreads, 0, s>>>(a); break;
+    case 3: k_mutate<Pol<K, 3>><<<g, kMutThreads, 0, s>>>(a); break;
+    case 4: k_mutate<Pol<K, 4>><<<g, kMutThreads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <template <int, int> class Pol, int K>
+cudaError_t launch_loglik_k(const LoglikArgs& a, cudaStream_t s)
+{
+    const int g = mutate_grid(a.P);
+    switch (a.m.I) {
+    case 1: k_loglik<Pol<K, 1>><<<g, kMutThreads, 0, s>>>(a); break;
+    case 2: k_loglik<Pol<K, 2>><<<g, kMutThreads, 0, s>>>(a); break;
+    case 3: k_loglik<Pol<K, 3>><<<g, kMutThreads, 0, s>>>(a); break;
+    case 4: k_loglik<Pol<K, 4>><<<g, kMutThreads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace smc
+
+#define SMC_INSTANTIATE_EGARCH(TAG, POL, K)                                                     \
+    namespace smc {                                                                             \
+    cudaError_t launch_mutate_##TAG##_k##K(const MutateArgs& a, cudaStream_t s)                 \
+    {                                                                                           \
+        return launch_mutate_k<POL, K>(a, s);                                                   \
+    }                                                                                           \
+    cudaError_t launch_loglik_##TAG##_k##K(const LoglikArgs& a, cudaStream_t s)                 \
+    {                                                                                           \
+        return launch_loglik_k<POL, K>(a, s);                                                   \
+    }                                                                                           \
+    }

@@ -1,0 +1,519 @@
+// Per-particle likelihood recursions and the observation pipeline.
+//
+// EGARCH(K, I) of Section 5.1: parameters from Table 1 through the transforms
+// (EGARCH_tran1)-(EGARCH_tran2); for t = 1..T
+//   v_kt  = alpha_k v_k,t-1 + beta_k (|eps_t-1| - (2/pi)^1/2) + gamma_k eps_t-1
+//   h_t   = sigma_Y exp(sum_k v_kt / 2),   eps_t = (y_t - mu_Y) / h_t
+//   l_t   = -1/2 log 2pi - log h_t + log sum_i p_i / sigma_i exp(-(eps_t - mu_i)^2 / 2 sigma_i^2)
+// with v_k0 = 0 and no shock before the first observation (v_k1 = 0; the
+// eps_0 = 0 reading v_k1 = -beta_k (2/pi)^1/2 is selectable).
+//
+// FP32 path (EgarchF32): the recursion runs in base-2 units so that every
+// exponential is one hardware ex2:
+//   v'_k = v_k log2(e) / 2, eps scaled by s = (log2(e)/2)^1/2,
+//   log2 h_t = log2 sigma_Y + sum_k v'_kt,
+//   mixture exponent x_it = log2(p_i / sigma_i) - (s (eps_t - mu_i) / sigma_i)^2.
+// The mixture log-sum-exp is max-shifted; the shifted sums s_t in [1, I] are
+// multiplied together and one lg2 is taken per 32 observations.  Sums of the
+// per-observation terms stay in FP32 for 32 observations and are then added
+// into an FP64 accumulator (the log likelihood itself is FP64).
+// FP64 path (EgarchF64): the four steps as written, in double precision.
+#pragma once
+
+#include "common.cuh"
+
+namespace smc {
+
+constexpr double kLog2Pi = 1.83787706640934548356;
+constexpr double kSqrt2OverPi = 0.79788456080286535588;
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr double kLog2e = 1.44269504088896340736;
+constexpr double kSfac = 0.84932180028801904272;       // (log2(e) / 2)^1/2
+constexpr double kLog2Sfac = -0.23556494171288733624;  // log2 of kSfac
+constexpr double kLogSfac = -0.16328232405373808766;   // ln of kSfac
+
+// Device view of a model (see smc.h for the host-side description).
+struct ModelDev {
+    int kind;        // 0 EGARCH, 1 LINREG
+    int K, I, gamma, eps0_zero;
+    int p;           // LINREG regressors
+    double sigma;    // LINREG disturbance s.d.
+    int d_full, d;
+    const int* free_idx;        // [d] or null (all parameters free)
+    const double* theta_fixed;  // [d_full] or null
+    const double* prior_mean;   // [d]
+    const double* prior_sd;     // [d]
+    const double* prior_lo;     // [d]
+};
+
+// Full parameter vector from a particle's free parameters.
+template <typename Real>
+__device__ __forceinline__ void full_theta(const ModelDev& m, const double* th, Real* full)
+{
+    if (!m.free_idx) {
+        for (int i = 0; i < m.d_full; ++i) full[i] = (Real)th[i];
+        return;
+    }
+    for (int i = 0; i < m.d_full; ++i) full[i] = m.theta_fixed ? (Real)m.theta_fixed[i] : Real(0);
+    for (int k = 0; k < m.d; ++k) full[m.free_idx[k]] = (Real)th[k];
+}
+
+// Log prior density kernel (Gaussian per free parameter, truncated below).
+__device__ __forceinline__ double log_prior(const ModelDev& m, const double* th)
+{
+    double lp = 0.0;
+    for (int k = 0; k < m.d; ++k) {
+        const double x = th[k];
+        if (!(x >= m.prior_lo[k]) || !isfinite(x)) return -INFINITY;
+        const double z = (x - m.prior_mean[k]) / m.prior_sd[k];
+        lp += -0.5 * kLog2Pi - log(m.prior_sd[k]) - 0.5 * z * z;
+    }
+    return lp;
+}
+
+// Table 1 transforms and (EGARCH_tran1)-(EGARCH_tran2).
+template <typename Real, int K, int I>
+struct EgarchParams {
+    Real mu_y, log_sigma_y;
+    Real alpha[K], beta[K], gamma[K];
+    Real p[I], mu[I], sig[I];
+};
+
+template <typename Real, int K, int I>
+__device__ __forceinline__ void egarch_transform(const Real* th, int has_gamma,
+                                                 EgarchParams<Real, K, I>& q)
+{
+    int j = 0;
+    q.mu_y = th[j++] / Real(1000);
+    q.log_sigma_y = th[j++];
+#pragma unroll
+    for (int k = 0; k < K; ++k) q.alpha[k] = tanh(th[j + k]);
+    j += K;
+#pragma unroll
+    for (int k = 0; k < K; ++k) q.beta[k] = exp(th[j + k]);
+    j += K;
+#pragma unroll
+    for (int k = 0; k < K; ++k) q.gamma[k] = has_gamma ? th[j + k] : Real(0);
+    if (has_gamma) j += K;
+    if constexpr (I == 1) {
+        q.p[0] = Real(1);
+        q.mu[0] = Real(0);
+        q.sig[0] = Real(1);
+    } else {
+        Real pstar[I], mustar[I], sigstar[I];
+#pragma unroll
+        for (int i = 0; i < I; ++i) pstar[i] = tanh(th[j + i]) + Real(1);
+#pragma unroll
+        for (int i = 0; i < I; ++i) mustar[i] = th[j + I + i];
+#pragma unroll
+        for (int i = 0; i < I; ++i) sigstar[i] = exp(th[j + 2 * I + i]);
+        Real psum = 0;
+#pragma unroll
+        for (int i = 0; i < I; ++i) psum += pstar[i];
+        Real pmu = 0;
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+            q.p[i] = pstar[i] / psum;
+            pmu += q.p[i] * mustar[i];
+        }
+        Real s = 0;
+        Real mu2[I];
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+            mu2[i] = mustar[i] - pmu;
+            s += q.p[i] * (mu2[i] * mu2[i] + sigstar[i] * sigstar[i]);
+        }
+        const Real c = Real(1) / sqrt(s);
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+            q.mu[i] = c * mu2[i];
+            q.sig[i] = c * sigstar[i];
+        }
+    }
+}
+
+// ------------------------------------------------------------- FP32 recursion
+template <int K, int I>
+struct EgarchF32 {
+    float mu, lsy2p;                       // mu_Y; log2 sigma_Y - log2 s
+    float al[K], be[K], ga[K], nb[K];      // alpha; beta, gamma in scaled units; -beta c log2(e)/2
+    float a[I], b[I], c[I];                // 1/sigma_i; -mu_i s / sigma_i; log2(p_i / sigma_i)
+    float v0[K];                           // v'_k1
+    float v[K], es;                        // recursion state (scaled units)
+    float sh, sm, prod;                    // partial sums over the current 32 observations
+    double acc;                            // FP64 sum of completed partials (log2 units)
+
+    __device__ __forceinline__ void setup(const float* th, int has_gamma, int eps0_zero)
+    {
+        EgarchParams<float, K, I> q;
+        egarch_transform<float, K, I>(th, has_gamma, q);
+        mu = q.mu_y;
+        lsy2p = q.log_sigma_y * (float)kLog2e - (float)kLog2Sfac;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            al[k] = q.alpha[k];
+            be[k] = q.beta[k] * (float)(kLog2e / 2.0 / kSfac);
+            ga[k] = q.gamma[k] * (float)(kLog2e / 2.0 / kSfac);
+            nb[k] = -q.beta[k] * (float)(kSqrt2OverPi * kLog2e / 2.0);
+            v0[k] = eps0_zero ? nb[k] : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+            a[i] = 1.0f / q.sig[i];
+            b[i] = -q.mu[i] * (float)kSfac / q.sig[i];
+            c[i] = log2f(q.p[i] / q.sig[i]);
+        }
+        es = 0.0f;
+        sh = sm = 0.0f;
+        prod = 1.0f;
+        acc = 0.0;
+    }
+
+    template <bool kFirst>
+    __device__ __forceinline__ void step(float y)
+    {
+        if constexpr (kFirst) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = v0[k];
+        } else {
+            const float ae = fabsf(es);
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = fmaf(al[k], v[k], fmaf(be[k], ae, fmaf(ga[k], es, nb[k])));
+        }
+        float e = lsy2p + v[0];
+#pragma unroll
+        for (int k = 1; k < K; ++k) e += v[k];
+        sh += e;
+        es = (y - mu) * ex2_approx(-e);
+        if constexpr (I == 1) {
+            sm = fmaf(-es, es, sm);
+        } else if constexpr (I == 2) {
+            const float z0 = fmaf(a[0], es, b[0]), z1 = fmaf(a[1], es, b[1]);
+            const float x0 = fmaf(-z0, z0, c[0]), x1 = fmaf(-z1, z1, c[1]);
+            sm += fmaxf(x0, x1);
+            prod = fmaf(prod, ex2_approx(-fabsf(x0 - x1)), prod);
+        } else {
+            float x[I];
+#pragma unroll
+            for (int i = 0; i < I; ++i) {
+                const float z = fmaf(a[i], es, b[i]);
+                x[i] = fmaf(-z, z, c[i]);
+            }
+            float m = x[0];
+#pragma unroll
+            for (int i = 1; i < I; ++i) m = fmaxf(m, x[i]);
+            float s = ex2_approx(x[0] - m);
+#pragma unroll
+            for (int i = 1; i < I; ++i) s += ex2_approx(x[i] - m);
+            sm += m;
+            prod *= s;
+        }
+    }
+
+    __device__ __forceinline__ void flush()
+    {
+        float u = sm - sh;
+        if constexpr (I >= 2) u += lg2_approx(prod);
+        acc += (double)u;
+        sh = sm = 0.0f;
+        prod = 1.0f;
+    }
+
+    // log p(y_1:T | theta); call after the last flush.
+    __device__ __forceinline__ double finish(int T) const
+    {
+        return kLn2 * acc + (double)T * (-0.5 * kLog2Pi - kLogSfac);
+    }
+
+    __device__ __forceinline__ void state_out(double* st) const
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k) st[k] = (double)v[k] * (2.0 * kLn2);
+        st[K] = (double)es / kSfac;
+    }
+};
+
+// ------------------------------------------------------------- FP64 recursion
+template <int K, int I>
+struct EgarchF64 {
+    double mu, lsy;
+    double al[K], be[K], ga[K], v0[K];
+    double ainv[I], mui[I], lps[I];        // 1/sigma_i, mu_i, log p_i - log sigma_i
+    double v[K], eps, acc;
+
+    __device__ __forceinline__ void setup(const double* th, int has_gamma, int eps0_zero)
+    {
+        EgarchParams<double, K, I> q;
+        egarch_transform<double, K, I>(th, has_gamma, q);
+        mu = q.mu_y;
+        lsy = q.log_sigma_y;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            al[k] = q.alpha[k];
+            be[k] = q.beta[k];
+            ga[k] = q.gamma[k];
+            v0[k] = eps0_zero ? -q.beta[k] * kSqrt2OverPi : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+            ainv[i] = 1.0 / q.sig[i];
+            mui[i] = q.mu[i];
+            lps[i] = log(q.p[i]) - log(q.sig[i]);
+        }
+        eps = 0.0;
+        acc = 0.0;
+    }
+
+    template <bool kFirst>
+    __device__ __forceinline__ void step(double y)
+    {
+        if constexpr (kFirst) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = v0[k];
+        } else {
+            const double ae = fabs(eps) - kSqrt2OverPi;
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = al[k] * v[k] + be[k] * ae + ga[k] * eps;
+        }
+        double vs = 0.0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) vs += v[k];
+        const double lh = lsy + 0.5 * vs;                 // log h_t
+        eps = (y - mu) * exp(-lh);
+        double l;
+        if constexpr (I == 1) {
+            l = -0.5 * eps * eps;
+        } else {
+            double x[I];
+            double m = -INFINITY;
+#pragma unroll
+            for (int i = 0; i < I; ++i) {
+                const double z = (eps - mui[i]) * ainv[i];
+                x[i] = lps[i] - 0.5 * z * z;
+                m = fmax(m, x[i]);
+            }
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < I; ++i) s += exp(x[i] - m);
+            l = m + log(s);
+        }
+        acc += l - lh;
+    }
+
+    __device__ __forceinline__ void flush() {}
+
+    __device__ __forceinline__ double finish(int T) const
+    {
+        return acc + (double)T * (-0.5 * kLog2Pi);
+    }
+
+    __device__ __forceinline__ void state_out(double* st) const
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k) st[k] = v[k];
+        st[K] = eps;
+    }
+};
+
+// ------------------------------------------------------ observation pipeline
+// Double-buffered staging of observation elements into shared memory: chunk c
+// lives in buffer c & 1 and is filled by one bulk async copy (plus at most 15
+// bytes of tail by plain loads so that no global read passes the end of the
+// caller's array).  The buffer is refilled with chunk c + 2 once every thread
+// has finished chunk c.
+template <typename T, int kChunk>
+struct ObsPipe {
+    static_assert((kChunk * sizeof(T)) % 16 == 0, "chunk must be a multiple of 16 bytes");
+    T* buf;               // [2][kChunk] in shared memory, 16-byte aligned
+    uint64_t* bar;        // [2] mbarriers in shared memory
+    const T* src;         // global, 16-byte aligned
+    int64_t n;            // total elements
+    int nchunks;
+
+    __device__ __forceinline__ void issue(int c)
+    {
+        const int b = c & 1;
+        const int64_t off = (int64_t)c * kChunk;
+        const int cnt = (int)min((int64_t)kChunk, n - off);
+        constexpr int kVec = 16 / (int)sizeof(T);
+        const int bulk = cnt & ~(kVec - 1);
+        for (int i = bulk; i < cnt; ++i) buf[b * kChunk + i] = src[off + i];
+        mbar_arrive_expect_tx(&bar[b], (uint32_t)(bulk * sizeof(T)));
+        if (bulk > 0) bulk_copy_g2s(&buf[b * kChunk], src + off, (uint32_t)(bulk * sizeof(T)), &bar[b]);
+    }
+
+    // Block-collective start; returns false when there is nothing to stage.
+    __device__ __forceinline__ void start()
+    {
+        if (threadIdx.x == 0) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && nchunks > 0) {
+            issue(0);
+            if (nchunks > 1) issue(1);
+        }
+    }
+
+    // Block-collective wait for chunk c.  Returns false (for every thread) if
+    // any thread's bounded wait ran out.
+    __device__ __forceinline__ bool wait(int c)
+    {
+        const bool ok = mbar_wait_bounded(&bar[c & 1], (uint32_t)((c >> 1) & 1));
+        return !__syncthreads_or(!ok);
+    }
+
+    // Block-collective release of chunk c's buffer and refill with chunk c + 2.
+    __device__ __forceinline__ void release(int c)
+    {
+        __syncthreads();
+        if (threadIdx.x == 0 && c + 2 < nchunks) {
+            fence_proxy_async_smem();
+            issue(c + 2);
+        }
+    }
+
+    // After an abandoned wait: give chunks still in flight a bounded chance to
+    // land before the block exits.
+    __device__ __forceinline__ void drain(int c)
+    {
+        if (threadIdx.x == 0)
+            for (int k = c; k < nchunks && k < c + 2; ++k) mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1));
+        __syncthreads();
+    }
+};
+
+constexpr int kChunkF32 = 1024;   // observations per staged chunk (4 KB)
+constexpr int kChunkF64 = 512;    // elements per staged chunk (4 KB)
+
+// Runs the FP32 EGARCH recursion of one particle over T observations staged
+// through `pipe`.  Every thread of the block must call it (it contains block
+// barriers); `active` selects whose result matters.  Returns false on a
+// staging timeout.
+template <int K, int I>
+__device__ __forceinline__ bool run_egarch_f32(EgarchF32<K, I>& mdl, ObsPipe<float, kChunkF32>& pipe,
+                                               int T)
+{
+    for (int c = 0; c < pipe.nchunks; ++c) {
+        if (!pipe.wait(c)) {
+            pipe.drain(c);
+            return false;
+        }
+        const float* yb = pipe.buf + (c & 1) * kChunkF32;
+        const int cnt = min(kChunkF32, T - c * kChunkF32);
+        const int nunits = cnt >> 5;
+        for (int u = 0; u < nunits; ++u) {
+            const float4* y4 = reinterpret_cast<const float4*>(yb + 32 * u);
+            if (c == 0 && u == 0) {
+                float4 q = y4[0];
+                mdl.template step<true>(q.x);
+                mdl.template step<false>(q.y);
+                mdl.template step<false>(q.z);
+                mdl.template step<false>(q.w);
+#pragma unroll
+                for (int j = 1; j < 8; ++j) {
+                    q = y4[j];
+                    mdl.template step<false>(q.x);
+                    mdl.template step<false>(q.y);
+                    mdl.template step<false>(q.z);
+                    mdl.template step<false>(q.w);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float4 q = y4[j];
+                    mdl.template step<false>(q.x);
+                    mdl.template step<false>(q.y);
+                    mdl.template step<false>(q.z);
+                    mdl.template step<false>(q.w);
+                }
+            }
+            mdl.flush();
+        }
+        const int rem = cnt & 31;
+        if (rem) {
+            for (int r = 0; r < rem; ++r) {
+                const int tl = 32 * nunits + r;
+                if (c == 0 && tl == 0) mdl.template step<true>(yb[tl]);
+                else mdl.template step<false>(yb[tl]);
+            }
+            mdl.flush();
+        }
+        pipe.release(c);
+    }
+    return true;
+}
+
+template <int K, int I>
+__device__ __forceinline__ bool run_egarch_f64(EgarchF64<K, I>& mdl, ObsPipe<double, kChunkF64>& pipe,
+                                               int T)
+{
+    for (int c = 0; c < pipe.nchunks; ++c) {
+        if (!pipe.wait(c)) {
+            pipe.drain(c);
+            return false;
+        }
+        const double* yb = pipe.buf + (c & 1) * kChunkF64;
+        const int cnt = min(kChunkF64, T - c * kChunkF64);
+        int r = 0;
+        if (c == 0 && cnt > 0) {
+            mdl.template step<true>(yb[0]);
+            r = 1;
+        }
+        for (; r < cnt; ++r) mdl.template step<false>(yb[r]);
+        pipe.release(c);
+    }
+    return true;
+}
+
+// Conjugate normal linear regression: y_t = x_t' beta + e_t, e_t ~ N(0, sigma^2)
+// with sigma known.  Records are [x_t1 .. x_tp, y_t] (p + 1 doubles).
+struct LinregF64 {
+    double beta[8];
+    int p;
+    double inv2s2, c0;
+    double acc;
+
+    __device__ __forceinline__ void setup(const double* th, int p_, double sigma)
+    {
+        p = p_;
+        for (int i = 0; i < p; ++i) beta[i] = th[i];
+        inv2s2 = 0.5 / (sigma * sigma);
+        c0 = -0.5 * kLog2Pi - log(sigma);
+        acc = 0.0;
+    }
+
+    __device__ __forceinline__ void step(const double* rec)
+    {
+        double m = 0.0;
+        for (int i = 0; i < p; ++i) m += rec[i] * beta[i];
+        const double r = rec[p] - m;
+        acc += -r * r * inv2s2;
+    }
+
+    __device__ __forceinline__ double finish(int T) const { return acc + (double)T * c0; }
+};
+
+// Records of width W staged in chunks of whole records.
+__device__ __forceinline__ bool run_linreg(LinregF64& mdl, ObsPipe<double, kChunkF64>& pipe, int T, int W)
+{
+    // chunk boundaries fall on record boundaries when kChunkF64 % W == 0; the
+    // host restricts W to divisors of kChunkF64 (W in {1, 2, 4, 8}) by padding
+    // records with zero columns.
+    const int rec_per_chunk = kChunkF64 / W;
+    for (int c = 0; c < pipe.nchunks; ++c) {
+        if (!pipe.wait(c)) {
+            pipe.drain(c);
+            return false;
+        }
+        const double* rb = pipe.buf + (c & 1) * kChunkF64;
+        const int nrec = min(rec_per_chunk, T - c * rec_per_chunk);
+        for (int r = 0; r < nrec; ++r) mdl.step(rb + r * W);
+        pipe.release(c);
+    }
+    return true;
+}
+
+}  // namespace smc

@@ -284,3 +284,20 @@ def test_nse_coverage_over_seeds():
     # 95% nominal; binomial(120, .95) has sd 2.4, so >= 102 is about 4 sd low
     assert hits_m >= 102, hits_m
     assert hits_ml >= 96, hits_ml
+
+
+def test_resample_large_group_many_residual_draws():
+    """N = 8192 with one dominant weight: almost every count is fractional, so
+    nearly N residual draws are made and the residual total is near Q N."""
+    N = 8192
+    w = np.full(N, 1e-3)
+    w[5] = 1.0
+    idx = O.resample(w, 1, N, resid=True, seed=2, cycle=3)[0]
+    c = np.bincount(idx, minlength=N)
+    assert c.sum() == N
+    wt = w / w.sum()
+    assert c[5] >= np.floor(N * wt[5])
+    # the residual draws spread over the small particles in proportion
+    others = np.delete(c, 5)
+    exp_other = N * wt[0] - np.floor(N * wt[0])
+    assert abs(others.mean() - (N * wt[0])) < 0.1 + 4 * np.sqrt(exp_other / (N - 1))
