@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 sequential posterior simulator.
+
+Metric: M-phase particle x observation likelihood evaluations per second.  One
+step is one whole simulator run (Algorithm 2: prior draws -> C, S, M cycles ->
+log marginal likelihood) on the workload of Section 5's shape: EGARCH with
+K = 2 factors and I = 2 mixture components, T = 5000 synthetic daily returns,
+J = 64 groups x N = 1024 particles, FP32 recursion with FP64 accumulators,
+random-walk Metropolis adapted toward 0.25 acceptance, power tempering.
+`value` = sum over steps of the M-phase evaluations / summed step time, with
+the observations and prior draws resident in HBM; `e2e` repeats the run through
+the public API from host buffers (context creation, host->device copies of
+observations and prior draws, and the read-back of the result inside the timed
+region).  Each step's device time is bracketed by CUDA events on the run's
+stream; L2 is flushed between steps by writing a 256 MB buffer.
+
+`--impl reference` times the FP64 CPU oracle on the host cores instead (bounded
+sample: one Metropolis iteration over a subsample of particles per step).
+Multi-GPU: independent replicas, one per rank (the path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT_GB300 = 152
+SM_MAX_MHZ_FALLBACK = 2070.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="egarch22_T5000")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cycles", type=int, default=0, help="cap on cycles per run (0 = full run; profiling only)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- roofline
+def alu_ops_per_eval(K, I, gamma):
+    """Algorithmic per-observation work of the FP32 recursion (one particle):
+    FP32 lane operations and SFU (MUFU) operations.  See the roofline section of
+    the design notes for the derivation."""
+    fp32 = 1 + (3 if gamma else 2) * K + K + 1 + 2
+    fp32 += {1: 1, 2: 8}.get(I, 7 * I)
+    mufu = 1 + {1: 0, 2: 1}.get(I, I)
+    return fp32, mufu
+
+
+def alu_peak_evals(K, I, gamma, sms, mhz):
+    """Evaluations/s bound: issue (4 x 32 lanes/clk/SM, every instruction) and
+    SFU (16 lanes/clk/SM) limits at the given SM clock."""
+    fp32, mufu = alu_ops_per_eval(K, I, gamma)
+    issue = 128.0 / (fp32 + mufu)
+    sfu = 16.0 / mufu
+    bound = min(issue, sfu)
+    return sms * mhz * 1e6 * bound, ("issue" if issue <= sfu else "mufu")
+
+
+def sm_max_mhz():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return float(json.load(f).get("sm_max_mhz", SM_MAX_MHZ_FALLBACK)), "of measured"
+    except Exception:
+        return SM_MAX_MHZ_FALLBACK, "of fallback"
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (read-only queries)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            os.unlink(self.path)
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for name, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+            except Exception:
+                continue
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), reasons=sorted(reasons),
+                       samples=len(sm))
+        return out
+
+
+# ------------------------------------------------------------ distributed
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# -------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(w, y, budget_s=12.0, sample=256):
+    """The FP64 oracle's M-phase rate (one random-walk Metropolis iteration over
+    `sample` posterior-like particles x all T observations per call), on every
+    host core, repeated for about `budget_s` seconds."""
+    import numpy as np
+    import oracle as O
+    from paper_1304_4334_gb300 import inputs as I
+
+    spec = O.ModelSpec(K=w.K, I=w.I, gamma=w.gamma)
+    th = I.posterior_cloud(I.theta_of_truth(w.truth, I_model=w.I, gamma=w.gamma), sample, 0.02, seed=5)
+    cores = os.cpu_count() or 1
+    ll, st = O.loglik(spec, y, th, with_state=True, nthreads=cores)
+    lp = O.logprior(spec, th)
+    _, V = O.mean_cov(th)
+    Lm, _ = O.cholesky(0.09 * V)
+    evals, t0, it = 0.0, time.perf_counter(), 0
+    while True:
+        th, ll, lp, st, _, _ = O.mutate_rw(spec, y, th, ll, lp, st, Lm, 1.0, 7, 1, it, nthreads=cores)
+        it += 1
+        evals += sample * len(y)
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return {"value": evals / el, "unit": "particle*obs lik evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{it} random-walk Metropolis iterations x {sample} particles x T={len(y)} "
+                      f"({w.name}), FP64 C oracle, {cores} OpenMP threads, {el:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_1304_4334_gb300 import inputs as I
+    import oracle
+    oracle.build()
+    w = I.WORKLOADS[args.workload]
+    y = w.data()
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w, y, budget_s=0.5, sample=64)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_oracle_rate(w, y, budget_s=4.0, sample=256)
+        vals.append(last["value"])
+    total = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    line = {"metric": "M-phase particle*obs lik evals/s", "value": value,
+            "unit": "particle*obs lik evals/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "K": w.K, "I": w.I, "T": w.T,
+                                            "J": w.J, "N": w.N, "sampler": "rw"},
+            "cpu_baseline": {"value": value, "unit": "particle*obs lik evals/s", "cores": last["cores"],
+                             "kind": "oracle", "sample": last["sample"]},
+            "e2e": {"value": value, "unit": "particle*obs lik evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import numpy as np
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1304_4334_gb300 import inputs as I
+    from paper_1304_4334_gb300 import smc as S
+
+    w = I.WORKLOADS[args.workload]
+    y = w.data()
+    m = S.model_egarch(w.K, w.I, w.gamma)
+    mean, sd, lo = S.model_prior(m)
+    th0 = I.draw_prior(mean, sd, lo, w.P, seed=w.prior_seed + 1000 * rank)
+    prec = S.FP32 if w.precision == "f32" else S.FP64
+    cfg = S.config_default(J=w.J, N=w.N, precision=prec, rbar=w.rbar, kappa=w.kappa, seed=1 + rank)
+    stream = torch.cuda.Stream()
+    th0_dev = torch.as_tensor(np.ascontiguousarray(th0.T), device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        ctx = S.init(m, cfg, y, th0, stream=stream.cuda_stream)
+    seed_of = lambda k: 1 + rank + 7919 * k
+
+    def one_run(k):
+        ctx.reset(th0_dev, seed_of(k), theta0_on_device=True)
+        ctx.run(args.cycles)
+        lml = ctx.log_ml()
+        return ctx.totals(), lml
+
+    for k in range(args.warmup):
+        one_run(k)
+    torch.cuda.synchronize()
+
+    ctx.profile(True)
+    ctx.mutate_time(reset=True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = S.launch_count()
+    clocks.start()
+    ev = []
+    evals_total, cycles, msteps = 0.0, [], []
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        (cyc, ms, evl), lml = one_run(args.warmup + k)
+        e1.record(stream)
+        ev.append((e0, e1))
+        evals_total += evl
+        cycles.append(cyc)
+        msteps.append(ms)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    launches = S.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(step_ms) / 1e3
+    mut_ms, mut_n = ctx.mutate_time(reset=True)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ee = torch.tensor([evals_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(ee, op=dist.ReduceOp.SUM)
+        t_total, evals_all = float(tt.item()), float(ee.item())
+    else:
+        evals_all = evals_total
+    value = evals_all / t_total
+
+    # ---- end to end through the public API from host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        e2e_time, e2e_evals, h2d, d2h = 0.0, 0.0, 0, 0
+        for k in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c2 = S.init(m, cfg, y, th0, stream=stream.cuda_stream)
+            c2.run(args.cycles)
+            c2.log_ml()
+            cyc2, ms2, evl2 = c2.totals()
+            hb, db = c2.transfer_bytes()
+            c2.close()
+            e2e_time += time.perf_counter() - t0
+            e2e_evals += evl2
+            h2d, d2h = hb, db
+        e2e = {"value": e2e_evals / e2e_time, "unit": "particle*obs lik evals/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # ---- roofline of the dominant kernel (fused RW mutate) ----
+    mhz, src = sm_max_mhz()
+    peak, pipe = alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, mhz)
+    avg_launch_s = (mut_ms / mut_n) / 1e3 if mut_n else float("nan")
+    achieved = w.P * w.T / avg_launch_s if mut_n else float("nan")
+    fp32_ops, mufu_ops = alu_ops_per_eval(w.K, w.I, w.gamma)
+    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
+            "frac": achieved / peak, "traffic": None, "pipe": pipe, "peak_source": f"{src} SM clock {mhz:.0f} MHz x {SM_COUNT_GB300} SMs",
+            "ops_per_eval": {"fp32": fp32_ops, "mufu": mufu_ops},
+            "kernel": "k_mutate<PolicyEgarchF32<2,2>>", "avg_launch_ms": avg_launch_s * 1e3,
+            "launches": mut_n, "share_of_step": (mut_ms / 1e3) / t_total if t_total else None}
+    if clk.get("sm_mhz"):
+        roof["frac_at_median_clock"] = achieved / alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, clk["sm_mhz"])[0]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_rate(w, y)
+
+    if rank == 0:
+        line = {"metric": "M-phase particle*obs lik evals/s", "value": value,
+                "unit": "particle*obs lik evals/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": w.name, "K": w.K, "I": w.I, "T": w.T, "J": w.J, "N": w.N,
+                           "precision": "fp32 recursion, fp64 accumulators", "tempering": "power",
+                           "sampler": "rw", "stop_rule": f"deterministic Rbar={w.rbar} kappa={w.kappa}",
+                           "cycles_per_run": cycles, "metropolis_steps_per_run": msteps,
+                           "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+                "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+                "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
+                "wall_s": wall}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

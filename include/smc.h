@@ -168,6 +168,20 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info);
  * number of cycles run by this call. */
 smc_status smc_run(smc_ctx* ctx, int max_cycles, smc_cycle_info* info, int* ncycles);
 
+/* Restarts the run from new prior draws (same layout rules as smc_init),
+ * keeping the context's buffers and observations; seed replaces the
+ * configured seed.  No device memory is allocated. */
+smc_status smc_reset(smc_ctx* ctx, const double* theta0, int theta0_on_device, uint64_t seed);
+
+/* Totals since the last smc_init/smc_reset: cycles, Metropolis iterations and
+ * M-phase particle x observation likelihood evaluations (host outputs,
+ * nullable). */
+smc_status smc_run_totals(smc_ctx* ctx, int* cycles, int64_t* metropolis_steps, double* evals);
+
+/* Bytes this context has copied host->device and device->host since it was
+ * created (host outputs, nullable). */
+smc_status smc_transfer_bytes(smc_ctx* ctx, uint64_t* h2d, uint64_t* d2h);
+
 /* log wbar^(J,N) with its working NSE from (ML_se), and log wtilde^(J,N)
  * (Section 4.2).  Host outputs; any may be NULL. */
 smc_status smc_log_ml(smc_ctx* ctx, double* log_ml, double* nse, double* log_ml_tilde);

@@ -1,0 +1,914 @@
+// Host driver and C ABI (include/smc.h).
+//
+// The driver runs Algorithm 2 with the Section 3.3 specifics on one GPU.  All
+// particle data stay on the device; a cycle enqueues its kernels on the
+// context's stream and reads back one small control block after the C/S
+// phases (the power reached, RSS) and one after the M phase (acceptance), so
+// the host decides the number of Metropolis iterations exactly as the paper's
+// rules state.
+#include "../../include/smc.h"
+#include "kernels.cuh"
+#include "phase.cuh"
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace smc {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+#define SMC_DECL_EGARCH(TAG, K)                                                 \
+    cudaError_t launch_mutate_##TAG##_k##K(const MutateArgs& a, cudaStream_t s); \
+    cudaError_t launch_loglik_##TAG##_k##K(const LoglikArgs& a, cudaStream_t s);
+SMC_DECL_EGARCH(f32, 1)
+SMC_DECL_EGARCH(f32, 2)
+SMC_DECL_EGARCH(f32, 3)
+SMC_DECL_EGARCH(f32, 4)
+SMC_DECL_EGARCH(f64, 1)
+SMC_DECL_EGARCH(f64, 2)
+SMC_DECL_EGARCH(f64, 3)
+SMC_DECL_EGARCH(f64, 4)
+cudaError_t launch_mutate_linreg(const MutateArgs& a, cudaStream_t s);
+cudaError_t launch_loglik_linreg(const LoglikArgs& a, cudaStream_t s);
+
+cudaError_t launch_mutate(const MutateArgs& a, int precision, cudaStream_t s)
+{
+    count_launch();
+    if (a.m.kind == SMC_LINREG) return launch_mutate_linreg(a, s);
+    if (precision == SMC_FP32) {
+        switch (a.m.K) {
+        case 1: return launch_mutate_f32_k1(a, s);
+        case 2: return launch_mutate_f32_k2(a, s);
+        case 3: return launch_mutate_f32_k3(a, s);
+        case 4: return launch_mutate_f32_k4(a, s);
+        }
+    } else {
+        switch (a.m.K) {
+        case 1: return launch_mutate_f64_k1(a, s);
+        case 2: return launch_mutate_f64_k2(a, s);
+        case 3: return launch_mutate_f64_k3(a, s);
+        case 4: return launch_mutate_f64_k4(a, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_loglik(const LoglikArgs& a, int precision, cudaStream_t s)
+{
+    count_launch();
+    if (a.m.kind == SMC_LINREG) return launch_loglik_linreg(a, s);
+    if (precision == SMC_FP32) {
+        switch (a.m.K) {
+        case 1: return launch_loglik_f32_k1(a, s);
+        case 2: return launch_loglik_f32_k2(a, s);
+        case 3: return launch_loglik_f32_k3(a, s);
+        case 4: return launch_loglik_f32_k4(a, s);
+        }
+    } else {
+        switch (a.m.K) {
+        case 1: return launch_loglik_f64_k1(a, s);
+        case 2: return launch_loglik_f64_k2(a, s);
+        case 3: return launch_loglik_f64_k3(a, s);
+        case 4: return launch_loglik_f64_k4(a, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------ small kernels
+// Particle-major [P][d] -> parameter-major [d][P].
+__global__ void k_to_soa(const double* __restrict__ in, int P, int d, double* __restrict__ out)
+{
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)P * d) return;
+    const size_t p = e / d, i = e % d;
+    out[i * (size_t)P + p] = in[e];
+}
+
+__global__ void k_to_aos(const double* __restrict__ in, int P, int d, double* __restrict__ out)
+{
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)P * d) return;
+    const size_t p = e / d, i = e % d;
+    out[e] = in[i * (size_t)P + p];
+}
+
+__global__ void k_f64_to_f32(const double* __restrict__ in, size_t n, float* __restrict__ out)
+{
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = (float)in[e];
+}
+
+// Data tempering start: log prior of the prior draws, empty-sample likelihood
+// and volatility state at v_k0 = 0.
+__global__ void k_init_data_tempering(ModelDev m, const double* __restrict__ theta, int P, int ns,
+                                      double* ll, double* lp, double* state)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    double th[kMaxD];
+    for (int i = 0; i < m.d; ++i) th[i] = theta[i * (size_t)P + p];
+    lp[p] = log_prior(m, th);
+    ll[p] = 0.0;
+    for (int k = 0; k < ns; ++k) state[k * (size_t)P + p] = 0.0;
+}
+
+__global__ void k_mark_pending(Ctl* ctl)
+{
+    if (threadIdx.x == 0) ctl->pending = 1;
+}
+
+}  // namespace smc
+
+using namespace smc;
+
+// ================================================================ context
+struct smc_ctx {
+    smc_model model;
+    smc_config cfg;
+    ModelDev mdev;
+    int T = 0, P = 0, d = 0, ns = 0, W = 1;
+    cudaStream_t stream = nullptr;
+    // observations
+    void* obs = nullptr;             // float[T] (FP32 EGARCH) or double[T*W]
+    // particles, double-buffered for the S-phase gather
+    double* theta[2] = {nullptr, nullptr};
+    double* ll[2] = {nullptr, nullptr};
+    double* lp[2] = {nullptr, nullptr};
+    double* state[2] = {nullptr, nullptr};
+    int cur = 0;
+    double* thp = nullptr;           // proposal scratch [d][P]
+    double* logw = nullptr;          // [P] data tempering log weights
+    double* g = nullptr;             // [3][P] test functions
+    // per-group estimators
+    double* a = nullptr;             // [J]
+    double* lw = nullptr;            // [J]
+    double* gstat = nullptr;         // [J][3]
+    int32_t* idx = nullptr;          // [P]
+    double* cov_part = nullptr;
+    int cov_G = 0;
+    double* search_part = nullptr;
+    double* mom_part = nullptr;      // [nf][J][2]
+    double* mom_out = nullptr;       // [nf][4]
+    double* ml_out = nullptr;        // [3]
+    double* L = nullptr;             // [d][d]
+    double** gather_ptrs = nullptr;  // [2][nrows] device row-pointer tables
+    int gather_rows = 0;
+    Ctl* ctl = nullptr;
+    Ctl* ctl_host = nullptr;         // pinned
+    // run state
+    int cycle = 0, t_prev = 0, done = 0;
+    double phi = 0.0;
+    int64_t msteps = 0;
+    double evals = 0.0;
+    uint64_t h2d = 0, d2h = 0;
+    // profiling
+    int profile = 0;
+    double mutate_ms = 0.0;
+    uint64_t mutate_launches = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    std::string err;
+};
+
+static smc_status set_err(smc_ctx* c, smc_status st, const char* fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return st;
+}
+
+#define CU(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return set_err(ctx, SMC_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                           __FILE__, __LINE__);                                               \
+    } while (0)
+
+static void fill_model_dev(const smc_model& m, ModelDev& d)
+{
+    std::memset(&d, 0, sizeof d);
+    d.kind = m.model;
+    d.K = m.K;
+    d.I = m.I;
+    d.gamma = m.gamma;
+    d.eps0_zero = m.eps0_zero;
+    d.p = m.p;
+    d.sigma = m.sigma;
+    d.d_full = m.d_full;
+    d.d = m.n_free > 0 ? m.n_free : m.d_full;
+    d.has_free = m.n_free > 0;
+    for (int i = 0; i < SMC_MAX_D; ++i) {
+        d.free_idx[i] = m.free_idx[i];
+        d.theta_fixed[i] = m.theta_fixed[i];
+        d.prior_mean[i] = m.prior_mean[i];
+        const double sd = m.prior_sd[i] > 0.0 ? m.prior_sd[i] : 1.0;
+        d.prior_isd[i] = 1.0 / sd;
+        d.prior_c[i] = -0.5 * kLog2Pi - std::log(sd);
+        d.prior_lo[i] = m.prior_lo[i];
+    }
+}
+
+static smc_status validate_model(const smc_model* m, smc_ctx* ctx)
+{
+    if (!m) return set_err(ctx, SMC_EINVAL, "model is NULL");
+    if (m->model == SMC_EGARCH) {
+        if (m->K < 1 || m->K > kMaxK || m->I < 1 || m->I > kMaxI)
+            return set_err(ctx, SMC_EINVAL, "EGARCH needs 1 <= K <= %d and 1 <= I <= %d", kMaxK, kMaxI);
+    } else if (m->model == SMC_LINREG) {
+        if (m->p < 1 || m->p > 7 || !(m->sigma > 0.0))
+            return set_err(ctx, SMC_EINVAL, "LINREG needs 1 <= p <= 7 and sigma > 0");
+    } else {
+        return set_err(ctx, SMC_EINVAL, "unknown model %d", m->model);
+    }
+    if (m->d_full < 1 || m->d_full > SMC_MAX_D) return set_err(ctx, SMC_EINVAL, "bad d_full %d", m->d_full);
+    if (m->n_free < 0 || m->n_free > m->d_full) return set_err(ctx, SMC_EINVAL, "bad n_free %d", m->n_free);
+    const int d = m->n_free > 0 ? m->n_free : m->d_full;
+    for (int i = 0; i < m->n_free; ++i)
+        if (m->free_idx[i] < 0 || m->free_idx[i] >= m->d_full)
+            return set_err(ctx, SMC_EINVAL, "free_idx[%d] out of range", i);
+    for (int i = 0; i < d; ++i)
+        if (!(m->prior_sd[i] > 0.0) || !std::isfinite(m->prior_mean[i]))
+            return set_err(ctx, SMC_EINVAL, "prior %d invalid", i);
+    return SMC_OK;
+}
+
+extern "C" {
+
+smc_status smc_model_egarch(smc_model* m, int K, int I, int gamma)
+{
+    if (!m || K < 1 || K > kMaxK || I < 1 || I > kMaxI) return SMC_EINVAL;
+    std::memset(m, 0, sizeof *m);
+    m->model = SMC_EGARCH;
+    m->K = K;
+    m->I = I;
+    m->gamma = gamma ? 1 : 0;
+    int j = 0;
+    auto put = [&](double mean, double sd, double lo) {
+        m->prior_mean[j] = mean;
+        m->prior_sd[j] = sd;
+        m->prior_lo[j] = lo;
+        ++j;
+    };
+    // Table 1 (Section 5.1).
+    put(0.0, 1.0, -INFINITY);                                      // theta_1
+    put(std::log(0.01), 1.0, -INFINITY);                           // theta_2
+    for (int k = 0; k < K; ++k) put(std::atanh(0.95), 1.0, -INFINITY);   // theta_3k
+    for (int k = 0; k < K; ++k) put(std::log(0.10), 1.0, -INFINITY);     // theta_4k
+    if (gamma)
+        for (int k = 0; k < K; ++k) put(0.0, 0.2, -INFINITY);      // theta_5k
+    if (I >= 2) {
+        for (int i = 0; i < I; ++i) put(0.0, 1.0, -INFINITY);      // theta_6i
+        for (int i = 0; i < I; ++i) put(0.0, 1.0, -INFINITY);      // theta_7i
+        for (int i = 0; i < I; ++i) put(0.0, 1.0, -3.0);           // theta_8i
+    }
+    m->d_full = j;
+    return SMC_OK;
+}
+
+int smc_linreg_width(int p) { return p + 1 <= 2 ? 2 : (p + 1 <= 4 ? 4 : 8); }
+
+smc_status smc_model_linreg(smc_model* m, int p, double sigma, const double* prior_mean,
+                            const double* prior_sd)
+{
+    if (!m || p < 1 || p > 7 || !(sigma > 0.0) || !prior_mean || !prior_sd) return SMC_EINVAL;
+    std::memset(m, 0, sizeof *m);
+    m->model = SMC_LINREG;
+    m->p = p;
+    m->sigma = sigma;
+    m->d_full = p;
+    for (int i = 0; i < p; ++i) {
+        m->prior_mean[i] = prior_mean[i];
+        m->prior_sd[i] = prior_sd[i];
+        m->prior_lo[i] = -INFINITY;
+    }
+    return SMC_OK;
+}
+
+int smc_model_dim(const smc_model* m) { return m ? (m->n_free > 0 ? m->n_free : m->d_full) : 0; }
+
+void smc_config_default(smc_config* c)
+{
+    std::memset(c, 0, sizeof *c);
+    c->J = 64;
+    c->N = 1024;
+    c->precision = SMC_FP32;
+    c->tempering = SMC_POWER;
+    c->mutation = SMC_RW;
+    c->resampler = SMC_RESIDUAL;
+    c->d1 = 0.5;
+    c->d2 = 0.2;
+    c->stop_rule = SMC_STOP_DET;
+    c->rbar = 7;
+    c->kappa = 3;
+    c->rmax = 100;
+    c->e1 = 0.35;
+    c->e2 = 0.90;
+    c->h0_tenths = 5;
+    c->hmin_tenths = 1;
+    c->hmax_tenths = 10;
+    c->acc_target = 0.25;
+    c->h_reset_each_cycle = 0;
+    c->n_force = 0;
+    c->search_passes = 6;
+    c->seed = 1;
+}
+
+uint64_t smc_launch_count(void) { return g_launches.load(); }
+
+const char* smc_status_str(smc_status s)
+{
+    switch (s) {
+    case SMC_OK: return "ok";
+    case SMC_EINVAL: return "invalid argument";
+    case SMC_ENOMEM: return "out of memory";
+    case SMC_ECUDA: return "CUDA error";
+    case SMC_EDEGENERATE: return "degenerate weights";
+    case SMC_ENONFINITE: return "non-finite input";
+    case SMC_ETIMEOUT: return "device wait timed out";
+    case SMC_EDONE: return "run complete";
+    }
+    return "unknown status";
+}
+
+const char* smc_last_error(const smc_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------- helpers
+static void release(smc_ctx* c)
+{
+    if (!c) return;
+    void* ptrs[] = {c->obs, c->theta[0], c->theta[1], c->ll[0], c->ll[1], c->lp[0], c->lp[1],
+                    c->state[0], c->state[1], c->thp, c->logw, c->g, c->a, c->lw, c->gstat,
+                    c->idx, c->cov_part, c->search_part, c->mom_part, c->mom_out, c->ml_out,
+                    c->L, c->gather_ptrs, c->ctl};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->ctl_host) cudaFreeHost(c->ctl_host);
+    for (auto& e : c->ev_pool) cudaEventDestroy(e);
+    for (auto& pr : c->ev_pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+}
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t n)
+{
+    return cudaMalloc((void**)p, (n ? n : 1) * sizeof(T));
+}
+
+static smc_status check_device_error(smc_ctx* ctx)
+{
+    if (ctx->ctl_host->err & kErrTimeout) return set_err(ctx, SMC_ETIMEOUT, "a bounded device wait ran out");
+    if (ctx->ctl_host->err & kErrDegenerate) return set_err(ctx, SMC_EDEGENERATE, "a group has zero total weight");
+    if (ctx->ctl_host->err & kErrBounds) return set_err(ctx, SMC_ECUDA, "internal index check failed");
+    return SMC_OK;
+}
+
+static smc_status sync_ctl(smc_ctx* ctx)
+{
+    CU(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->d2h += sizeof(Ctl);
+    CU(cudaStreamSynchronize(ctx->stream));
+    return check_device_error(ctx);
+}
+
+static smc_status fold_profile(smc_ctx* ctx)
+{
+    for (auto& pr : ctx->ev_pending) {
+        float ms = 0.0f;
+        CU(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        ctx->mutate_ms += ms;
+        ctx->ev_pool.push_back(pr.first);
+        ctx->ev_pool.push_back(pr.second);
+    }
+    ctx->ev_pending.clear();
+    return SMC_OK;
+}
+
+static cudaEvent_t take_event(smc_ctx* ctx)
+{
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// One M-phase Metropolis iteration: covariance + Cholesky (with the pending h
+// update), then the fused proposal/likelihood/accept kernel.
+static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
+{
+    const smc_config& c = ctx->cfg;
+    const int P = ctx->P, d = ctx->d;
+    double* th = ctx->theta[ctx->cur];
+    CU(launch_cov(th, d, P, ctx->cov_part, ctx->cov_G, ctx->ctl, 0, c.acc_target, c.hmin_tenths,
+                  c.hmax_tenths, nullptr, nullptr, ctx->L, ctx->stream));
+    MutateArgs a;
+    a.m = ctx->mdev;
+    a.obs = ctx->obs;
+    a.T = Tm;
+    a.W = ctx->W;
+    a.theta = th;
+    a.ll = ctx->ll[ctx->cur];
+    a.lp = ctx->lp[ctx->cur];
+    a.state = ctx->ns ? ctx->state[ctx->cur] : nullptr;
+    a.thp = ctx->thp;
+    a.P = P;
+    a.ns = ctx->ns;
+    a.L = ctx->L;
+    a.phi = phi;
+    a.seed = c.seed;
+    a.cycle = (uint64_t)ctx->cycle;
+    a.iter = (uint64_t)r;
+    a.acc_count = &ctx->ctl->acc_count;
+    a.err = &ctx->ctl->err;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ctx->profile) {
+        e0 = take_event(ctx);
+        e1 = take_event(ctx);
+        CU(cudaEventRecord(e0, ctx->stream));
+    }
+    CU(launch_mutate(a, c.precision, ctx->stream));
+    if (ctx->profile) {
+        CU(cudaEventRecord(e1, ctx->stream));
+        ctx->ev_pending.push_back({e0, e1});
+        ctx->mutate_launches += 1;
+    }
+    k_mark_pending<<<1, 32, 0, ctx->stream>>>(ctx->ctl);
+    count_launch();
+    return SMC_OK;
+}
+
+static smc_status test_functions(smc_ctx* ctx, int rne_only)
+{
+    // EGARCH: g1..g3 rows; other models: the parameters themselves.
+    const int P = ctx->P;
+    if (ctx->model.model == SMC_EGARCH) {
+        CU(launch_testfn(ctx->mdev, ctx->cfg.precision, ctx->theta[ctx->cur], ctx->state[ctx->cur], P,
+                         ctx->g, ctx->stream));
+        CU(launch_moments(ctx->g, 3, ctx->cfg.J, ctx->cfg.N, ctx->mom_part, ctx->mom_out, ctx->ctl, 0,
+                          ctx->stream));
+    } else {
+        CU(launch_moments(ctx->theta[ctx->cur], ctx->d, ctx->cfg.J, ctx->cfg.N, ctx->mom_part,
+                          ctx->mom_out, ctx->ctl, 0, ctx->stream));
+    }
+    (void)rne_only;
+    return SMC_OK;
+}
+
+// S phase (resampling within groups + gather into the other buffer set).
+static smc_status s_phase(smc_ctx* ctx, int mode)
+{
+    const smc_config& c = ctx->cfg;
+    SelectArgs s;
+    std::memset(&s, 0, sizeof s);
+    s.mode = mode;
+    s.ll = ctx->ll[ctx->cur];
+    s.logw = ctx->logw;
+    s.J = c.J;
+    s.N = c.N;
+    s.resid = c.resampler == SMC_RESIDUAL;
+    s.seed = c.seed;
+    s.cycle = (uint64_t)ctx->cycle;
+    s.a = ctx->a;
+    s.lw = ctx->lw;
+    s.gstat = ctx->gstat;
+    s.idx = ctx->idx;
+    s.ctl = ctx->ctl;
+    s.err = &ctx->ctl->err;
+    CU(launch_select(s, ctx->stream));
+    GatherArgs g;
+    g.idx = ctx->idx;
+    g.N = c.N;
+    g.P = ctx->P;
+    g.nrows = ctx->gather_rows;
+    g.src = ctx->gather_ptrs + (size_t)ctx->cur * ctx->gather_rows * 2;
+    g.dst = ctx->gather_ptrs + (size_t)ctx->cur * ctx->gather_rows * 2 + ctx->gather_rows;
+    CU(launch_gather(g, ctx->stream));
+    ctx->cur ^= 1;
+    return SMC_OK;
+}
+
+static smc_status start_run(smc_ctx* ctx, const double* theta0, int theta0_on_device);
+
+extern "C" {
+
+smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, const double* X,
+                    int T, const double* theta0, int theta0_on_device, void* stream, smc_ctx** out)
+{
+    if (!out) return SMC_EINVAL;
+    *out = nullptr;
+    smc_ctx* ctx = new (std::nothrow) smc_ctx();
+    if (!ctx) return SMC_ENOMEM;
+    *out = ctx;   // caller frees even on error, so the message stays readable
+    smc_status st = validate_model(m, ctx);
+    if (st != SMC_OK) return st;
+    if (!c) return set_err(ctx, SMC_EINVAL, "config is NULL");
+    if (c->J < 2 || c->N < 1 || c->N > SMC_MAX_N)
+        return set_err(ctx, SMC_EINVAL, "need J >= 2 and 1 <= N <= %d", SMC_MAX_N);
+    if ((long long)c->J * c->N > (1ll << 30)) return set_err(ctx, SMC_EINVAL, "too many particles");
+    if (T < 1 || !y) return set_err(ctx, SMC_EINVAL, "need T >= 1 observations");
+    if (m->model == SMC_LINREG && !X) return set_err(ctx, SMC_EINVAL, "LINREG needs X");
+    if (!theta0) return set_err(ctx, SMC_EINVAL, "theta0 is NULL");
+    if (c->mutation != SMC_RW) return set_err(ctx, SMC_EINVAL, "only random-walk mutation is built");
+    if (c->tempering != SMC_POWER && c->tempering != SMC_DATA)
+        return set_err(ctx, SMC_EINVAL, "unknown tempering %d", c->tempering);
+    if (c->precision != SMC_FP32 && c->precision != SMC_FP64)
+        return set_err(ctx, SMC_EINVAL, "unknown precision %d", c->precision);
+    if (m->model == SMC_LINREG && c->precision != SMC_FP64)
+        return set_err(ctx, SMC_EINVAL, "LINREG runs in FP64 only");
+    if (!(c->d1 > 0.0 && c->d1 < 1.0) || c->rbar < 1 || c->kappa < 1 || c->rmax < 1 ||
+        c->hmin_tenths < 1 || c->hmax_tenths < c->hmin_tenths || c->h0_tenths < c->hmin_tenths ||
+        c->h0_tenths > c->hmax_tenths || c->search_passes < 1 || c->n_force < 0 ||
+        c->n_force > SMC_MAX_FORCE)
+        return set_err(ctx, SMC_EINVAL, "invalid simulator settings");
+    for (int t = 0; t < T; ++t)
+        if (!std::isfinite(y[t])) return set_err(ctx, SMC_ENONFINITE, "y[%d] is not finite", t);
+    if (X)
+        for (long long i = 0; i < (long long)T * m->p; ++i)
+            if (!std::isfinite(X[i])) return set_err(ctx, SMC_ENONFINITE, "X[%lld] is not finite", i);
+
+    ctx->model = *m;
+    ctx->cfg = *c;
+    fill_model_dev(*m, ctx->mdev);
+    ctx->T = T;
+    ctx->P = c->J * c->N;
+    ctx->d = ctx->mdev.d;
+    ctx->ns = m->model == SMC_EGARCH ? m->K + 1 : 0;
+    ctx->W = m->model == SMC_LINREG ? smc_linreg_width(m->p) : 1;
+    ctx->stream = (cudaStream_t)stream;
+    const int P = ctx->P, d = ctx->d, J = c->J;
+    const size_t Ps = (size_t)P;
+
+    // observations
+    if (m->model == SMC_LINREG) {
+        std::vector<double> rec((size_t)T * ctx->W, 0.0);
+        for (int t = 0; t < T; ++t) {
+            for (int i = 0; i < m->p; ++i) rec[(size_t)t * ctx->W + i] = X[(size_t)t * m->p + i];
+            rec[(size_t)t * ctx->W + m->p] = y[t];
+        }
+        double* o;
+        CU(dalloc(&o, rec.size()));
+        ctx->obs = o;
+        CU(cudaMemcpyAsync(o, rec.data(), rec.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        ctx->h2d += rec.size() * sizeof(double);
+        CU(cudaStreamSynchronize(ctx->stream));
+    } else if (c->precision == SMC_FP32) {
+        double* tmp;
+        float* o;
+        CU(dalloc(&tmp, T));
+        CU(dalloc(&o, T));
+        ctx->obs = o;
+        CU(cudaMemcpyAsync(tmp, y, (size_t)T * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        ctx->h2d += (size_t)T * sizeof(double);
+        k_f64_to_f32<<<(T + 255) / 256, 256, 0, ctx->stream>>>(tmp, (size_t)T, o);
+        count_launch();
+        CU(cudaStreamSynchronize(ctx->stream));
+        cudaFree(tmp);
+    } else {
+        double* o;
+        CU(dalloc(&o, T));
+        ctx->obs = o;
+        CU(cudaMemcpyAsync(o, y, (size_t)T * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        ctx->h2d += (size_t)T * sizeof(double);
+    }
+
+    for (int b = 0; b < 2; ++b) {
+        CU(dalloc(&ctx->theta[b], Ps * d));
+        CU(dalloc(&ctx->ll[b], Ps));
+        CU(dalloc(&ctx->lp[b], Ps));
+        CU(dalloc(&ctx->state[b], Ps * (ctx->ns ? ctx->ns : 1)));
+    }
+    CU(dalloc(&ctx->thp, Ps * d));
+    CU(dalloc(&ctx->logw, Ps));
+    CU(dalloc(&ctx->g, Ps * 3));
+    CU(dalloc(&ctx->a, J));
+    CU(dalloc(&ctx->lw, J));
+    CU(dalloc(&ctx->gstat, (size_t)J * 3));
+    CU(dalloc(&ctx->idx, Ps));
+    ctx->cov_G = cov_grid(P);
+    CU(dalloc(&ctx->cov_part, (size_t)ctx->cov_G * (d + d * (d + 1) / 2)));
+    CU(dalloc(&ctx->search_part, search_part_len(P)));
+    const int nf_max = d + 3;
+    CU(dalloc(&ctx->mom_part, (size_t)nf_max * J * 2));
+    CU(dalloc(&ctx->mom_out, (size_t)nf_max * 4));
+    CU(dalloc(&ctx->ml_out, 3));
+    CU(dalloc(&ctx->L, (size_t)d * d));
+    CU(dalloc(&ctx->ctl, 1));
+    CU(cudaMallocHost((void**)&ctx->ctl_host, sizeof(Ctl)));
+
+    // gather tables: rows of theta, ll, lp, state for both directions
+    ctx->gather_rows = d + 2 + ctx->ns;
+    std::vector<double*> tab((size_t)2 * 2 * ctx->gather_rows);
+    for (int dir = 0; dir < 2; ++dir) {
+        const int from = dir, to = dir ^ 1;
+        double** srcs = &tab[(size_t)dir * 2 * ctx->gather_rows];
+        double** dsts = srcs + ctx->gather_rows;
+        int r = 0;
+        for (int i = 0; i < d; ++i, ++r) {
+            srcs[r] = ctx->theta[from] + (size_t)i * Ps;
+            dsts[r] = ctx->theta[to] + (size_t)i * Ps;
+        }
+        srcs[r] = ctx->ll[from];
+        dsts[r++] = ctx->ll[to];
+        srcs[r] = ctx->lp[from];
+        dsts[r++] = ctx->lp[to];
+        for (int k = 0; k < ctx->ns; ++k, ++r) {
+            srcs[r] = ctx->state[from] + (size_t)k * Ps;
+            dsts[r] = ctx->state[to] + (size_t)k * Ps;
+        }
+    }
+    CU(dalloc(&ctx->gather_ptrs, tab.size()));
+    CU(cudaMemcpyAsync(ctx->gather_ptrs, tab.data(), tab.size() * sizeof(double*), cudaMemcpyHostToDevice,
+                       ctx->stream));
+
+    st = start_run(ctx, theta0, theta0_on_device);
+    if (st != SMC_OK) return st;
+    return SMC_OK;
+}
+
+}  // extern "C"
+
+// Algorithm 1, step 1: particles from the prior, their log prior and (power
+// tempering) full-sample log likelihood; estimator and control state zeroed.
+static smc_status start_run(smc_ctx* ctx, const double* theta0, int theta0_on_device)
+{
+    const smc_config* c = &ctx->cfg;
+    const int P = ctx->P, d = ctx->d, J = c->J, T = ctx->T;
+    const size_t Ps = (size_t)P;
+    if (theta0_on_device) {
+        CU(cudaMemcpyAsync(ctx->theta[0], theta0, Ps * d * sizeof(double), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+    } else {
+        CU(cudaMemcpyAsync(ctx->thp, theta0, Ps * d * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        ctx->h2d += Ps * d * sizeof(double);
+        const size_t n = Ps * d;
+        k_to_soa<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->thp, P, d, ctx->theta[0]);
+        count_launch();
+    }
+    Ctl init;
+    std::memset(&init, 0, sizeof init);
+    init.h_tenths = c->h0_tenths;
+    CU(cudaMemcpyAsync(ctx->ctl, &init, sizeof init, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemsetAsync(ctx->a, 0, (size_t)J * sizeof(double), ctx->stream));
+    if (c->tempering == SMC_POWER) {
+        LoglikArgs la;
+        la.m = ctx->mdev;
+        la.obs = ctx->obs;
+        la.T = T;
+        la.W = ctx->W;
+        la.theta = ctx->theta[0];
+        la.ll = ctx->ll[0];
+        la.lp = ctx->lp[0];
+        la.state = ctx->ns ? ctx->state[0] : nullptr;
+        la.P = P;
+        la.ns = ctx->ns;
+        la.err = &ctx->ctl->err;
+        CU(launch_loglik(la, c->precision, ctx->stream));
+    } else {
+        k_init_data_tempering<<<(P + 255) / 256, 256, 0, ctx->stream>>>(ctx->mdev, ctx->theta[0], P,
+                                                                        ctx->ns, ctx->ll[0], ctx->lp[0],
+                                                                        ctx->state[0]);
+        count_launch();
+    }
+    ctx->cur = 0;
+    ctx->cycle = 0;
+    ctx->t_prev = 0;
+    ctx->done = 0;
+    ctx->phi = 0.0;
+    ctx->msteps = 0;
+    ctx->evals = 0.0;
+    return sync_ctl(ctx);
+}
+
+extern "C" {
+
+smc_status smc_reset(smc_ctx* ctx, const double* theta0, int theta0_on_device, uint64_t seed)
+{
+    if (!ctx || !theta0) return SMC_EINVAL;
+    ctx->cfg.seed = seed;
+    return start_run(ctx, theta0, theta0_on_device);
+}
+
+smc_status smc_run_totals(smc_ctx* ctx, int* cycles, int64_t* metropolis_steps, double* evals)
+{
+    if (!ctx) return SMC_EINVAL;
+    if (cycles) *cycles = ctx->cycle;
+    if (metropolis_steps) *metropolis_steps = ctx->msteps;
+    if (evals) *evals = ctx->evals;
+    return SMC_OK;
+}
+
+smc_status smc_transfer_bytes(smc_ctx* ctx, uint64_t* h2d, uint64_t* d2h)
+{
+    if (!ctx) return SMC_EINVAL;
+    if (h2d) *h2d = ctx->h2d;
+    if (d2h) *d2h = ctx->d2h;
+    return SMC_OK;
+}
+
+smc_status smc_profile(smc_ctx* ctx, int enable)
+{
+    if (!ctx) return SMC_EINVAL;
+    ctx->profile = enable ? 1 : 0;
+    return SMC_OK;
+}
+
+smc_status smc_mutate_time(smc_ctx* ctx, double* ms, uint64_t* launches, int reset)
+{
+    if (!ctx) return SMC_EINVAL;
+    CU(cudaStreamSynchronize(ctx->stream));
+    smc_status st = fold_profile(ctx);
+    if (st != SMC_OK) return st;
+    if (ms) *ms = ctx->mutate_ms;
+    if (launches) *launches = ctx->mutate_launches;
+    if (reset) {
+        ctx->mutate_ms = 0.0;
+        ctx->mutate_launches = 0;
+    }
+    return SMC_OK;
+}
+
+smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
+{
+    if (!ctx) return SMC_EINVAL;
+    if (ctx->done) return set_err(ctx, SMC_EDONE, "the run has reached the full posterior");
+    const smc_config& c = ctx->cfg;
+    const int P = ctx->P;
+    ctx->cycle += 1;
+    int t_l = ctx->T;
+    double rss = 1.0;
+    int forced = 0;
+    smc_status st;
+    if (c.tempering == SMC_POWER) {
+        // ---- C phase: next power by k-ary bisection on RSS ----
+        CU(launch_power_search(ctx->ll[ctx->cur], P, c.d1, c.search_passes, ctx->search_part, ctx->ctl,
+                               ctx->stream));
+        // ---- S phase (weights dphi * l_n) ----
+        st = s_phase(ctx, 0);
+        if (st != SMC_OK) return st;
+        CU(launch_cycle_close(ctx->gstat, ctx->lw, c.J, c.N, 1, ctx->ctl, ctx->stream));
+        st = sync_ctl(ctx);
+        if (st != SMC_OK) return st;
+        ctx->phi = ctx->ctl_host->phi;
+        rss = ctx->ctl_host->rss;
+        forced = ctx->ctl_host->last;
+    } else {
+        return set_err(ctx, SMC_EINVAL, "data tempering is not built in this version");
+    }
+    // ---- M phase ----
+    const double phim = c.tempering == SMC_POWER ? ctx->phi : 1.0;
+    const int Tm = c.tempering == SMC_POWER ? ctx->T : t_l;
+    if (c.h_reset_each_cycle) {
+        // the pending count (if any) was applied at the end of the last M phase
+        int h0 = c.h0_tenths;
+        CU(cudaMemcpyAsync(&ctx->ctl->h_tenths, &h0, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    int R = c.stop_rule == SMC_STOP_DET ? (rss < c.d2 ? c.kappa * c.rbar : c.rbar) : c.rmax;
+    const double E = forced ? c.e2 : c.e1;
+    int r = 0;
+    for (; r < R; ++r) {
+        st = m_iteration(ctx, r, Tm, phim);
+        if (st != SMC_OK) return st;
+        if (c.stop_rule == SMC_STOP_RNE) {
+            st = test_functions(ctx, 1);
+            if (st != SMC_OK) return st;
+            st = sync_ctl(ctx);
+            if (st != SMC_OK) return st;
+            if (ctx->ctl_host->mean_rne >= E) {
+                ++r;
+                break;
+            }
+        }
+    }
+    CU(launch_adapt_h(ctx->ctl, P, c.acc_target, c.hmin_tenths, c.hmax_tenths, ctx->stream));
+    st = sync_ctl(ctx);
+    if (st != SMC_OK) return st;
+    if (ctx->profile) {
+        st = fold_profile(ctx);
+        if (st != SMC_OK) return st;
+    }
+    ctx->t_prev = t_l;
+    ctx->msteps += r;
+    ctx->evals += (double)r * (double)P * (double)Tm;
+    if (c.tempering == SMC_POWER ? ctx->ctl_host->last : (t_l >= ctx->T)) ctx->done = 1;
+    if (info) {
+        info->cycle = ctx->cycle;
+        info->t = t_l;
+        info->phi = phim;
+        info->rss = rss;
+        info->R = r;
+        info->h_tenths = ctx->ctl_host->h_tenths;
+        info->acc_rate = ctx->ctl_host->acc_n ? ctx->ctl_host->acc_sum / ctx->ctl_host->acc_n : 0.0;
+        info->evals = (double)r * (double)P * (double)Tm;
+        info->done = ctx->done;
+    }
+    return SMC_OK;
+}
+
+smc_status smc_run(smc_ctx* ctx, int max_cycles, smc_cycle_info* info, int* ncycles)
+{
+    if (!ctx) return SMC_EINVAL;
+    int n = 0;
+    smc_cycle_info ci;
+    std::memset(&ci, 0, sizeof ci);
+    while (!ctx->done && (max_cycles <= 0 || n < max_cycles)) {
+        smc_status st = smc_cycle(ctx, &ci);
+        if (st != SMC_OK) {
+            if (ncycles) *ncycles = n;
+            return st;
+        }
+        ++n;
+    }
+    if (info) *info = ci;
+    if (ncycles) *ncycles = n;
+    return SMC_OK;
+}
+
+smc_status smc_log_ml(smc_ctx* ctx, double* log_ml, double* nse, double* log_ml_tilde)
+{
+    if (!ctx) return SMC_EINVAL;
+    CU(launch_ml(ctx->a, ctx->cfg.J, ctx->ctl, ctx->ml_out, ctx->stream));
+    double h[3];
+    CU(cudaMemcpyAsync(h, ctx->ml_out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->d2h += sizeof h;
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (log_ml) *log_ml = h[0];
+    if (nse) *nse = h[1];
+    if (log_ml_tilde) *log_ml_tilde = h[2];
+    return SMC_OK;
+}
+
+smc_status smc_moments(smc_ctx* ctx, double* out, int* nf)
+{
+    if (!ctx || !out) return SMC_EINVAL;
+    const int d = ctx->d, J = ctx->cfg.J, N = ctx->cfg.N;
+    CU(launch_moments(ctx->theta[ctx->cur], d, J, N, ctx->mom_part, ctx->mom_out, nullptr, 0, ctx->stream));
+    CU(cudaMemcpyAsync(out, ctx->mom_out, (size_t)d * 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    int n = d;
+    if (ctx->model.model == SMC_EGARCH) {
+        CU(launch_testfn(ctx->mdev, ctx->cfg.precision, ctx->theta[ctx->cur], ctx->state[ctx->cur], ctx->P,
+                         ctx->g, ctx->stream));
+        CU(launch_moments(ctx->g, 3, J, N, ctx->mom_part, ctx->mom_out, nullptr, 0, ctx->stream));
+        CU(cudaMemcpyAsync(out + (size_t)d * 4, ctx->mom_out, 3 * 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        n += 3;
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (nf) *nf = n;
+    return SMC_OK;
+}
+
+smc_status smc_get_particles(smc_ctx* ctx, double* theta, double* loglik, double* logprior, double* state)
+{
+    if (!ctx) return SMC_EINVAL;
+    const int P = ctx->P, d = ctx->d;
+    const size_t Ps = (size_t)P;
+    if (theta) {
+        const size_t n = Ps * d;
+        k_to_aos<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->theta[ctx->cur], P, d, ctx->thp);
+        count_launch();
+        CU(cudaMemcpyAsync(theta, ctx->thp, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    if (loglik) CU(cudaMemcpyAsync(loglik, ctx->ll[ctx->cur], Ps * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (logprior) CU(cudaMemcpyAsync(logprior, ctx->lp[ctx->cur], Ps * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (state && ctx->ns) {
+        CU(cudaStreamSynchronize(ctx->stream));
+        const size_t n = Ps * ctx->ns;
+        k_to_aos<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(ctx->state[ctx->cur], P, ctx->ns, ctx->thp);
+        count_launch();
+        CU(cudaMemcpyAsync(state, ctx->thp, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    return SMC_OK;
+}
+
+void smc_free(smc_ctx* ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    release(ctx);
+    delete ctx;
+}
+
+}  // extern "C"

@@ -17,6 +17,7 @@ constexpr int kMaxD = 32;       // free parameters carried by a particle
 constexpr int kMaxK = 4;        // volatility factors
 constexpr int kMaxI = 4;        // mixture components
 constexpr int kMaxState = kMaxK + 1;
+constexpr int kMaxN = 8192;      // particles per group (S-phase shared memory)
 
 enum : uint32_t { kTagNormal = 1u, kTagUniform = 2u, kTagResample = 3u };
 
@@ -195,10 +196,17 @@ __device__ inline uint64_t block_inclusive_scan_u64(uint64_t v, uint64_t* scratc
 
 // ------------------------------------------------- mbarrier + bulk async copy
 // Observation staging uses the Blackwell bulk-copy engine (cp.async.bulk, the
-// non-tensor form of TMA) completing on an mbarrier.  Every wait is bounded:
-// after kSpinLimit unsuccessful polls the wait reports failure and the caller
-// records an error instead of hanging.
-constexpr uint32_t kSpinLimit = 1u << 24;
+// non-tensor form of TMA) completing on an mbarrier.  Every wait is bounded in
+// wall time (kWaitLimitNs on the global nanosecond timer): when it runs out the
+// wait reports failure and the caller records an error instead of hanging.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
@@ -243,9 +251,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
 {
-    for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-    return false;
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
 }
 
 // Global -> shared bulk copy of `bytes` (multiple of 16, both addresses

@@ -1,0 +1,735 @@
+// C-phase search, S phase, covariance/Cholesky and estimator kernels.
+#include "phase.cuh"
+
+#include <cstdio>
+
+namespace smc {
+
+extern void count_launch();
+
+int device_sm_count()
+{
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0, n = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached = n > 0 ? n : 1;
+    }
+    return cached;
+}
+
+// ============================================================ covariance
+// V_lr of Section 3.3 is the sample variance of the current particles, pooled
+// over all J N.  Sums are taken about a shift (particle 0) so that the final
+// combination does not cancel: V = [S2 - S1 S1'/P] / (P - 1) on shifted data.
+constexpr int kCovThreads = 256;
+constexpr int kCovTile = 64;
+constexpr int kCovMaxAcc = (kMaxD + kMaxD * (kMaxD + 1) / 2 + kCovThreads - 1) / kCovThreads;
+
+int cov_grid(int P)
+{
+    const int by_tiles = (P + kCovTile - 1) / kCovTile;
+    const int cap = 2 * device_sm_count();
+    return by_tiles < cap ? by_tiles : cap;
+}
+
+__device__ __forceinline__ void unpack_pair(int e, int& i, int& k)
+{
+    // e = i (i + 1) / 2 + k, 0 <= k <= i
+    int ii = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while ((ii + 1) * (ii + 2) / 2 <= e) ++ii;
+    while (ii * (ii + 1) / 2 > e) --ii;
+    i = ii;
+    k = e - ii * (ii + 1) / 2;
+}
+
+__global__ void __launch_bounds__(kCovThreads) k_cov_partial(const double* __restrict__ theta, int d,
+                                                            int P, double* __restrict__ part)
+{
+    __shared__ double tile[kMaxD][kCovTile + 1];
+    __shared__ double shift[kMaxD];
+    __shared__ int pi_[kMaxD * (kMaxD + 1) / 2], pk_[kMaxD * (kMaxD + 1) / 2];
+    const int npair = d * (d + 1) / 2;
+    const int nacc = d + npair;
+    const size_t Ps = (size_t)P;
+    for (int e = threadIdx.x; e < npair; e += blockDim.x) unpack_pair(e, pi_[e], pk_[e]);
+    for (int i = threadIdx.x; i < d; i += blockDim.x) shift[i] = theta[i * Ps];
+    double acc[kCovMaxAcc];
+#pragma unroll
+    for (int r = 0; r < kCovMaxAcc; ++r) acc[r] = 0.0;
+    const int per = (P + gridDim.x - 1) / gridDim.x;
+    const int n0 = blockIdx.x * per;
+    const int n1 = min(P, n0 + per);
+    __syncthreads();
+    for (int base = n0; base < n1; base += kCovTile) {
+        const int cnt = min(kCovTile, n1 - base);
+        for (int e = threadIdx.x; e < d * kCovTile; e += blockDim.x) {
+            const int i = e / kCovTile, n = e % kCovTile;
+            tile[i][n] = n < cnt ? theta[i * Ps + base + n] - shift[i] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kCovMaxAcc; ++r) {
+            const int e = threadIdx.x + r * blockDim.x;
+            if (e < d) {
+                double s = 0.0;
+                for (int n = 0; n < cnt; ++n) s += tile[e][n];
+                acc[r] += s;
+            } else if (e < nacc) {
+                const int i = pi_[e - d], k = pk_[e - d];
+                double s = 0.0;
+                for (int n = 0; n < cnt; ++n) s = fma(tile[i][n], tile[k][n], s);
+                acc[r] += s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < kCovMaxAcc; ++r) {
+        const int e = threadIdx.x + r * blockDim.x;
+        if (e < nacc) part[(size_t)blockIdx.x * nacc + e] = acc[r];
+    }
+}
+
+__device__ void apply_h_update(Ctl* ctl, int P, double target, int hmin, int hmax)
+{
+    if (ctl->pending) {
+        const double rate = (double)ctl->acc_count / (double)P;
+        int h = ctl->h_tenths + (rate > target ? 1 : -1);
+        h = h < hmin ? hmin : (h > hmax ? hmax : h);
+        ctl->h_tenths = h;
+        ctl->acc_sum += rate;
+        ctl->acc_n += 1;
+        ctl->acc_count = 0ull;
+        ctl->pending = 0;
+    }
+}
+
+__global__ void k_adapt_h(Ctl* ctl, int P, double target, int hmin, int hmax)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) apply_h_update(ctl, P, target, hmin, hmax);
+}
+
+// Combines the partial sums, updates h from the previous iteration's
+// acceptance (when a control block is given) and factors Sigma = h^2 V by a
+// right-looking Cholesky in shared memory; a non-positive pivot zeroes its
+// column, as in the oracle.
+__global__ void __launch_bounds__(kCovThreads) k_cov_final(const double* __restrict__ part, int G, int d,
+                                                          int P, const double* __restrict__ theta,
+                                                          Ctl* ctl, int fixed_h, double target,
+                                                          int hmin, int hmax, double* mean_out,
+                                                          double* cov_out, double* L_out)
+{
+    __shared__ double S1[kMaxD];
+    __shared__ double A[kMaxD][kMaxD + 1];
+    __shared__ double shift[kMaxD];
+    __shared__ double hh;
+    const int npair = d * (d + 1) / 2;
+    const int nacc = d + npair;
+    const size_t Ps = (size_t)P;
+    if (threadIdx.x == 0) {
+        int h = fixed_h;
+        if (ctl) {
+            apply_h_update(ctl, P, target, hmin, hmax);
+            h = ctl->h_tenths;
+        }
+        hh = (h / 10.0) * (h / 10.0);
+    }
+    for (int i = threadIdx.x; i < d; i += blockDim.x) shift[i] = theta[i * Ps];
+    for (int e = threadIdx.x; e < d; e += blockDim.x) {
+        double s = 0.0;
+        for (int g = 0; g < G; ++g) s += part[(size_t)g * nacc + e];
+        S1[e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < npair; e += blockDim.x) {
+        int i, k;
+        unpack_pair(e, i, k);
+        double s = 0.0;
+        for (int g = 0; g < G; ++g) s += part[(size_t)g * nacc + d + e];
+        const double c = (s - S1[i] * S1[k] / (double)P) / (double)(P - 1);
+        A[i][k] = c;
+        A[k][i] = c;
+    }
+    __syncthreads();
+    if (mean_out)
+        for (int i = threadIdx.x; i < d; i += blockDim.x) mean_out[i] = shift[i] + S1[i] / (double)P;
+    if (cov_out)
+        for (int e = threadIdx.x; e < d * d; e += blockDim.x) cov_out[e] = A[e / d][e % d];
+    for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
+        const int i = e / d, k = e % d;
+        if (k <= i) A[i][k] *= hh;
+    }
+    __syncthreads();
+    for (int j = 0; j < d; ++j) {
+        if (threadIdx.x == 0) A[j][j] = A[j][j] > 0.0 ? sqrt(A[j][j]) : 0.0;
+        __syncthreads();
+        const double ljj = A[j][j];
+        for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) A[i][j] = ljj > 0.0 ? A[i][j] / ljj : 0.0;
+        __syncthreads();
+        const int m = d - j - 1;
+        for (int e = threadIdx.x; e < m * (m + 1) / 2; e += blockDim.x) {
+            int ii, kk;
+            unpack_pair(e, ii, kk);
+            ii += j + 1;
+            kk += j + 1;
+            A[ii][kk] = fma(-A[ii][j], A[kk][j], A[ii][kk]);
+        }
+        __syncthreads();
+    }
+    if (L_out)
+        for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
+            const int i = e / d, k = e % d;
+            L_out[e] = k <= i ? A[i][k] : 0.0;
+        }
+}
+
+cudaError_t launch_cov(const double* theta, int d, int P, double* part, int G, Ctl* ctl,
+                       int fixed_h_tenths, double acc_target, int hmin, int hmax, double* mean,
+                       double* cov, double* L, cudaStream_t s)
+{
+    k_cov_partial<<<G, kCovThreads, 0, s>>>(theta, d, P, part);
+    count_launch();
+    k_cov_final<<<1, kCovThreads, 0, s>>>(part, G, d, P, theta, ctl, fixed_h_tenths, acc_target,
+                                          hmin, hmax, mean, cov, L);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adapt_h(Ctl* ctl, int P, double acc_target, int hmin, int hmax, cudaStream_t s)
+{
+    k_adapt_h<<<1, 32, 0, s>>>(ctl, P, acc_target, hmin, hmax);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ===================================================== power-tempering search
+// RSS(dphi) = (sum_n w_n)^2 / (P sum_n w_n^2) with w_n = exp(dphi (l_n - max l))
+// (Section 3.3, pooled over all particles).  One pass evaluates 32 candidate
+// increments spread evenly over (lo, hi]: lane c of every warp owns candidate
+// c and the warp walks its particles with shuffles.  Candidate weights are
+// FP32 hardware exponentials, summed in FP32 over one warp tile and in FP64
+// across tiles; the chosen power is then used in FP64 for the weights.
+constexpr int kSearchThreads = 256;
+constexpr int kCand = 32;
+
+int search_grid(int P)
+{
+    const int by = (P + kSearchThreads - 1) / kSearchThreads;
+    const int cap = 2 * device_sm_count();
+    return by < cap ? by : cap;
+}
+
+size_t search_part_len(int P)
+{
+    return (size_t)search_grid(P) * kCand * 2 + 2 * (size_t)search_grid(P);
+}
+
+__global__ void __launch_bounds__(kSearchThreads) k_llmax_partial(const double* __restrict__ ll, int P,
+                                                                 double* part)
+{
+    __shared__ double red[32];
+    double m = -INFINITY;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < P; n += gridDim.x * blockDim.x) {
+        const double x = ll[n];
+        if (x > m) m = x;
+    }
+    m = block_max(m, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = m;
+}
+
+__global__ void k_search_init(const double* part, int G, Ctl* ctl)
+{
+    if (threadIdx.x != 0) return;
+    double m = -INFINITY;
+    for (int g = 0; g < G; ++g) m = fmax(m, part[g]);
+    ctl->llmax = m;
+    ctl->lo = 0.0;
+    ctl->hi = 1.0 - ctl->phi;
+    ctl->pass = 0;
+    ctl->done = (m == -INFINITY) || !(ctl->hi > 0.0);
+    ctl->last = ctl->done;
+    ctl->dphi = ctl->hi;
+    if (m == -INFINITY) raise_error(&ctl->err, kErrDegenerate);
+}
+
+__device__ __forceinline__ double candidate(double lo, double hi, int c)
+{
+    return c == kCand - 1 ? hi : lo + (hi - lo) * (double)(c + 1) / (double)kCand;
+}
+
+__global__ void __launch_bounds__(kSearchThreads) k_power_pass(const double* __restrict__ ll, int P,
+                                                              const Ctl* ctl, double* part)
+{
+    if (ctl->done) return;
+    __shared__ double s1w[kSearchThreads / 32][kCand], s2w[kSearchThreads / 32][kCand];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double llmax = ctl->llmax;
+    const float dc = (float)(candidate(ctl->lo, ctl->hi, lane) * kLog2e);
+    double s1 = 0.0, s2 = 0.0;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    for (int base = gw * 32; base < P; base += nw * 32) {
+        const int n = base + lane;
+        const float x = n < P ? (float)(ll[n] - llmax) : -INFINITY;
+        float a1 = 0.0f, a2 = 0.0f;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const float xj = __shfl_sync(0xffffffffu, x, j);
+            const float w = xj == -INFINITY ? 0.0f : ex2_approx(dc * xj);
+            a1 += w;
+            a2 = fmaf(w, w, a2);
+        }
+        s1 += (double)a1;
+        s2 += (double)a2;
+    }
+    s1w[warp][lane] = s1;
+    s2w[warp][lane] = s2;
+    __syncthreads();
+    if (warp == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t1 += s1w[w][lane];
+            t2 += s2w[w][lane];
+        }
+        part[((size_t)blockIdx.x * kCand + lane) * 2 + 0] = t1;
+        part[((size_t)blockIdx.x * kCand + lane) * 2 + 1] = t2;
+    }
+}
+
+__global__ void k_power_select(const double* part, int G, int P, double d1, int passes, Ctl* ctl)
+{
+    if (ctl->done) return;
+    const int lane = threadIdx.x;
+    double t1 = 0.0, t2 = 0.0;
+    for (int g = 0; g < G; ++g) {
+        t1 += part[((size_t)g * kCand + lane) * 2 + 0];
+        t2 += part[((size_t)g * kCand + lane) * 2 + 1];
+    }
+    const double rss = t1 * t1 / ((double)P * t2);
+    const unsigned below = __ballot_sync(0xffffffffu, rss < d1);
+    if (lane == 0) {
+        const double lo = ctl->lo, hi = ctl->hi;
+        if (below == 0u) {
+            // RSS stays >= D1 up to hi: in the first pass this takes the whole
+            // remaining power (the last cycle); later it cannot occur because hi
+            // was itself a candidate with RSS < D1.
+            ctl->dphi = hi;
+            ctl->done = 1;
+            ctl->last = ctl->pass == 0;
+        } else {
+            const int c = __ffs(below) - 1;
+            const double nhi = candidate(lo, hi, c);
+            const double nlo = c == 0 ? lo : candidate(lo, hi, c - 1);
+            ctl->lo = nlo;
+            ctl->hi = nhi;
+            ctl->dphi = nhi;
+            ctl->pass += 1;
+            if (ctl->pass >= passes) ctl->done = 1;
+        }
+    }
+}
+
+cudaError_t launch_power_search(const double* ll, int P, double d1, int passes, double* part,
+                                Ctl* ctl, cudaStream_t s)
+{
+    const int G = search_grid(P);
+    double* mx = part + (size_t)G * kCand * 2;
+    k_llmax_partial<<<G, kSearchThreads, 0, s>>>(ll, P, mx);
+    count_launch();
+    k_search_init<<<1, 32, 0, s>>>(mx, G, ctl);
+    count_launch();
+    for (int p = 0; p < passes; ++p) {
+        k_power_pass<<<G, kSearchThreads, 0, s>>>(ll, P, ctl, part);
+        count_launch();
+        k_power_select<<<1, 32, 0, s>>>(part, G, P, d1, passes, ctl);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+// ================================================================= S phase
+// One block per group.  Weights (FP64): w_n = exp(log w_n - max_n log w_n);
+// log wbar_j(l-1) = max + log(sum_n w_n / N) (Section 4.2).  Resampling in
+// integer fixed point (the reading stated in smc.h): everything after the
+// quantisation is integer arithmetic, so the selected indices do not depend
+// on summation order or thread count.
+constexpr int kSelThreads = 1024;
+
+size_t select_smem(int N) { return (size_t)N * (sizeof(uint64_t) + sizeof(uint32_t)); }
+
+__device__ int upper_bound_u64(const uint64_t* a, int n, uint64_t u)
+{
+    int lo = 0, hi = n;   // first index with a[idx] > u
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] > u) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo < n ? lo : n - 1;
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int N = a.N;
+    double* ws = reinterpret_cast<double*>(sm_raw);                        // w, then q, then prefix r
+    uint64_t* qs = reinterpret_cast<uint64_t*>(sm_raw);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(sm_raw + (size_t)N * sizeof(uint64_t));
+    __shared__ double redd[32];
+    __shared__ uint64_t redu[32];
+    __shared__ int bad;
+    const int j = blockIdx.x;
+    const size_t base = (size_t)j * N;
+    const int tid = threadIdx.x;
+    if (tid == 0) bad = 0;
+
+    // ---- weights ----
+    double wmax;
+    if (a.mode == 2) {
+        double m = 0.0;
+        for (int n = tid; n < N; n += blockDim.x) {
+            const double w = a.w[base + n];
+            ws[n] = w;
+            if (w > m) m = w;
+        }
+        wmax = block_max(m, redd);
+    } else {
+        const double dphi = a.mode == 0 ? a.ctl->dphi : 0.0;
+        double m = -INFINITY;
+        for (int n = tid; n < N; n += blockDim.x) {
+            double lw;
+            if (a.mode == 0) {
+                const double l = a.ll[base + n];
+                lw = l == -INFINITY ? -INFINITY : dphi * l;
+            } else {
+                lw = a.logw[base + n];
+            }
+            if (isnan(lw)) lw = -INFINITY;
+            ws[n] = lw;
+            if (lw > m) m = lw;
+        }
+        const double lmax = block_max(m, redd);
+        double s1 = 0.0, s2 = 0.0;
+        for (int n = tid; n < N; n += blockDim.x) {
+            const double w = lmax == -INFINITY ? 0.0 : exp(ws[n] - lmax);
+            ws[n] = w;
+            s1 += w;
+            s2 += w * w;
+        }
+        s1 = block_sum(s1, redd);
+        s2 = block_sum(s2, redd);
+        if (tid == 0) {
+            const double lwj = lmax + log(s1 / (double)N);
+            a.lw[j] = lwj;
+            a.a[j] += lwj;
+            a.gstat[3 * j + 0] = lmax;
+            a.gstat[3 * j + 1] = s1;
+            a.gstat[3 * j + 2] = s2;
+        }
+        wmax = lmax == -INFINITY ? 0.0 : 1.0;
+    }
+    if (!(wmax > 0.0) || !isfinite(wmax)) {
+        if (tid == 0) raise_error(a.err, kErrDegenerate);
+        for (int n = tid; n < N; n += blockDim.x) a.idx[base + n] = n;
+        return;
+    }
+
+    // ---- quantise: q_n = floor(2^32 w_n / max w) ----
+    const int per = (N + blockDim.x - 1) / blockDim.x;
+    const int n0 = min(N, tid * per), n1 = min(N, n0 + per);
+    __syncthreads();
+    uint64_t qloc = 0;
+    for (int n = n0; n < n1; ++n) {
+        const double w = ws[n];
+        const double wn = w > 0.0 ? w / wmax : 0.0;
+        const uint64_t q = (uint64_t)floor(ldexp(wn, 32));
+        qs[n] = q;
+        qloc += q;
+    }
+    const uint64_t Q = block_sum<uint64_t>(qloc, redu);
+    if (Q == 0) {
+        if (tid == 0) raise_error(a.err, kErrDegenerate);
+        for (int n = tid; n < N; n += blockDim.x) a.idx[base + n] = n;
+        return;
+    }
+    // ---- deterministic counts and residuals ----
+    uint64_t placed = 0, rloc = 0;
+    for (int n = n0; n < n1; ++n) {
+        const uint64_t q = qs[n];
+        uint64_t c = 0, r = q;
+        if (a.resid) {
+            c = ((uint64_t)N * q) / Q;                 // floor(N w~_n)
+            r = (uint64_t)N * q - Q * c;
+        }
+        cnt[n] = (uint32_t)c;
+        qs[n] = r;
+        placed += c;
+        rloc += r;
+    }
+    const uint64_t M = (uint64_t)N - block_sum<uint64_t>(placed, redu);
+    // inclusive prefix of the residuals
+    const uint64_t incl = block_inclusive_scan_u64(rloc, redu);
+    uint64_t run = incl - rloc;
+    for (int n = n0; n < n1; ++n) {
+        run += qs[n];
+        qs[n] = run;
+    }
+    __syncthreads();
+    const uint64_t R = qs[N - 1];
+    // ---- residual draws ----
+    for (uint64_t m = tid; m < M; m += blockDim.x) {
+        const U64x4 x = philox4x64_10((uint64_t)j, m, a.cycle, (uint64_t)kTagResample << 32, a.seed, 0);
+        const uint64_t u = __umul64hi(x.v0, R);
+        const int n = upper_bound_u64(qs, N, u);
+        atomicAdd(&cnt[n], 1u);
+    }
+    __syncthreads();
+    // ---- expand counts into indices ----
+    uint64_t cl = 0;
+    for (int n = n0; n < n1; ++n) cl += cnt[n];
+    const uint64_t cincl = block_inclusive_scan_u64(cl, redu);
+    uint64_t off = cincl - cl;
+    for (int n = n0; n < n1; ++n) {
+        const uint32_t c = cnt[n];
+        for (uint32_t k = 0; k < c; ++k) {
+            if (off < (uint64_t)N) a.idx[base + off] = n;
+            else bad = 1;
+            ++off;
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && bad) raise_error(a.err, kErrBounds);
+}
+
+cudaError_t launch_select(const SelectArgs& a, cudaStream_t s)
+{
+    const size_t sm = select_smem(a.N);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)select_smem(kMaxN));
+        attr = true;
+    }
+    k_select<<<a.J, kSelThreads, sm, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void k_gather(GatherArgs a)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.P) return;
+    const int j = s / a.N;
+    const int src = j * a.N + a.idx[s];
+    for (int r = 0; r < a.nrows; ++r) a.dst[r][s] = a.src[r][src];
+}
+
+cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s)
+{
+    k_gather<<<(a.P + 255) / 256, 256, 0, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Pooled RSS at the chosen power from per-group (max, sum, sum of squares),
+// log wtilde += log(J^-1 sum_j wbar_j(l-1)), and phi += dphi.
+__global__ void k_cycle_close(const double* gstat, const double* lw, int J, int N, int power, Ctl* ctl)
+{
+    if (threadIdx.x != 0) return;
+    double M = -INFINITY;
+    for (int j = 0; j < J; ++j) M = fmax(M, gstat[3 * j]);
+    double s1 = 0.0, s2 = 0.0;
+    for (int j = 0; j < J; ++j) {
+        if (gstat[3 * j] == -INFINITY) continue;
+        const double e = exp(gstat[3 * j] - M);
+        s1 += gstat[3 * j + 1] * e;
+        s2 += gstat[3 * j + 2] * e * e;
+    }
+    ctl->rss = s1 * s1 / ((double)J * (double)N * s2);
+    double lm = -INFINITY;
+    for (int j = 0; j < J; ++j) lm = fmax(lm, lw[j]);
+    double s = 0.0;
+    for (int j = 0; j < J; ++j) s += exp(lw[j] - lm);
+    ctl->ltilde += lm + log(s / (double)J);
+    if (power) ctl->phi = ctl->last ? 1.0 : ctl->phi + ctl->dphi;
+    ctl->acc_sum = 0.0;
+    ctl->acc_n = 0;
+}
+
+cudaError_t launch_cycle_close(const double* gstat, const double* lw, int J, int N, int power,
+                               Ctl* ctl, cudaStream_t s)
+{
+    k_cycle_close<<<1, 32, 0, s>>>(gstat, lw, J, N, power, ctl);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ===================================================== moments and estimators
+// Test functions of Section 5.2 at the end state (v_kt, eps_t).
+template <typename Real, int K, int I>
+__global__ void k_testfn(ModelDev m, const double* __restrict__ theta, const double* __restrict__ state,
+                         int P, double* g)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const size_t Ps = (size_t)P;
+    double th[kMaxD];
+    for (int i = 0; i < m.d; ++i) th[i] = theta[i * Ps + p];
+    Real full[kMaxD];
+    full_theta<Real>(m, th, full);
+    EgarchParams<Real, K, I> q;
+    egarch_transform<Real, K, I>(full, m.gamma, q);
+    const Real eps = (Real)state[K * Ps + p];
+    Real vs = 0, vn = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const Real v = (Real)state[k * Ps + p];
+        vs += v;
+        vn += q.alpha[k] * v + q.beta[k] * (fabs(eps) - (Real)kSqrt2OverPi) + q.gamma[k] * eps;
+    }
+    const Real g1 = q.log_sigma_y + vs / Real(2);
+    Real g2 = 0;
+#pragma unroll
+    for (int i = 0; i < I; ++i) g2 += q.p[i] * (q.mu[i] * q.mu[i] * q.mu[i] + Real(3) * q.mu[i] * q.sig[i] * q.sig[i]);
+    const Real hn = exp(q.log_sigma_y + vn / Real(2));
+    const Real x = (Real(-0.03) - q.mu_y) / hn;
+    Real g3 = 0;
+#pragma unroll
+    for (int i = 0; i < I; ++i) g3 += q.p[i] * Real(0.5) * erfc(-((x - q.mu[i]) / q.sig[i]) * (Real)0.70710678118654752440);
+    g[0 * Ps + p] = (double)g1;
+    g[1 * Ps + p] = (double)g2;
+    g[2 * Ps + p] = (double)g3;
+}
+
+template <typename Real, int K>
+static void testfn_k(const ModelDev& m, const double* th, const double* st, int P, double* g, cudaStream_t s)
+{
+    const int G = (P + 255) / 256;
+    switch (m.I) {
+    case 1: k_testfn<Real, K, 1><<<G, 256, 0, s>>>(m, th, st, P, g); break;
+    case 2: k_testfn<Real, K, 2><<<G, 256, 0, s>>>(m, th, st, P, g); break;
+    case 3: k_testfn<Real, K, 3><<<G, 256, 0, s>>>(m, th, st, P, g); break;
+    default: k_testfn<Real, K, 4><<<G, 256, 0, s>>>(m, th, st, P, g); break;
+    }
+}
+
+template <typename Real>
+static void testfn_real(const ModelDev& m, const double* th, const double* st, int P, double* g, cudaStream_t s)
+{
+    switch (m.K) {
+    case 1: testfn_k<Real, 1>(m, th, st, P, g, s); break;
+    case 2: testfn_k<Real, 2>(m, th, st, P, g, s); break;
+    case 3: testfn_k<Real, 3>(m, th, st, P, g, s); break;
+    default: testfn_k<Real, 4>(m, th, st, P, g, s); break;
+    }
+}
+
+cudaError_t launch_testfn(const ModelDev& m, int precision, const double* theta,
+                          const double* state, int P, double* g, cudaStream_t s)
+{
+    if (precision == 1) testfn_real<float>(m, theta, state, P, g, s);
+    else testfn_real<double>(m, theta, state, P, g, s);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Per group and function: mean and centred sum of squares (two passes in the
+// block), combined across groups with the parallel formula
+//   sum_jn (g - gbar)^2 = sum_j [M2_j + N (gbar_j - gbar)^2].
+__global__ void k_group_moments(const double* __restrict__ g, int nf, int N, int P, double* part)
+{
+    __shared__ double red[32];
+    const int j = blockIdx.x, f = blockIdx.y;
+    const double* row = g + (size_t)f * P + (size_t)j * N;
+    double s = 0.0;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) s += row[n];
+    const double mean = block_sum(s, red) / (double)N;
+    double q = 0.0;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const double e = row[n] - mean;
+        q += e * e;
+    }
+    q = block_sum(q, red);
+    if (threadIdx.x == 0) {
+        part[((size_t)f * gridDim.x + j) * 2 + 0] = mean;
+        part[((size_t)f * gridDim.x + j) * 2 + 1] = q;
+    }
+}
+
+__global__ void k_moments_final(const double* part, int nf, int J, int N, double* out, Ctl* ctl,
+                                int rne_from)
+{
+    __shared__ double rne_s[64];
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+        const double* pf = part + (size_t)f * J * 2;
+        double gbar = 0.0;
+        for (int j = 0; j < J; ++j) gbar += pf[2 * j];
+        gbar /= (double)J;                                   // (garnd_approx)
+        double between = 0.0, within = 0.0;
+        for (int j = 0; j < J; ++j) {
+            const double e = pf[2 * j] - gbar;
+            between += e * e;
+            within += pf[2 * j + 1];
+        }
+        const double total = within + (double)N * between;
+        const double var_hat = total / ((double)N * J - 1.0);
+        const double v_hat = (double)N / (J - 1.0) * between;    // (vhat)
+        out[4 * f + 0] = gbar;
+        out[4 * f + 1] = sqrt(var_hat);
+        out[4 * f + 2] = sqrt(between / ((double)J * (J - 1.0)));  // (NSE_def)
+        out[4 * f + 3] = v_hat > 0.0 ? var_hat / v_hat : INFINITY;
+        if (f < 64) rne_s[f] = out[4 * f + 3];
+    }
+    __syncthreads();
+    if (ctl && threadIdx.x == 0) {
+        double s = 0.0;
+        int n = 0;
+        for (int f = rne_from; f < nf && f < 64; ++f) {
+            s += rne_s[f];
+            ++n;
+        }
+        ctl->mean_rne = n ? s / n : 0.0;
+    }
+}
+
+cudaError_t launch_moments(const double* g, int nf, int J, int N, double* part, double* out,
+                           Ctl* ctl, int rne_from, cudaStream_t s)
+{
+    dim3 grid(J, nf);
+    k_group_moments<<<grid, 256, 0, s>>>(g, nf, N, J * N, part);
+    count_launch();
+    k_moments_final<<<1, 64, 0, s>>>(part, nf, J, N, out, ctl, rne_from);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// log wbar = log J^-1 sum_j exp(a_j); NSE of log wbar from (ML_se):
+// [J (J-1)]^-1 sum_j (wbar_j - wbar)^2 / wbar^2, all scaled by exp(max a).
+__global__ void k_ml(const double* a, int J, const Ctl* ctl, double* out)
+{
+    if (threadIdx.x != 0) return;
+    double amax = -INFINITY;
+    for (int j = 0; j < J; ++j) amax = fmax(amax, a[j]);
+    double rbar = 0.0;
+    for (int j = 0; j < J; ++j) rbar += exp(a[j] - amax);
+    rbar /= (double)J;
+    double ss = 0.0;
+    for (int j = 0; j < J; ++j) {
+        const double r = exp(a[j] - amax) - rbar;
+        ss += r * r;
+    }
+    out[0] = amax + log(rbar);
+    out[1] = sqrt(ss / ((double)J * (J - 1.0))) / rbar;
+    out[2] = ctl ? ctl->ltilde : 0.0;
+}
+
+cudaError_t launch_ml(const double* a, int J, const Ctl* ctl, double* out, cudaStream_t s)
+{
+    k_ml<<<1, 32, 0, s>>>(a, J, ctl, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace smc

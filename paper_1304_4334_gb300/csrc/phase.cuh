@@ -1,0 +1,89 @@
+// C, S and estimator kernels around the M phase, and the device-resident
+// control block that lets a whole cycle run without host round trips between
+// its kernels.
+#pragma once
+
+#include "recursion.cuh"
+
+namespace smc {
+
+// Device-resident control state of a run.
+struct Ctl {
+    // M phase: step size in tenths (Section 3.3) and acceptance bookkeeping.
+    int h_tenths;
+    int pending;                    // an acceptance count awaits its h update
+    unsigned long long acc_count;   // accepted proposals of the pending iteration
+    double acc_sum;                 // sum of acceptance rates in this cycle
+    int acc_n;                      // iterations in this cycle
+    // C phase, power tempering: k-ary search state.
+    double llmax, lo, hi, dphi, rss, phi;
+    int pass, done, last;
+    // RNE stopping rule.
+    double mean_rne;
+    // Estimators (Section 4.2): log wtilde accumulates log of J^-1 sum_j wbar_j(l-1).
+    double ltilde;
+    int err;
+};
+
+// ---- launchers (phase.cu) ----
+int device_sm_count();
+
+// Covariance: partial sums per block, then a single block that combines them,
+// applies the pending step-size update and factors h^2 V.
+int cov_grid(int P);
+cudaError_t launch_cov(const double* theta, int d, int P, double* part, int G, Ctl* ctl,
+                       int fixed_h_tenths, double acc_target, int hmin, int hmax, double* mean,
+                       double* cov, double* L, cudaStream_t s);
+// Applies a pending acceptance count to h (end of an M phase).
+cudaError_t launch_adapt_h(Ctl* ctl, int P, double acc_target, int hmin, int hmax, cudaStream_t s);
+
+// Power-tempering search; part sized search_part_len(P) doubles.
+int search_grid(int P);
+size_t search_part_len(int P);
+cudaError_t launch_power_search(const double* ll, int P, double d1, int passes, double* part,
+                                Ctl* ctl, cudaStream_t s);
+
+// S phase: per group weights, log-mean weight (a_j, lw_j), resampling, then gather.
+// mode 0: weights from ctl->dphi * ll; mode 1: from logw; mode 2: w given directly.
+struct SelectArgs {
+    int mode;
+    const double* ll;
+    const double* logw;
+    const double* w;
+    int J, N;
+    int resid;
+    uint64_t seed, cycle;
+    double* a;        // [J] += log wbar_j (modes 0, 1)
+    double* lw;       // [J] log wbar_j of this cycle (modes 0, 1)
+    double* gstat;    // [J][3] (max log w, sum w, sum w^2) of this cycle (modes 0, 1)
+    int32_t* idx;     // [J*N]
+    Ctl* ctl;
+    int* err;
+};
+size_t select_smem(int N);
+cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
+
+struct GatherArgs {
+    const int32_t* idx;
+    int N, P;
+    int nrows;                 // rows of length P to gather
+    const double* const* src;  // device array of nrows row pointers
+    double* const* dst;        // device array of nrows row pointers
+};
+cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
+
+// After the S phase: pooled RSS at the chosen power, log wtilde, phi update.
+cudaError_t launch_cycle_close(const double* gstat, const double* lw, int J, int N, int power,
+                               Ctl* ctl, cudaStream_t s);
+
+// Test functions g1..g3 (Section 5.2) into g[3][P].
+cudaError_t launch_testfn(const ModelDev& m, int precision, const double* theta,
+                          const double* state, int P, double* g, cudaStream_t s);
+// Group moments of nf rows of g ([nf][J*N]) into out[nf][4] (device); optional
+// mean RNE of rows [rne_from, nf) into ctl->mean_rne.
+cudaError_t launch_moments(const double* g, int nf, int J, int N, double* part, double* out,
+                           Ctl* ctl, int rne_from, cudaStream_t s);
+// log ML and NSE from a[J]; out[0..2] = log wbar, NSE, log wtilde (from ctl, if given).
+cudaError_t launch_ml(const double* a, int J, const Ctl* ctl, double* out, cudaStream_t s);
+
+}  // namespace smc

@@ -32,29 +32,32 @@ constexpr double kSfac = 0.84932180028801904272;       // (log2(e) / 2)^1/2
 constexpr double kLog2Sfac = -0.23556494171288733624;  // log2 of kSfac
 constexpr double kLogSfac = -0.16328232405373808766;   // ln of kSfac
 
-// Device view of a model (see smc.h for the host-side description).
+// Device view of a model, passed by value in kernel parameters so that every
+// thread reads it through the uniform constant path.
 struct ModelDev {
     int kind;        // 0 EGARCH, 1 LINREG
     int K, I, gamma, eps0_zero;
     int p;           // LINREG regressors
     double sigma;    // LINREG disturbance s.d.
     int d_full, d;
-    const int* free_idx;        // [d] or null (all parameters free)
-    const double* theta_fixed;  // [d_full] or null
-    const double* prior_mean;   // [d]
-    const double* prior_sd;     // [d]
-    const double* prior_lo;     // [d]
+    int has_free;    // 0: all d_full parameters free
+    int free_idx[kMaxD];
+    double theta_fixed[kMaxD];
+    double prior_mean[kMaxD];
+    double prior_isd[kMaxD];   // 1 / prior s.d.
+    double prior_c[kMaxD];     // -1/2 log 2pi - log prior s.d.
+    double prior_lo[kMaxD];
 };
 
 // Full parameter vector from a particle's free parameters.
 template <typename Real>
 __device__ __forceinline__ void full_theta(const ModelDev& m, const double* th, Real* full)
 {
-    if (!m.free_idx) {
+    if (!m.has_free) {
         for (int i = 0; i < m.d_full; ++i) full[i] = (Real)th[i];
         return;
     }
-    for (int i = 0; i < m.d_full; ++i) full[i] = m.theta_fixed ? (Real)m.theta_fixed[i] : Real(0);
+    for (int i = 0; i < m.d_full; ++i) full[i] = (Real)m.theta_fixed[i];
     for (int k = 0; k < m.d; ++k) full[m.free_idx[k]] = (Real)th[k];
 }
 
@@ -65,8 +68,8 @@ __device__ __forceinline__ double log_prior(const ModelDev& m, const double* th)
     for (int k = 0; k < m.d; ++k) {
         const double x = th[k];
         if (!(x >= m.prior_lo[k]) || !isfinite(x)) return -INFINITY;
-        const double z = (x - m.prior_mean[k]) / m.prior_sd[k];
-        lp += -0.5 * kLog2Pi - log(m.prior_sd[k]) - 0.5 * z * z;
+        const double z = (x - m.prior_mean[k]) * m.prior_isd[k];
+        lp += m.prior_c[k] - 0.5 * z * z;
     }
     return lp;
 }
