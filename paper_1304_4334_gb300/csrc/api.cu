@@ -37,6 +37,37 @@ SMC_DECL_EGARCH(f64, 3)
 SMC_DECL_EGARCH(f64, 4)
 cudaError_t launch_mutate_linreg(const MutateArgs& a, cudaStream_t s);
 cudaError_t launch_loglik_linreg(const LoglikArgs& a, cudaStream_t s);
+cudaError_t launch_cdata_f32_k1(const CdataArgs& a, cudaStream_t s);
+cudaError_t launch_cdata_f32_k2(const CdataArgs& a, cudaStream_t s);
+cudaError_t launch_cdata_f32_k3(const CdataArgs& a, cudaStream_t s);
+cudaError_t launch_cdata_f32_k4(const CdataArgs& a, cudaStream_t s);
+cudaError_t launch_cdata_f64_k1(const CdataArgs& a, cudaStream_t s);
+cudaError_t launch_cdata_f64_k2(const CdataArgs& a, cudaStream_t s);
+cudaError_t launch_cdata_f64_k3(const CdataArgs& a, cudaStream_t s);
+cudaError_t launch_cdata_f64_k4(const CdataArgs& a, cudaStream_t s);
+cudaError_t launch_cdata_linreg(const CdataArgs& a, cudaStream_t s);
+
+cudaError_t launch_cdata(const CdataArgs& a, int precision, cudaStream_t s)
+{
+    count_launch();
+    if (a.m.kind == SMC_LINREG) return launch_cdata_linreg(a, s);
+    if (precision == SMC_FP32) {
+        switch (a.m.K) {
+        case 1: return launch_cdata_f32_k1(a, s);
+        case 2: return launch_cdata_f32_k2(a, s);
+        case 3: return launch_cdata_f32_k3(a, s);
+        case 4: return launch_cdata_f32_k4(a, s);
+        }
+    } else {
+        switch (a.m.K) {
+        case 1: return launch_cdata_f64_k1(a, s);
+        case 2: return launch_cdata_f64_k2(a, s);
+        case 3: return launch_cdata_f64_k3(a, s);
+        case 4: return launch_cdata_f64_k4(a, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_mutate(const MutateArgs& a, int precision, cudaStream_t s)
 {
@@ -120,11 +151,6 @@ __global__ void k_init_data_tempering(ModelDev m, const double* __restrict__ the
     for (int k = 0; k < ns; ++k) state[k * (size_t)P + p] = 0.0;
 }
 
-__global__ void k_mark_pending(Ctl* ctl)
-{
-    if (threadIdx.x == 0) ctl->pending = 1;
-}
-
 }  // namespace smc
 
 using namespace smc;
@@ -155,6 +181,7 @@ struct smc_ctx {
     double* cov_part = nullptr;
     int cov_G = 0;
     double* search_part = nullptr;
+    double* cd_part = nullptr;       // [G][kCdataChunk][3] data-tempering statistics
     double* mom_part = nullptr;      // [nf][J][2]
     double* mom_out = nullptr;       // [nf][4]
     double* ml_out = nullptr;        // [3]
@@ -355,7 +382,7 @@ static void release(smc_ctx* c)
     if (!c) return;
     void* ptrs[] = {c->obs, c->theta[0], c->theta[1], c->ll[0], c->ll[1], c->lp[0], c->lp[1],
                     c->state[0], c->state[1], c->thp, c->logw, c->g, c->a, c->lw, c->gstat,
-                    c->idx, c->cov_part, c->search_part, c->mom_part, c->mom_out, c->ml_out,
+                    c->idx, c->cov_part, c->search_part, c->cd_part, c->mom_part, c->mom_out, c->ml_out,
                     c->L, c->gather_ptrs, c->ctl};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -441,6 +468,7 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
     a.cycle = (uint64_t)ctx->cycle;
     a.iter = (uint64_t)r;
     a.acc_count = &ctx->ctl->acc_count;
+    a.pending = &ctx->ctl->pending;
     a.err = &ctx->ctl->err;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ctx->profile) {
@@ -454,8 +482,6 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
         ctx->ev_pending.push_back({e0, e1});
         ctx->mutate_launches += 1;
     }
-    k_mark_pending<<<1, 32, 0, ctx->stream>>>(ctx->ctl);
-    count_launch();
     return SMC_OK;
 }
 
@@ -607,8 +633,9 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
     CU(dalloc(&ctx->gstat, (size_t)J * 3));
     CU(dalloc(&ctx->idx, Ps));
     ctx->cov_G = cov_grid(P);
-    CU(dalloc(&ctx->cov_part, (size_t)ctx->cov_G * (d + d * (d + 1) / 2)));
+    CU(dalloc(&ctx->cov_part, (size_t)(ctx->cov_G + 1) * (d + d * (d + 1) / 2)));
     CU(dalloc(&ctx->search_part, search_part_len(P)));
+    CU(dalloc(&ctx->cd_part, (size_t)((P + kMutThreads - 1) / kMutThreads) * kCdataChunk * 3));
     const int nf_max = d + 3;
     CU(dalloc(&ctx->mom_part, (size_t)nf_max * J * 2));
     CU(dalloc(&ctx->mom_out, (size_t)nf_max * 4));
@@ -774,7 +801,48 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
         rss = ctx->ctl_host->rss;
         forced = ctx->ctl_host->last;
     } else {
-        return set_err(ctx, SMC_EINVAL, "data tempering is not built in this version");
+        // ---- C phase: add observations until RSS < D1 (Algorithm 1, 2(a)) ----
+        CU(cudaMemsetAsync(ctx->logw, 0, (size_t)P * sizeof(double), ctx->stream));
+        ForceDates fd;
+        std::memset(&fd, 0, sizeof fd);
+        fd.n = c.n_force;
+        for (int i = 0; i < c.n_force; ++i) fd.t[i] = c.force_dates[i];
+        const int G = (P + kMutThreads - 1) / kMutThreads;
+        int s0 = ctx->t_prev;
+        for (;;) {
+            CdataArgs ca;
+            ca.m = ctx->mdev;
+            ca.obs = ctx->obs;
+            ca.T = ctx->T;
+            ca.W = ctx->W;
+            ca.theta = ctx->theta[ctx->cur];
+            ca.state = ctx->state[ctx->cur];
+            ca.ll = ctx->ll[ctx->cur];
+            ca.logw = ctx->logw;
+            ca.P = P;
+            ca.ns = ctx->ns;
+            ca.s0 = s0;
+            ca.B = ctx->T - s0 < kCdataChunk ? ctx->T - s0 : kCdataChunk;
+            ca.part = ctx->cd_part;
+            ca.stop = &ctx->ctl->cd_stop;
+            ca.commit = 0;
+            CU(launch_cdata(ca, c.precision, ctx->stream));
+            CU(launch_cdata_select(ctx->cd_part, G, ca.B, s0, ctx->T, P, c.d1, fd, ctx->ctl, ctx->stream));
+            ca.commit = 1;
+            CU(launch_cdata(ca, c.precision, ctx->stream));
+            st = sync_ctl(ctx);
+            if (st != SMC_OK) return st;
+            s0 += ctx->ctl_host->cd_stop;
+            if (ctx->ctl_host->cd_found) break;
+        }
+        t_l = s0;
+        rss = ctx->ctl_host->rss;
+        forced = ctx->ctl_host->cd_forced || t_l == ctx->T;
+        // ---- S phase (weights from the accumulated log weights) ----
+        st = s_phase(ctx, 1);
+        if (st != SMC_OK) return st;
+        CU(launch_cycle_close(ctx->gstat, ctx->lw, c.J, c.N, 0, ctx->ctl, ctx->stream));
+        ctx->phi = 1.0;
     }
     // ---- M phase ----
     const double phim = c.tempering == SMC_POWER ? ctx->phi : 1.0;

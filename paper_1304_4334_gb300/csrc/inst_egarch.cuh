@@ -36,6 +36,20 @@ cudaError_t launch_loglik_k(const LoglikArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <template <int, int> class Pol, int K>
+cudaError_t launch_cdata_k(const CdataArgs& a, cudaStream_t s)
+{
+    const int g = mutate_grid(a.P);
+    switch (a.m.I) {
+    case 1: k_cdata<Pol<K, 1>><<<g, kMutThreads, 0, s>>>(a); break;
+    case 2: k_cdata<Pol<K, 2>><<<g, kMutThreads, 0, s>>>(a); break;
+    case 3: k_cdata<Pol<K, 3>><<<g, kMutThreads, 0, s>>>(a); break;
+    case 4: k_cdata<Pol<K, 4>><<<g, kMutThreads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace smc
 
 #define SMC_INSTANTIATE_EGARCH(TAG, POL, K)                                                     \
@@ -47,5 +61,9 @@ cudaError_t launch_loglik_k(const LoglikArgs& a, cudaStream_t s)
     cudaError_t launch_loglik_##TAG##_k##K(const LoglikArgs& a, cudaStream_t s)                 \
     {                                                                                           \
         return launch_loglik_k<POL, K>(a, s);                                                   \
+    }                                                                                           \
+    cudaError_t launch_cdata_##TAG##_k##K(const CdataArgs& a, cudaStream_t s)                   \
+    {                                                                                           \
+        return launch_cdata_k<POL, K>(a, s);                                                    \
     }                                                                                           \
     }

@@ -15,4 +15,10 @@ cudaError_t launch_loglik_linreg(const LoglikArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_cdata_linreg(const CdataArgs& a, cudaStream_t s)
+{
+    k_cdata<PolicyLinreg><<<mutate_grid(a.P), kMutThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace smc

@@ -30,6 +30,7 @@ struct MutateArgs {
     double phi;
     uint64_t seed, cycle, iter;
     unsigned long long* acc_count;   // += accepted proposals
+    int* pending;                    // set to 1 (nullable): an acceptance count awaits its h update
     int* err;
 };
 
@@ -60,6 +61,12 @@ struct PolicyEgarchF32 {
     }
     __device__ static bool run(Model& mdl, ObsPipe<Obs, kChunk>& pipe, int T, int) { return run_egarch_f32(mdl, pipe, T); }
     __device__ static void state_out(const Model& mdl, double* st) { mdl.state_out(st); }
+    __device__ static void load_state(Model& mdl, const double* st) { mdl.load_state(st); }
+    __device__ static double logdens(Model& mdl, const Obs* obs, int s, int)
+    {
+        const Obs y = obs[s - 1];
+        return s == 1 ? mdl.template logdens<true>(y) : mdl.template logdens<false>(y);
+    }
 };
 
 template <int K, int I>
@@ -75,6 +82,12 @@ struct PolicyEgarchF64 {
     }
     __device__ static bool run(Model& mdl, ObsPipe<Obs, kChunk>& pipe, int T, int) { return run_egarch_f64(mdl, pipe, T); }
     __device__ static void state_out(const Model& mdl, double* st) { mdl.state_out(st); }
+    __device__ static void load_state(Model& mdl, const double* st) { mdl.load_state(st); }
+    __device__ static double logdens(Model& mdl, const Obs* obs, int s, int)
+    {
+        const Obs y = obs[s - 1];
+        return s == 1 ? mdl.template logdens<true>(y) : mdl.template logdens<false>(y);
+    }
 };
 
 struct PolicyLinreg {
@@ -89,6 +102,11 @@ struct PolicyLinreg {
     }
     __device__ static bool run(Model& mdl, ObsPipe<Obs, kChunk>& pipe, int T, int W) { return run_linreg(mdl, pipe, T, W); }
     __device__ static void state_out(const Model&, double*) {}
+    __device__ static void load_state(Model&, const double*) {}
+    __device__ static double logdens(Model& mdl, const Obs* obs, int s, int W)
+    {
+        return mdl.logdens(obs + (size_t)(s - 1) * W);
+    }
 };
 
 __device__ __forceinline__ double tempered_target(double lp, double ll, double phi)
@@ -166,6 +184,7 @@ __global__ void __launch_bounds__(kMutThreads) k_mutate(MutateArgs a)
     if ((threadIdx.x & 31) == 0 && nacc) atomicAdd(&acc_s, nacc);
     __syncthreads();
     if (threadIdx.x == 0 && acc_s) atomicAdd(a.acc_count, (unsigned long long)acc_s);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.pending) *a.pending = 1;
 }
 
 template <class Pol>
@@ -210,8 +229,109 @@ __global__ void __launch_bounds__(kMutThreads) k_loglik(LoglikArgs a)
     }
 }
 
+// ------------------------------------------------- data-tempering C phase
+// Algorithm 1, step 2(a): w_jn(s) = w_jn(s-1) p(y_s | y_1:s-1, theta_jn) for
+// s = t_l-1 + 1, ..., stopping at the first s with RSS(s) < D1 (Section 3.3),
+// at a date of interest, or at T.  The search runs speculatively over a chunk
+// of up to kCdataChunk observations: each block reduces, for every s of the
+// chunk, (max log w, sum w, sum w^2) over its particles; a one-warp kernel
+// combines the blocks and finds the stopping observation; a commit pass then
+// advances every particle's recursion state, log likelihood and log weight to
+// it.  The RSS statistic uses FP32 exponentials of log-weight differences; the
+// log weights themselves are FP64.
+constexpr int kCdataChunk = 32;
+
+struct CdataArgs {
+    ModelDev m;
+    const void* obs;
+    int T, W;
+    const double* theta;   // [d][P]
+    double* state;         // [ns][P] recursion state at s0 (updated by the commit pass)
+    double* ll;            // [P] log likelihood of y_1:s0 (updated by the commit pass)
+    double* logw;          // [P] log weight since the cycle start (updated by the commit pass)
+    int P, ns;
+    int s0;                // observations already absorbed
+    int B;                 // observations in this chunk (<= kCdataChunk, s0 + B <= T)
+    double* part;          // [gridDim][B][3] statistics pass output
+    const int* stop;       // commit pass: observations to absorb (device)
+    int commit;
+};
+
+template <class Pol>
+__global__ void __launch_bounds__(kMutThreads) k_cdata(CdataArgs a)
+{
+    using Real = typename Pol::Real;
+    using Obs = typename Pol::Obs;
+    __shared__ double trip[kMutThreads / 32][kCdataChunk][3];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = p < a.P;
+    const int pp = active ? p : a.P - 1;
+    const size_t P = (size_t)a.P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double th[kMaxD];
+    for (int i = 0; i < a.m.d; ++i) th[i] = a.theta[i * P + pp];
+    typename Pol::Model mdl;
+    {
+        Real full[kMaxD];
+        full_theta<Real>(a.m, th, full);
+        Pol::setup(mdl, a.m, full);
+    }
+    double st[kMaxState];
+    for (int k = 0; k < Pol::kNs; ++k) st[k] = a.state[k * P + pp];
+    if (a.s0 > 0) Pol::load_state(mdl, st);
+    double lw = a.logw[pp];
+    const Obs* obs = (const Obs*)a.obs;
+    if (a.commit) {
+        const int n = *a.stop;
+        double add = 0.0;
+        for (int q = 0; q < n; ++q) add += Pol::logdens(mdl, obs, a.s0 + q + 1, a.W);
+        if (isnan(add)) add = -INFINITY;
+        if (active) {
+            a.ll[p] += add;
+            a.logw[p] = lw + add;
+            if (Pol::kNs) {
+                Pol::state_out(mdl, st);
+                for (int k = 0; k < Pol::kNs; ++k) a.state[k * P + p] = st[k];
+            }
+        }
+        return;
+    }
+    for (int q = 0; q < a.B; ++q) {
+        double l = Pol::logdens(mdl, obs, a.s0 + q + 1, a.W);
+        lw += isnan(l) ? -INFINITY : l;
+        const double x = active ? lw : -INFINITY;
+        const double mw = warp_max(x);
+        float w = 0.0f;
+        if (x != -INFINITY && mw != -INFINITY) w = ex2_approx((float)((x - mw) * kLog2e));
+        const float s1 = warp_sum(w);
+        const float s2 = warp_sum(w * w);
+        if (lane == 0) {
+            trip[warp][q][0] = mw;
+            trip[warp][q][1] = s1;
+            trip[warp][q][2] = s2;
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < a.B; q += blockDim.x) {
+        double M = -INFINITY;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = fmax(M, trip[w][q][0]);
+        double S1 = 0.0, S2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (trip[w][q][0] == -INFINITY) continue;
+            const double e = exp(trip[w][q][0] - M);
+            S1 += trip[w][q][1] * e;
+            S2 += trip[w][q][2] * e * e;
+        }
+        double* o = a.part + ((size_t)blockIdx.x * a.B + q) * 3;
+        o[0] = M;
+        o[1] = S1;
+        o[2] = S2;
+    }
+}
+
 // Host-side launchers (defined in the instantiation units).
 cudaError_t launch_mutate(const MutateArgs& a, int precision, cudaStream_t s);
 cudaError_t launch_loglik(const LoglikArgs& a, int precision, cudaStream_t s);
+cudaError_t launch_cdata(const CdataArgs& a, int precision, cudaStream_t s);
 
 }  // namespace smc

@@ -23,6 +23,10 @@ int device_sm_count()
 // V_lr of Section 3.3 is the sample variance of the current particles, pooled
 // over all J N.  Sums are taken about a shift (particle 0) so that the final
 // combination does not cancel: V = [S2 - S1 S1'/P] / (P - 1) on shifted data.
+// Within a tile of 64 particles the shifted values and their products are
+// summed in FP32 (the FP64 pipe of this part is 1/64 of its FP32 rate); tiles
+// and blocks are combined in FP64.  V only scales the random-walk proposal, so
+// its ~1e-6 relative accuracy leaves the Metropolis kernel exact.
 constexpr int kCovThreads = 256;
 constexpr int kCovTile = 64;
 constexpr int kCovMaxAcc = (kMaxD + kMaxD * (kMaxD + 1) / 2 + kCovThreads - 1) / kCovThreads;
@@ -47,7 +51,7 @@ __device__ __forceinline__ void unpack_pair(int e, int& i, int& k)
 __global__ void __launch_bounds__(kCovThreads) k_cov_partial(const double* __restrict__ theta, int d,
                                                             int P, double* __restrict__ part)
 {
-    __shared__ double tile[kMaxD][kCovTile + 1];
+    __shared__ float tile[kMaxD][kCovTile + 1];
     __shared__ double shift[kMaxD];
     __shared__ int pi_[kMaxD * (kMaxD + 1) / 2], pk_[kMaxD * (kMaxD + 1) / 2];
     const int npair = d * (d + 1) / 2;
@@ -66,21 +70,21 @@ __global__ void __launch_bounds__(kCovThreads) k_cov_partial(const double* __res
         const int cnt = min(kCovTile, n1 - base);
         for (int e = threadIdx.x; e < d * kCovTile; e += blockDim.x) {
             const int i = e / kCovTile, n = e % kCovTile;
-            tile[i][n] = n < cnt ? theta[i * Ps + base + n] - shift[i] : 0.0;
+            tile[i][n] = n < cnt ? (float)(theta[i * Ps + base + n] - shift[i]) : 0.0f;
         }
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < kCovMaxAcc; ++r) {
             const int e = threadIdx.x + r * blockDim.x;
             if (e < d) {
-                double s = 0.0;
+                float s = 0.0f;
                 for (int n = 0; n < cnt; ++n) s += tile[e][n];
-                acc[r] += s;
+                acc[r] += (double)s;
             } else if (e < nacc) {
                 const int i = pi_[e - d], k = pk_[e - d];
-                double s = 0.0;
-                for (int n = 0; n < cnt; ++n) s = fma(tile[i][n], tile[k][n], s);
-                acc[r] += s;
+                float s = 0.0f;
+                for (int n = 0; n < cnt; ++n) s = fmaf(tile[i][n], tile[k][n], s);
+                acc[r] += (double)s;
             }
         }
         __syncthreads();
@@ -111,6 +115,18 @@ __global__ void k_adapt_h(Ctl* ctl, int P, double target, int hmin, int hmax)
     if (threadIdx.x == 0 && blockIdx.x == 0) apply_h_update(ctl, P, target, hmin, hmax);
 }
 
+// Sum of the G block partials of each accumulator entry: one block per entry,
+// fixed combination order.  Result in part[G * nacc + e].
+__global__ void __launch_bounds__(128) k_cov_combine(double* part, int G, int nacc)
+{
+    __shared__ double red[32];
+    const int e = blockIdx.x;
+    double s = 0.0;
+    for (int g = threadIdx.x; g < G; g += blockDim.x) s += part[(size_t)g * nacc + e];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part[(size_t)G * nacc + e] = s;
+}
+
 // Combines the partial sums, updates h from the previous iteration's
 // acceptance (when a control block is given) and factors Sigma = h^2 V by a
 // right-looking Cholesky in shared memory; a non-positive pivot zeroes its
@@ -137,17 +153,13 @@ __global__ void __launch_bounds__(kCovThreads) k_cov_final(const double* __restr
         hh = (h / 10.0) * (h / 10.0);
     }
     for (int i = threadIdx.x; i < d; i += blockDim.x) shift[i] = theta[i * Ps];
-    for (int e = threadIdx.x; e < d; e += blockDim.x) {
-        double s = 0.0;
-        for (int g = 0; g < G; ++g) s += part[(size_t)g * nacc + e];
-        S1[e] = s;
-    }
+    const double* tot = part + (size_t)G * nacc;
+    for (int e = threadIdx.x; e < d; e += blockDim.x) S1[e] = tot[e];
     __syncthreads();
     for (int e = threadIdx.x; e < npair; e += blockDim.x) {
         int i, k;
         unpack_pair(e, i, k);
-        double s = 0.0;
-        for (int g = 0; g < G; ++g) s += part[(size_t)g * nacc + d + e];
+        const double s = tot[d + e];
         const double c = (s - S1[i] * S1[k] / (double)P) / (double)(P - 1);
         A[i][k] = c;
         A[k][i] = c;
@@ -190,6 +202,9 @@ cudaError_t launch_cov(const double* theta, int d, int P, double* part, int G, C
                        double* cov, double* L, cudaStream_t s)
 {
     k_cov_partial<<<G, kCovThreads, 0, s>>>(theta, d, P, part);
+    count_launch();
+    const int nacc = d + d * (d + 1) / 2;
+    k_cov_combine<<<nacc, 128, 0, s>>>(part, G, nacc);
     count_launch();
     k_cov_final<<<1, kCovThreads, 0, s>>>(part, G, d, P, theta, ctl, fixed_h_tenths, acc_target,
                                           hmin, hmax, mean, cov, L);
@@ -298,15 +313,28 @@ __global__ void __launch_bounds__(kSearchThreads) k_power_pass(const double* __r
     }
 }
 
-__global__ void k_power_select(const double* part, int G, int P, double d1, int passes, Ctl* ctl)
+__global__ void __launch_bounds__(1024) k_power_select(const double* part, int G, int P, double d1,
+                                                      int passes, Ctl* ctl)
 {
     if (ctl->done) return;
-    const int lane = threadIdx.x;
+    __shared__ double r1[32][kCand + 1], r2[32][kCand + 1];
+    const int c = threadIdx.x & 31, w = threadIdx.x >> 5;
     double t1 = 0.0, t2 = 0.0;
-    for (int g = 0; g < G; ++g) {
-        t1 += part[((size_t)g * kCand + lane) * 2 + 0];
-        t2 += part[((size_t)g * kCand + lane) * 2 + 1];
+    for (int g = w; g < G; g += 32) {
+        t1 += part[((size_t)g * kCand + c) * 2 + 0];
+        t2 += part[((size_t)g * kCand + c) * 2 + 1];
     }
+    r1[w][c] = t1;
+    r2[w][c] = t2;
+    __syncthreads();
+    if (w != 0) return;
+    t1 = 0.0;
+    t2 = 0.0;
+    for (int k = 0; k < 32; ++k) {
+        t1 += r1[k][c];
+        t2 += r2[k][c];
+    }
+    const int lane = c;
     const double rss = t1 * t1 / ((double)P * t2);
     const unsigned below = __ballot_sync(0xffffffffu, rss < d1);
     if (lane == 0) {
@@ -319,9 +347,9 @@ __global__ void k_power_select(const double* part, int G, int P, double d1, int 
             ctl->done = 1;
             ctl->last = ctl->pass == 0;
         } else {
-            const int c = __ffs(below) - 1;
-            const double nhi = candidate(lo, hi, c);
-            const double nlo = c == 0 ? lo : candidate(lo, hi, c - 1);
+            const int cc = __ffs(below) - 1;
+            const double nhi = candidate(lo, hi, cc);
+            const double nlo = cc == 0 ? lo : candidate(lo, hi, cc - 1);
             ctl->lo = nlo;
             ctl->hi = nhi;
             ctl->dphi = nhi;
@@ -343,7 +371,7 @@ cudaError_t launch_power_search(const double* ll, int P, double d1, int passes, 
     for (int p = 0; p < passes; ++p) {
         k_power_pass<<<G, kSearchThreads, 0, s>>>(ll, P, ctl, part);
         count_launch();
-        k_power_select<<<1, 32, 0, s>>>(part, G, P, d1, passes, ctl);
+        k_power_select<<<1, 1024, 0, s>>>(part, G, P, d1, passes, ctl);
         count_launch();
     }
     return cudaGetLastError();
@@ -529,6 +557,51 @@ __global__ void k_gather(GatherArgs a)
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s)
 {
     k_gather<<<(a.P + 255) / 256, 256, 0, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+__global__ void k_cdata_select(const double* part, int G, int B, int s0, int T, int P, double d1,
+                               ForceDates fd, Ctl* ctl)
+{
+    const int q = threadIdx.x;
+    double rss = NAN;
+    bool stop = false, forced = false;
+    if (q < B) {
+        double M = -INFINITY;
+        for (int g = 0; g < G; ++g) M = fmax(M, part[((size_t)g * B + q) * 3]);
+        double S1 = 0.0, S2 = 0.0;
+        for (int g = 0; g < G; ++g) {
+            const double* o = part + ((size_t)g * B + q) * 3;
+            if (o[0] == -INFINITY) continue;
+            const double e = exp(o[0] - M);
+            S1 += o[1] * e;
+            S2 += o[2] * e * e;
+        }
+        rss = S1 * S1 / ((double)P * S2);
+        const int sobs = s0 + q + 1;
+        bool date = sobs == T;
+        for (int i = 0; i < fd.n; ++i) date = date || fd.t[i] == sobs;
+        const bool low = !(rss >= d1);   // RSS < D1 (a degenerate NaN also stops)
+        stop = low || date;
+        forced = date && !low;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, stop);
+    const int at = m ? __ffs(m) - 1 : (B - 1);
+    const double rss_at = __shfl_sync(0xffffffffu, rss, at);
+    const int forced_at = __shfl_sync(0xffffffffu, forced ? 1 : 0, at);
+    if (q == 0) {
+        ctl->cd_stop = m ? at + 1 : B;
+        ctl->cd_found = m ? 1 : 0;
+        ctl->cd_forced = m ? forced_at : 0;
+        ctl->rss = rss_at;
+    }
+}
+
+cudaError_t launch_cdata_select(const double* part, int G, int B, int s0, int T, int P, double d1,
+                                const ForceDates& fd, Ctl* ctl, cudaStream_t s)
+{
+    k_cdata_select<<<1, 32, 0, s>>>(part, G, B, s0, T, P, d1, fd, ctl);
     count_launch();
     return cudaGetLastError();
 }

@@ -18,6 +18,10 @@ struct Ctl {
     // C phase, power tempering: k-ary search state.
     double llmax, lo, hi, dphi, rss, phi;
     int pass, done, last;
+    // C phase, data tempering: observations to absorb from the current chunk,
+    // whether the chunk contains the stopping observation, and whether the
+    // stop was forced (date of interest or T with RSS >= D1).
+    int cd_stop, cd_found, cd_forced;
     // RNE stopping rule.
     double mean_rne;
     // Estimators (Section 4.2): log wtilde accumulates log of J^-1 sum_j wbar_j(l-1).
@@ -71,6 +75,15 @@ struct GatherArgs {
     double* const* dst;        // device array of nrows row pointers
 };
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
+
+// Data tempering: combine the per-block statistics of one chunk and choose
+// the stopping observation (first s with RSS(s) < D1, a date of interest, or T).
+struct ForceDates {
+    int n;
+    int t[64];
+};
+cudaError_t launch_cdata_select(const double* part, int G, int B, int s0, int T, int P, double d1,
+                                const ForceDates& fd, Ctl* ctl, cudaStream_t s);
 
 // After the S phase: pooled RSS at the chosen power, log wtilde, phi update.
 cudaError_t launch_cycle_close(const double* gstat, const double* lw, int J, int N, int power,

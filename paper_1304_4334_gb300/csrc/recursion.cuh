@@ -213,6 +213,51 @@ struct EgarchF32 {
         }
     }
 
+    // Continue from a saved state (natural units) and evaluate one observation's
+    // log density l_t in natural units (data-tempering C phase).
+    __device__ __forceinline__ void load_state(const double* st)
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = (float)(st[k] * (kLog2e / 2.0));
+        es = (float)(st[K] * kSfac);
+    }
+
+    template <bool kFirst>
+    __device__ __forceinline__ double logdens(float y)
+    {
+        if constexpr (kFirst) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = v0[k];
+        } else {
+            const float ae = fabsf(es);
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = fmaf(al[k], v[k], fmaf(be[k], ae, fmaf(ga[k], es, nb[k])));
+        }
+        float e = lsy2p + v[0];
+#pragma unroll
+        for (int k = 1; k < K; ++k) e += v[k];
+        es = (y - mu) * ex2_approx(-e);
+        float u;
+        if constexpr (I == 1) {
+            u = fmaf(-es, es, -e);
+        } else {
+            float x[I];
+#pragma unroll
+            for (int i = 0; i < I; ++i) {
+                const float z = fmaf(a[i], es, b[i]);
+                x[i] = fmaf(-z, z, c[i]);
+            }
+            float m = x[0];
+#pragma unroll
+            for (int i = 1; i < I; ++i) m = fmaxf(m, x[i]);
+            float sum = 0.0f;
+#pragma unroll
+            for (int i = 0; i < I; ++i) sum += ex2_approx(x[i] - m);
+            u = (m - e) + lg2_approx(sum);
+        }
+        return kLn2 * (double)u + (-0.5 * kLog2Pi - kLogSfac);
+    }
+
     __device__ __forceinline__ void flush()
     {
         float u = sm - sh;
@@ -308,6 +353,23 @@ struct EgarchF64 {
     __device__ __forceinline__ double finish(int T) const
     {
         return acc + (double)T * (-0.5 * kLog2Pi);
+    }
+
+    __device__ __forceinline__ void load_state(const double* st)
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = st[k];
+        eps = st[K];
+    }
+
+    template <bool kFirst>
+    __device__ __forceinline__ double logdens(double y)
+    {
+        const double before = acc;
+        step<kFirst>(y);
+        const double l = acc - before;
+        acc = before;
+        return l - 0.5 * kLog2Pi;
     }
 
     __device__ __forceinline__ void state_out(double* st) const
@@ -497,6 +559,14 @@ struct LinregF64 {
     }
 
     __device__ __forceinline__ double finish(int T) const { return acc + (double)T * c0; }
+
+    __device__ __forceinline__ double logdens(const double* rec) const
+    {
+        double m = 0.0;
+        for (int i = 0; i < p; ++i) m += rec[i] * beta[i];
+        const double r = rec[p] - m;
+        return -r * r * inv2s2 + c0;
+    }
 };
 
 // Records of width W staged in chunks of whole records.

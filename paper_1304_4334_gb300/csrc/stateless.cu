@@ -122,6 +122,7 @@ smc_status smc_mutate_rw(const smc_model* m, int precision, const void* obs, int
     a.cycle = cycle;
     a.iter = iter;
     a.acc_count = cnt;
+    a.pending = nullptr;
     a.err = nullptr;
     cudaError_t e = launch_mutate(a, precision, s);
     unsigned long long h = 0;
@@ -142,7 +143,7 @@ smc_status smc_cov_chol(const double* theta, int d, int P, int h_tenths, double*
     cudaStream_t s = (cudaStream_t)stream;
     const int G = cov_grid(P);
     double* part = nullptr;
-    CK(cudaMallocAsync((void**)&part, (size_t)G * (d + d * (d + 1) / 2) * sizeof(double), s));
+    CK(cudaMallocAsync((void**)&part, (size_t)(G + 1) * (d + d * (d + 1) / 2) * sizeof(double), s));
     cudaError_t e = launch_cov(theta, d, P, part, G, nullptr, h_tenths, 0.0, 1, 10, mean, cov, L, s);
     cudaFreeAsync(part, s);
     return from_cuda(e);

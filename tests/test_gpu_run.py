@@ -35,17 +35,21 @@ def _linreg(T=60, seed=3):
     return X, y, m0, s0, lml, mn, Vn
 
 
-@pytest.mark.parametrize("resampler", ["residual", "multinomial"])
-def test_linreg_run_matches_closed_form(S, resampler):
+@pytest.mark.parametrize("resampler,tempering", [("residual", "power"), ("multinomial", "power"),
+                                                ("residual", "data")])
+def test_linreg_run_matches_closed_form(S, resampler, tempering):
     X, y, m0, s0, lml, mn, Vn = _linreg()
     J, N = 16, 512
     m = S.model_linreg(3, 1.0, m0, s0)
     c = S.config_default(J=J, N=N, precision=S.FP64, seed=11,
+                         tempering=S.POWER if tempering == "power" else S.DATA,
                          resampler=S.RESIDUAL if resampler == "residual" else S.MULTINOMIAL)
     th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), J * N, seed=5)
     ctx = S.init(m, c, y, th0, X=X)
     n, info = ctx.run()
     assert info["done"] == 1 and info["phi"] == 1.0
+    if tempering == "data":
+        assert info["t"] == len(y)
     lm, nse, lt = ctx.log_ml()
     assert abs(lm - lml) < 3.5 * nse + 0.02, (lm, lml, nse)
     assert abs(lt - lml) < 5 * nse + 0.03
@@ -56,8 +60,8 @@ def test_linreg_run_matches_closed_form(S, resampler):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_one_parameter_egarch_matches_quadrature(S, precision):
+@pytest.mark.parametrize("precision,tempering", [("fp64", "power"), ("fp32", "power"), ("fp32", "data")])
+def test_one_parameter_egarch_matches_quadrature(S, precision, tempering):
     tr = I.EgarchTruth(0.0, 0.01, (0.95,), (0.12,), (-0.05,))
     y = I.simulate_egarch(tr, 300, seed=31)
     th_true = I.theta_of_truth(tr)
@@ -72,7 +76,8 @@ def test_one_parameter_egarch_matches_quadrature(S, precision):
     pmean = integrate.simpson(wq * grid, dx=dx) / Z
     J, N = 16, 256
     m = S.model_egarch(1, 1, True, free_idx=[1], theta_fixed=th_true)
-    c = S.config_default(J=J, N=N, precision=S.FP64 if precision == "fp64" else S.FP32, seed=3)
+    c = S.config_default(J=J, N=N, precision=S.FP64 if precision == "fp64" else S.FP32, seed=3,
+                         tempering=S.POWER if tempering == "power" else S.DATA)
     th0 = I.draw_prior([math.log(0.01)], [1.0], [-np.inf], J * N, seed=41)
     ctx = S.init(m, c, y, th0)
     ctx.run()
@@ -83,7 +88,8 @@ def test_one_parameter_egarch_matches_quadrature(S, precision):
     ctx.close()
 
 
-def test_egarch11_small_run_agrees_with_oracle(S):
+@pytest.mark.parametrize("tempering", ["power", "data"])
+def test_egarch11_small_run_agrees_with_oracle(S, tempering):
     """EGARCH(1,1), Gaussian shocks, 4 parameters, T = 500, J = 4 x N = 256,
     FP64, 10 Metropolis steps per M phase: GPU and oracle runs agree on log ML
     and posterior means within combined NSE."""
@@ -92,14 +98,16 @@ def test_egarch11_small_run_agrees_with_oracle(S):
     m = S.model_egarch(1, 1, False)
     mean, sd, lo = S.model_prior(m)
     th0 = I.draw_prior(mean, sd, lo, w.P, seed=w.prior_seed)
-    c = S.config_default(J=w.J, N=w.N, precision=S.FP64, rbar=10, kappa=1, seed=7)
+    tmode = S.POWER if tempering == "power" else S.DATA
+    c = S.config_default(J=w.J, N=w.N, precision=S.FP64, rbar=10, kappa=1, seed=7, tempering=tmode)
     ctx = S.init(m, c, y, th0)
     ctx.run()
     lm, nse, _ = ctx.log_ml()
     mom = ctx.moments()
     ctx.close()
     spec = O.ModelSpec(K=1, I=1, gamma=False)
-    r = O.smc_run(spec, y, th0, w.J, w.N, rbar=10, kappa=1, seed=7, nthreads=8)
+    r = O.smc_run(spec, y, th0, w.J, w.N, rbar=10, kappa=1, seed=7, nthreads=8,
+                  tempering=1 if tempering == "power" else 0)
     tol = lambda a, b: 4.0 * math.hypot(a, b) + 0.02
     assert abs(lm - r["log_ml"]) < tol(nse, r["log_ml_nse"]), (lm, r["log_ml"], nse, r["log_ml_nse"])
     for i in range(4):
@@ -154,6 +162,26 @@ def test_full_size_run_sampled_parity(S):
     # the posterior concentrates near the data-generating parameters
     th_true = I.theta_of_truth(w.truth)
     assert abs(np.mean(th[:, 1]) - th_true[1]) < 0.2
+
+
+def test_data_tempering_dates_of_interest(S):
+    """A forced stop at a date of interest ends a cycle there even with RSS >= D1."""
+    X, y, m0, s0, lml, mn, Vn = _linreg()
+    m = S.model_linreg(3, 1.0, m0, s0)
+    c = S.config_default(J=8, N=256, precision=S.FP64, tempering=S.DATA, seed=4, force_dates=[37, 45])
+    th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), 8 * 256, seed=6)
+    ctx = S.init(m, c, y, th0, X=X)
+    ts = []
+    while True:
+        inf = ctx.cycle()
+        if inf is None:
+            break
+        ts.append(inf["t"])
+    assert 37 in ts and 45 in ts and ts[-1] == len(y)
+    assert all(b > a for a, b in zip(ts, ts[1:]))
+    lm, nse, _ = ctx.log_ml()
+    assert abs(lm - lml) < 4 * nse + 0.02
+    ctx.close()
 
 
 def test_rne_stopping_rule_run(S):
