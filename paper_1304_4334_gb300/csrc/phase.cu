@@ -256,9 +256,10 @@ __global__ void __launch_bounds__(kSearchThreads) k_llmax_partial(const double* 
 
 __global__ void k_search_init(const double* part, int G, Ctl* ctl)
 {
-    if (threadIdx.x != 0) return;
     double m = -INFINITY;
-    for (int g = 0; g < G; ++g) m = fmax(m, part[g]);
+    for (int g = threadIdx.x; g < G; g += 32) m = fmax(m, part[g]);
+    m = warp_max(m);
+    if (threadIdx.x != 0) return;
     ctl->llmax = m;
     ctl->lo = 0.0;
     ctl->hi = 1.0 - ctl->phi;
@@ -610,21 +611,27 @@ cudaError_t launch_cdata_select(const double* part, int G, int B, int s0, int T,
 // log wtilde += log(J^-1 sum_j wbar_j(l-1)), and phi += dphi.
 __global__ void k_cycle_close(const double* gstat, const double* lw, int J, int N, int power, Ctl* ctl)
 {
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x;
     double M = -INFINITY;
-    for (int j = 0; j < J; ++j) M = fmax(M, gstat[3 * j]);
+    for (int j = lane; j < J; j += 32) M = fmax(M, gstat[3 * j]);
+    M = warp_max(M);
     double s1 = 0.0, s2 = 0.0;
-    for (int j = 0; j < J; ++j) {
+    for (int j = lane; j < J; j += 32) {
         if (gstat[3 * j] == -INFINITY) continue;
         const double e = exp(gstat[3 * j] - M);
         s1 += gstat[3 * j + 1] * e;
         s2 += gstat[3 * j + 2] * e * e;
     }
-    ctl->rss = s1 * s1 / ((double)J * (double)N * s2);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
     double lm = -INFINITY;
-    for (int j = 0; j < J; ++j) lm = fmax(lm, lw[j]);
+    for (int j = lane; j < J; j += 32) lm = fmax(lm, lw[j]);
+    lm = warp_max(lm);
     double s = 0.0;
-    for (int j = 0; j < J; ++j) s += exp(lw[j] - lm);
+    for (int j = lane; j < J; j += 32) s += exp(lw[j] - lm);
+    s = warp_sum(s);
+    if (lane != 0) return;
+    ctl->rss = s1 * s1 / ((double)J * (double)N * s2);
     ctl->ltilde += lm + log(s / (double)J);
     if (power) ctl->phi = ctl->last ? 1.0 : ctl->phi + ctl->dphi;
     ctl->acc_sum = 0.0;
@@ -782,17 +789,20 @@ cudaError_t launch_moments(const double* g, int nf, int J, int N, double* part, 
 // [J (J-1)]^-1 sum_j (wbar_j - wbar)^2 / wbar^2, all scaled by exp(max a).
 __global__ void k_ml(const double* a, int J, const Ctl* ctl, double* out)
 {
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x;
     double amax = -INFINITY;
-    for (int j = 0; j < J; ++j) amax = fmax(amax, a[j]);
-    double rbar = 0.0;
-    for (int j = 0; j < J; ++j) rbar += exp(a[j] - amax);
-    rbar /= (double)J;
+    for (int j = lane; j < J; j += 32) amax = fmax(amax, a[j]);
+    amax = warp_max(amax);
+    double rs = 0.0;
+    for (int j = lane; j < J; j += 32) rs += exp(a[j] - amax);
+    const double rbar = warp_sum(rs) / (double)J;
     double ss = 0.0;
-    for (int j = 0; j < J; ++j) {
+    for (int j = lane; j < J; j += 32) {
         const double r = exp(a[j] - amax) - rbar;
         ss += r * r;
     }
+    ss = warp_sum(ss);
+    if (lane != 0) return;
     out[0] = amax + log(rbar);
     out[1] = sqrt(ss / ((double)J * (J - 1.0))) / rbar;
     out[2] = ctl ? ctl->ltilde : 0.0;

@@ -105,7 +105,7 @@ __device__ __forceinline__ void egarch_transform(const Real* th, int has_gamma,
     } else {
         Real pstar[I], mustar[I], sigstar[I];
 #pragma unroll
-        for (int i = 0; i < I; ++i) pstar[i] = tanh(th[j + i]) + Real(1);
+        for (int i = 0; i < I; ++i) pstar[i] = Real(2) / (Real(1) + exp(Real(-2) * th[j + i]));  // tanh + 1 without cancellation
 #pragma unroll
         for (int i = 0; i < I; ++i) mustar[i] = th[j + I + i];
 #pragma unroll
@@ -136,14 +136,22 @@ __device__ __forceinline__ void egarch_transform(const Real* th, int has_gamma,
 }
 
 // ------------------------------------------------------------- FP32 recursion
+// The first factor carries log2 sigma_Y - log2 s: u = lsy2p + v'_1, so that
+// log2 h - log2 s = u + v'_2 + ... + v'_K; its update is
+//   u_t = alpha_1 u_t-1 + (1 - alpha_1) lsy2p + beta'_1 |es| + gamma'_1 es - beta_1 c log2(e)/2.
+// Each update is split into alpha v + const (independent of the last shock,
+// so it overlaps the previous exponential) and the shock terms, which keeps
+// the per-observation dependency chain to two FMAs, one add, one ex2 and one
+// multiply.
 template <int K, int I>
 struct EgarchF32 {
     float mu, lsy2p;                       // mu_Y; log2 sigma_Y - log2 s
-    float al[K], be[K], ga[K], nb[K];      // alpha; beta, gamma in scaled units; -beta c log2(e)/2
+    float al[K], be[K], ga[K], nb[K];      // alpha; beta, gamma in scaled units; constant term
     float a[I], b[I], c[I];                // 1/sigma_i; -mu_i s / sigma_i; log2(p_i / sigma_i)
-    float v0[K];                           // v'_k1
-    float v[K], es;                        // recursion state (scaled units)
+    float v0[K];                           // state after the first observation's update
+    float v[K], es;                        // recursion state (scaled units; v[0] includes lsy2p)
     float sh, sm, prod;                    // partial sums over the current 32 observations
+    float part;                            // sum of the completed 32-observation partials (<= 64 obs)
     double acc;                            // FP64 sum of completed partials (log2 units)
 
     __device__ __forceinline__ void setup(const float* th, int has_gamma, int eps0_zero)
@@ -157,9 +165,12 @@ struct EgarchF32 {
             al[k] = q.alpha[k];
             be[k] = q.beta[k] * (float)(kLog2e / 2.0 / kSfac);
             ga[k] = q.gamma[k] * (float)(kLog2e / 2.0 / kSfac);
-            nb[k] = -q.beta[k] * (float)(kSqrt2OverPi * kLog2e / 2.0);
-            v0[k] = eps0_zero ? nb[k] : 0.0f;
+            const float c0 = -q.beta[k] * (float)(kSqrt2OverPi * kLog2e / 2.0);
+            nb[k] = c0;
+            v0[k] = eps0_zero ? c0 : 0.0f;
         }
+        nb[0] = fmaf(1.0f - al[0], lsy2p, nb[0]);
+        v0[0] += lsy2p;
 #pragma unroll
         for (int i = 0; i < I; ++i) {
             a[i] = 1.0f / q.sig[i];
@@ -169,23 +180,41 @@ struct EgarchF32 {
         es = 0.0f;
         sh = sm = 0.0f;
         prod = 1.0f;
+        part = 0.0f;
         acc = 0.0;
+    }
+
+    __device__ __forceinline__ void update_volatility_first()
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = v0[k];
+    }
+
+    __device__ __forceinline__ void update_volatility()
+    {
+        float vp[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) vp[k] = fmaf(al[k], v[k], nb[k]);
+        const float ae = fabsf(es);
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = fmaf(be[k], ae, fmaf(ga[k], es, vp[k]));
+    }
+
+    // e = log2 h_t - log2 s
+    __device__ __forceinline__ float log2h() const
+    {
+        float e = v[0];
+#pragma unroll
+        for (int k = 1; k < K; ++k) e += v[k];
+        return e;
     }
 
     template <bool kFirst>
     __device__ __forceinline__ void step(float y)
     {
-        if constexpr (kFirst) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) v[k] = v0[k];
-        } else {
-            const float ae = fabsf(es);
-#pragma unroll
-            for (int k = 0; k < K; ++k) v[k] = fmaf(al[k], v[k], fmaf(be[k], ae, fmaf(ga[k], es, nb[k])));
-        }
-        float e = lsy2p + v[0];
-#pragma unroll
-        for (int k = 1; k < K; ++k) e += v[k];
+        if constexpr (kFirst) update_volatility_first();
+        else update_volatility();
+        const float e = log2h();
         sh += e;
         es = (y - mu) * ex2_approx(-e);
         if constexpr (I == 1) {
@@ -219,23 +248,16 @@ struct EgarchF32 {
     {
 #pragma unroll
         for (int k = 0; k < K; ++k) v[k] = (float)(st[k] * (kLog2e / 2.0));
+        v[0] += lsy2p;
         es = (float)(st[K] * kSfac);
     }
 
     template <bool kFirst>
     __device__ __forceinline__ double logdens(float y)
     {
-        if constexpr (kFirst) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) v[k] = v0[k];
-        } else {
-            const float ae = fabsf(es);
-#pragma unroll
-            for (int k = 0; k < K; ++k) v[k] = fmaf(al[k], v[k], fmaf(be[k], ae, fmaf(ga[k], es, nb[k])));
-        }
-        float e = lsy2p + v[0];
-#pragma unroll
-        for (int k = 1; k < K; ++k) e += v[k];
+        if constexpr (kFirst) update_volatility_first();
+        else update_volatility();
+        const float e = log2h();
         es = (y - mu) * ex2_approx(-e);
         float u;
         if constexpr (I == 1) {
@@ -258,25 +280,35 @@ struct EgarchF32 {
         return kLn2 * (double)u + (-0.5 * kLog2Pi - kLogSfac);
     }
 
+    // Closes a 32-observation partial (the product of shifted mixture sums
+    // stays below 4^32 = 2^64).
     __device__ __forceinline__ void flush()
     {
         float u = sm - sh;
         if constexpr (I >= 2) u += lg2_approx(prod);
-        acc += (double)u;
+        part += u;
         sh = sm = 0.0f;
         prod = 1.0f;
+    }
+
+    // Adds the FP32 partial of up to 64 observations into the FP64 sum.
+    __device__ __forceinline__ void flush64()
+    {
+        acc += (double)part;
+        part = 0.0f;
     }
 
     // log p(y_1:T | theta); call after the last flush.
     __device__ __forceinline__ double finish(int T) const
     {
-        return kLn2 * acc + (double)T * (-0.5 * kLog2Pi - kLogSfac);
+        return kLn2 * (acc + (double)part) + (double)T * (-0.5 * kLog2Pi - kLogSfac);
     }
 
     __device__ __forceinline__ void state_out(double* st) const
     {
+        st[0] = (double)(v[0] - lsy2p) * (2.0 * kLn2);
 #pragma unroll
-        for (int k = 0; k < K; ++k) st[k] = (double)v[k] * (2.0 * kLn2);
+        for (int k = 1; k < K; ++k) st[k] = (double)v[k] * (2.0 * kLn2);
         st[K] = (double)es / kSfac;
     }
 };
@@ -496,6 +528,7 @@ __device__ __forceinline__ bool run_egarch_f32(EgarchF32<K, I>& mdl, ObsPipe<flo
                 }
             }
             mdl.flush();
+            if (u & 1) mdl.flush64();
         }
         const int rem = cnt & 31;
         if (rem) {
