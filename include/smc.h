@@ -267,6 +267,22 @@ smc_status smc_resample(const double* w, int J, int N, int resampler, uint64_t s
  * g (device [nf][J*N], group-major columns).  out: host [nf][4]. */
 smc_status smc_group_moments(const double* g, int nf, int J, int N, double* out, void* stream);
 
+/* The same computation as smc_cov_chol for callers that cannot allocate
+ * device memory while they run (a framework that reserves the device memory
+ * budget up front, or a latency-bound loop that must not wait on the memory
+ * pool).  The paper has no counterpart: this is a deployment variant.  Its
+ * partial-sum scratch is a fixed array inside the library (about 1.1 MB per
+ * device that uses it, held until the process exits), so it calls no
+ * allocator.  Limits: 1 <= d <= SMC_MAX_D, P >= 2; other sizes return
+ * SMC_EINVAL.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls on a device share the array:
+ * calls whose kernels overlap on the GPU (unordered streams) race on it.
+ * Every entry read in a call is written earlier in the same call, so no
+ * clearing is needed.  Arguments, outputs and errors as smc_cov_chol. */
+smc_status smc_cov_chol_noalloc(const double* theta, int d, int P, int h_tenths, double* mean,
+                                double* cov, double* L, void* stream);
+
 /* log wbar, its NSE (ML_se) from per-group log products a (device [J]). */
 smc_status smc_ml_from_groups(const double* a, int J, double* log_ml, double* nse, void* stream);
 
