@@ -118,7 +118,7 @@ typedef struct {
     int precision;            /* SMC_FP32: recursion in FP32 with FP64 log-likelihood,
                                  log weights and estimators; SMC_FP64: all FP64 */
     int tempering;            /* SMC_POWER | SMC_DATA */
-    int mutation;             /* SMC_RW (MALA is not in this build) */
+    int mutation;             /* SMC_RW | SMC_MALA (Langevin proposal using the adjoint gradient) */
     int resampler;            /* SMC_RESIDUAL | SMC_MULTINOMIAL */
     double d1, d2;
     int stop_rule;            /* SMC_STOP_DET | SMC_STOP_RNE */
@@ -237,6 +237,27 @@ smc_status smc_mutate_rw(const smc_model* m, int precision, const void* obs, int
                          double* theta, double* ll, double* lp, double* state, int P,
                          const double* L, double phi, uint64_t seed, uint64_t cycle,
                          uint64_t iter, uint64_t* accepted, void* stream);
+
+/* Log likelihood and its gradient with respect to the (free) transformed
+ * parameters theta, by a hand-written adjoint (reverse-mode) sweep through the
+ * EGARCH recursion of Section 5.1 with checkpoints of the state every 32 (FP32)
+ * or 16 (FP64) observations; for LINREG the closed form sum_t (y_t - x_t'b) x_t
+ * / sigma^2.  Layouts as smc_loglik; grad: device [d][P].  Checkpoint scratch
+ * is allocated stream-ordered (about (K+1) T P / 32 values). */
+smc_status smc_loglik_grad(const smc_model* m, int precision, const void* obs, int T,
+                           const double* theta, int P, double* ll, double* grad, double* state,
+                           void* stream);
+
+/* One MALA iteration on device particles in place (an alternative Metropolis
+ * update in the sense of Section 3.3): theta* = theta + (1/2) L L' g + L z,
+ * g = grad log prior + phi grad (stored gradient of the log likelihood, device
+ * [d][P], updated on acceptance), z as in smc_mutate_rw; accepted with
+ * log u < [lp + phi l](theta*) - [lp + phi l](theta) + log q(theta | theta*)
+ * - log q(theta* | theta).  accepted (host, nullable) synchronises. */
+smc_status smc_mutate_mala(const smc_model* m, int precision, const void* obs, int T, double* theta,
+                           double* ll, double* lp, double* grad, double* state, int P, const double* L,
+                           double phi, uint64_t seed, uint64_t cycle, uint64_t iter, uint64_t* accepted,
+                           void* stream);
 
 /* Pooled mean and covariance V of theta (device [d][P]) and the lower
  * Cholesky factor of (h_tenths / 10)^2 V (Section 3.3, Sigma = h^2 V); a

@@ -8,6 +8,7 @@
 // rules state.
 #include "../../include/smc.h"
 #include "kernels.cuh"
+#include "mala.cuh"
 #include "phase.cuh"
 
 #include <atomic>
@@ -169,6 +170,8 @@ struct smc_ctx {
     double* ll[2] = {nullptr, nullptr};
     double* lp[2] = {nullptr, nullptr};
     double* state[2] = {nullptr, nullptr};
+    double* grad[2] = {nullptr, nullptr};  // MALA: likelihood gradient [d][P]
+    void* ckpt = nullptr;                  // MALA: recursion checkpoints
     int cur = 0;
     double* thp = nullptr;           // proposal scratch [d][P]
     double* logw = nullptr;          // [P] data tempering log weights
@@ -381,6 +384,7 @@ static void release(smc_ctx* c)
 {
     if (!c) return;
     void* ptrs[] = {c->obs, c->theta[0], c->theta[1], c->ll[0], c->ll[1], c->lp[0], c->lp[1],
+                    c->grad[0], c->grad[1], c->ckpt,
                     c->state[0], c->state[1], c->thp, c->logw, c->g, c->a, c->lw, c->gstat,
                     c->idx, c->cov_part, c->search_part, c->cd_part, c->mom_part, c->mom_out, c->ml_out,
                     c->L, c->gather_ptrs, c->ctl};
@@ -450,6 +454,42 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
     double* th = ctx->theta[ctx->cur];
     CU(launch_cov(th, d, P, ctx->cov_part, ctx->cov_G, ctx->ctl, 0, c.acc_target, c.hmin_tenths,
                   c.hmax_tenths, nullptr, nullptr, ctx->L, ctx->stream));
+    if (c.mutation == SMC_MALA) {
+        MalaArgs a;
+        a.m = ctx->mdev;
+        a.obs = ctx->obs;
+        a.T = Tm;
+        a.W = ctx->W;
+        a.theta = th;
+        a.ll = ctx->ll[ctx->cur];
+        a.lp = ctx->lp[ctx->cur];
+        a.state = ctx->ns ? ctx->state[ctx->cur] : nullptr;
+        a.grad = ctx->grad[ctx->cur];
+        a.ckpt = ctx->ckpt;
+        a.P = P;
+        a.ns = ctx->ns;
+        a.L = ctx->L;
+        a.phi = phi;
+        a.seed = c.seed;
+        a.cycle = (uint64_t)ctx->cycle;
+        a.iter = (uint64_t)r;
+        a.acc_count = &ctx->ctl->acc_count;
+        a.pending = &ctx->ctl->pending;
+        a.err = &ctx->ctl->err;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (ctx->profile) {
+            e0 = take_event(ctx);
+            e1 = take_event(ctx);
+            CU(cudaEventRecord(e0, ctx->stream));
+        }
+        CU(launch_mala(a, c.precision, ctx->stream));
+        if (ctx->profile) {
+            CU(cudaEventRecord(e1, ctx->stream));
+            ctx->ev_pending.push_back({e0, e1});
+            ctx->mutate_launches += 1;
+        }
+        return SMC_OK;
+    }
     MutateArgs a;
     a.m = ctx->mdev;
     a.obs = ctx->obs;
@@ -482,6 +522,24 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
         ctx->ev_pending.push_back({e0, e1});
         ctx->mutate_launches += 1;
     }
+    return SMC_OK;
+}
+
+// MALA: log likelihood and its gradient of the current particles over y_1:T.
+static smc_status refresh_gradient(smc_ctx* ctx, int T)
+{
+    GradArgs g;
+    g.m = ctx->mdev;
+    g.obs = ctx->obs;
+    g.T = T;
+    g.W = ctx->W;
+    g.theta = ctx->theta[ctx->cur];
+    g.P = ctx->P;
+    g.ll = ctx->ll[ctx->cur];
+    g.grad = ctx->grad[ctx->cur];
+    g.state = ctx->ns ? ctx->state[ctx->cur] : nullptr;
+    g.ckpt = ctx->ckpt;
+    CU(launch_loglik_grad(g, ctx->cfg.precision, ctx->stream));
     return SMC_OK;
 }
 
@@ -556,7 +614,8 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
     if (T < 1 || !y) return set_err(ctx, SMC_EINVAL, "need T >= 1 observations");
     if (m->model == SMC_LINREG && !X) return set_err(ctx, SMC_EINVAL, "LINREG needs X");
     if (!theta0) return set_err(ctx, SMC_EINVAL, "theta0 is NULL");
-    if (c->mutation != SMC_RW) return set_err(ctx, SMC_EINVAL, "only random-walk mutation is built");
+    if (c->mutation != SMC_RW && c->mutation != SMC_MALA)
+        return set_err(ctx, SMC_EINVAL, "unknown mutation %d", c->mutation);
     if (c->tempering != SMC_POWER && c->tempering != SMC_DATA)
         return set_err(ctx, SMC_EINVAL, "unknown tempering %d", c->tempering);
     if (c->precision != SMC_FP32 && c->precision != SMC_FP64)
@@ -626,6 +685,11 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
         CU(dalloc(&ctx->state[b], Ps * (ctx->ns ? ctx->ns : 1)));
     }
     CU(dalloc(&ctx->thp, Ps * d));
+    if (c->mutation == SMC_MALA) {
+        CU(dalloc(&ctx->grad[0], Ps * d));
+        CU(dalloc(&ctx->grad[1], Ps * d));
+        CU(cudaMalloc(&ctx->ckpt, mala_ckpt_bytes(ctx->mdev, c->precision, T, P)));
+    }
     CU(dalloc(&ctx->logw, Ps));
     CU(dalloc(&ctx->g, Ps * 3));
     CU(dalloc(&ctx->a, J));
@@ -645,7 +709,8 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
     CU(cudaMallocHost((void**)&ctx->ctl_host, sizeof(Ctl)));
 
     // gather tables: rows of theta, ll, lp, state for both directions
-    ctx->gather_rows = d + 2 + ctx->ns;
+    const int ng = c->mutation == SMC_MALA ? d : 0;
+    ctx->gather_rows = d + 2 + ctx->ns + ng;
     std::vector<double*> tab((size_t)2 * 2 * ctx->gather_rows);
     for (int dir = 0; dir < 2; ++dir) {
         const int from = dir, to = dir ^ 1;
@@ -663,6 +728,10 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
         for (int k = 0; k < ctx->ns; ++k, ++r) {
             srcs[r] = ctx->state[from] + (size_t)k * Ps;
             dsts[r] = ctx->state[to] + (size_t)k * Ps;
+        }
+        for (int i = 0; i < ng; ++i, ++r) {
+            srcs[r] = ctx->grad[from] + (size_t)i * Ps;
+            dsts[r] = ctx->grad[to] + (size_t)i * Ps;
         }
     }
     CU(dalloc(&ctx->gather_ptrs, tab.size()));
@@ -712,6 +781,10 @@ static smc_status start_run(smc_ctx* ctx, const double* theta0, int theta0_on_de
         la.ns = ctx->ns;
         la.err = &ctx->ctl->err;
         CU(launch_loglik(la, c->precision, ctx->stream));
+        if (c->mutation == SMC_MALA) {
+            smc_status st = refresh_gradient(ctx, T);
+            if (st != SMC_OK) return st;
+        }
     } else {
         k_init_data_tempering<<<(P + 255) / 256, 256, 0, ctx->stream>>>(ctx->mdev, ctx->theta[0], P,
                                                                         ctx->ns, ctx->ll[0], ctx->lp[0],
@@ -851,6 +924,10 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
         // the pending count (if any) was applied at the end of the last M phase
         int h0 = c.h0_tenths;
         CU(cudaMemcpyAsync(&ctx->ctl->h_tenths, &h0, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    if (c.mutation == SMC_MALA && c.tempering == SMC_DATA) {
+        st = refresh_gradient(ctx, Tm);
+        if (st != SMC_OK) return st;
     }
     int R = c.stop_rule == SMC_STOP_DET ? (rss < c.d2 ? c.kappa * c.rbar : c.rbar) : c.rmax;
     const double E = forced ? c.e2 : c.e1;

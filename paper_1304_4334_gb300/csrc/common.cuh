@@ -76,8 +76,10 @@ __device__ __forceinline__ void proposal_normals(uint64_t seed, uint64_t p, uint
                 z[n] = rho * c;
                 if (n + 1 < d) z[n + 1] = rho * s;
             } else {
-                const float ua = (float)uniform53(u[2 * pair]);
-                const float ub = (float)uniform53(u[2 * pair + 1]);
+                // 24-bit uniforms ((x >> 40) + 1/2) 2^-24: the same draws as the
+                // 53-bit ones to FP32 precision, without FP64 conversions
+                const float ua = ((float)(uint32_t)(u[2 * pair] >> 40) + 0.5f) * 0x1.0p-24f;
+                const float ub = ((float)(uint32_t)(u[2 * pair + 1] >> 40) + 0.5f) * 0x1.0p-24f;
                 const float rho = sqrtf(-2.0f * logf(ua));
                 float s, c;
                 sincospif(2.0f * ub, &s, &c);

@@ -1,0 +1,6 @@
+// FP32 gradient and MALA kernels, K = 2 volatility factors, I = 1..4.
+#include "mala.cuh"
+namespace smc {
+cudaError_t launch_grad_f32_k2(const GradArgs& a, cudaStream_t s) { return launch_grad_k<float, 2>(a, s); }
+cudaError_t launch_mala_f32_k2(const MalaArgs& a, cudaStream_t s) { return launch_mala_k<float, 2>(a, s); }
+}  // namespace smc

@@ -1,0 +1,6 @@
+// FP64 gradient and MALA kernels, K = 2 volatility factors, I = 1..4.
+#include "mala.cuh"
+namespace smc {
+cudaError_t launch_grad_f64_k2(const GradArgs& a, cudaStream_t s) { return launch_grad_k<double, 2>(a, s); }
+cudaError_t launch_mala_f64_k2(const MalaArgs& a, cudaStream_t s) { return launch_mala_k<double, 2>(a, s); }
+}  // namespace smc

@@ -15,7 +15,7 @@
 //   mixture exponent x_it = log2(p_i / sigma_i) - (s (eps_t - mu_i) / sigma_i)^2.
 // The mixture log-sum-exp is max-shifted; the shifted sums s_t in [1, I] are
 // multiplied together and one lg2 is taken per 32 observations.  Sums of the
-// per-observation terms stay in FP32 for 32 observations and are then added
+// per-observation terms stay in FP32 for 256 observations and are then added
 // into an FP64 accumulator (the log likelihood itself is FP64).
 // FP64 path (EgarchF64): the four steps as written, in double precision.
 #pragma once
@@ -151,7 +151,7 @@ struct EgarchF32 {
     float v0[K];                           // state after the first observation's update
     float v[K], es;                        // recursion state (scaled units; v[0] includes lsy2p)
     float sh, sm, prod;                    // partial sums over the current 32 observations
-    float part;                            // sum of the completed 32-observation partials (<= 64 obs)
+    float part;                            // sum of the completed 32-observation partials (<= 256 obs)
     double acc;                            // FP64 sum of completed partials (log2 units)
 
     __device__ __forceinline__ void setup(const float* th, int has_gamma, int eps0_zero)
@@ -291,8 +291,8 @@ struct EgarchF32 {
         prod = 1.0f;
     }
 
-    // Adds the FP32 partial of up to 64 observations into the FP64 sum.
-    __device__ __forceinline__ void flush64()
+    // Adds the FP32 partial of up to 256 observations into the FP64 sum.
+    __device__ __forceinline__ void flush_fp64()
     {
         acc += (double)part;
         part = 0.0f;
@@ -528,7 +528,7 @@ __device__ __forceinline__ bool run_egarch_f32(EgarchF32<K, I>& mdl, ObsPipe<flo
                 }
             }
             mdl.flush();
-            if (u & 1) mdl.flush64();
+            if ((u & 7) == 7) mdl.flush_fp64();
         }
         const int rem = cnt & 31;
         if (rem) {

@@ -3,6 +3,7 @@
 // allocated stream-ordered on the caller's stream and freed before returning.
 #include "../../include/smc.h"
 #include "kernels.cuh"
+#include "mala.cuh"
 #include "phase.cuh"
 
 #include <cmath>
@@ -132,6 +133,78 @@ smc_status smc_mutate_rw(const smc_model* m, int precision, const void* obs, int
         *accepted = h;
     }
     cudaFreeAsync(thp, s);
+    cudaFreeAsync(cnt, s);
+    return from_cuda(e);
+}
+
+smc_status smc_loglik_grad(const smc_model* m, int precision, const void* obs, int T,
+                           const double* theta, int P, double* ll, double* grad, double* state,
+                           void* stream)
+{
+    if (!model_ok(m, precision) || !obs || !theta || !ll || !grad || T < 1 || P < 1 || !aligned16(obs))
+        return SMC_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    GradArgs a;
+    a.m = ModelDev{};
+    model_dev(*m, a.m);
+    a.obs = obs;
+    a.T = T;
+    a.W = m->model == SMC_LINREG ? smc_linreg_width(m->p) : 1;
+    a.theta = theta;
+    a.P = P;
+    a.ll = ll;
+    a.grad = grad;
+    a.state = m->model == SMC_EGARCH ? state : nullptr;
+    a.ckpt = nullptr;
+    CK(cudaMallocAsync(&a.ckpt, mala_ckpt_bytes(a.m, precision, T, P), s));
+    const cudaError_t e = launch_loglik_grad(a, precision, s);
+    cudaFreeAsync(a.ckpt, s);
+    return from_cuda(e);
+}
+
+smc_status smc_mutate_mala(const smc_model* m, int precision, const void* obs, int T, double* theta,
+                           double* ll, double* lp, double* grad, double* state, int P, const double* L,
+                           double phi, uint64_t seed, uint64_t cycle, uint64_t iter, uint64_t* accepted,
+                           void* stream)
+{
+    if (!model_ok(m, precision) || !obs || !theta || !ll || !lp || !grad || !L || T < 1 || P < 1 ||
+        !aligned16(obs) || !(phi >= 0.0))
+        return SMC_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long* cnt = nullptr;
+    MalaArgs a;
+    a.m = ModelDev{};
+    model_dev(*m, a.m);
+    a.obs = obs;
+    a.T = T;
+    a.W = m->model == SMC_LINREG ? smc_linreg_width(m->p) : 1;
+    a.theta = theta;
+    a.ll = ll;
+    a.lp = lp;
+    a.state = m->model == SMC_EGARCH ? state : nullptr;
+    a.grad = grad;
+    a.ckpt = nullptr;
+    a.P = P;
+    a.ns = m->model == SMC_EGARCH ? m->K + 1 : 0;
+    a.L = L;
+    a.phi = phi;
+    a.seed = seed;
+    a.cycle = cycle;
+    a.iter = iter;
+    a.pending = nullptr;
+    a.err = nullptr;
+    CK(cudaMallocAsync(&a.ckpt, mala_ckpt_bytes(a.m, precision, T, P), s));
+    CK(cudaMallocAsync((void**)&cnt, sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+    a.acc_count = cnt;
+    cudaError_t e = launch_mala(a, precision, s);
+    unsigned long long h = 0;
+    if (e == cudaSuccess && accepted) {
+        e = cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        *accepted = h;
+    }
+    cudaFreeAsync(a.ckpt, s);
     cudaFreeAsync(cnt, s);
     return from_cuda(e);
 }

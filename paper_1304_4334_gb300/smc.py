@@ -103,6 +103,9 @@ def _declare(L):
     L.smc_linreg_width.restype = C.c_int
     L.smc_mutate_rw.argtypes = [P(smc_model), C.c_int, vp, C.c_int, vp, vp, vp, vp, C.c_int, vp,
                                 C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, P(C.c_uint64), vp]
+    L.smc_loglik_grad.argtypes = [P(smc_model), C.c_int, vp, C.c_int, vp, C.c_int, vp, vp, vp, vp]
+    L.smc_mutate_mala.argtypes = [P(smc_model), C.c_int, vp, C.c_int, vp, vp, vp, vp, vp, C.c_int, vp,
+                                  C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, P(C.c_uint64), vp]
     L.smc_cov_chol.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
     L.smc_power_search.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int, dp, dp, vp]
     L.smc_resample.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, vp, vp]
@@ -326,6 +329,24 @@ def mutate_rw(model, precision, obs, theta, ll, lp, state, L, phi, seed, cycle, 
     _check(lib().smc_mutate_rw(C.byref(model), precision, _ptr(obs), T, _ptr(theta), _ptr(ll),
                                _ptr(lp), _ptr(state), P, _ptr(L), float(phi), seed, cycle, it,
                                C.byref(acc), _stream(stream)))
+    return acc.value
+
+
+def loglik_grad(model, precision, obs, theta, ll, grad, state=None, stream=None):
+    """Log likelihood and its theta-gradient (adjoint kernel); grad float64 [d, P]."""
+    T = obs.shape[0]
+    P = theta.shape[1]
+    _check(lib().smc_loglik_grad(C.byref(model), precision, _ptr(obs), T, _ptr(theta), P, _ptr(ll),
+                                 _ptr(grad), _ptr(state), _stream(stream)))
+
+
+def mutate_mala(model, precision, obs, theta, ll, lp, grad, state, L, phi, seed, cycle, it, stream=None):
+    T = obs.shape[0]
+    P = theta.shape[1]
+    acc = C.c_uint64()
+    _check(lib().smc_mutate_mala(C.byref(model), precision, _ptr(obs), T, _ptr(theta), _ptr(ll),
+                                 _ptr(lp), _ptr(grad), _ptr(state), P, _ptr(L), float(phi), seed, cycle,
+                                 it, C.byref(acc), _stream(stream)))
     return acc.value
 
 
