@@ -211,6 +211,42 @@ const char* smc_last_error(const smc_ctx* ctx);
 const char* smc_status_str(smc_status s);
 
 /* ---------------------------------------------------------------------------
+ * Batched runs: n independent simulator runs (datasets of different length T,
+ * EGARCH models of different K and I; FP32, power tempering, random walk,
+ * deterministic stopping rule) advanced together cycle by cycle.  Each run is
+ * Algorithm 2 as in smc_cycle and keeps its own particles, seed and adaptation;
+ * the batch shares the M-phase launches: one persistent kernel per Metropolis
+ * iteration processes every run's particles from a work queue ordered by
+ * decreasing cost (T x per-observation work), and one iteration (batched
+ * covariance + persistent mutation) is a captured CUDA graph.
+ * ------------------------------------------------------------------------- */
+typedef struct smc_batch smc_batch;
+
+/* ys[i]: host observations of run i (Ts[i] of them); theta0s[i]: host prior
+ * draws [P_i][d_i].  On error *out is still set (free it with smc_batch_free). */
+smc_status smc_batch_init(int n, const smc_model* models, const smc_config* cfgs, const double* const* ys,
+                          const int* Ts, const double* const* theta0s, void* stream, smc_batch** out);
+/* Times `iters` M iterations for each candidate tile (64, 128, 256 particles
+ * per work item) on a snapshot of the particles (restored afterwards) and
+ * keeps the fastest; ms_per_iteration (host, nullable) gets its time. */
+smc_status smc_batch_autotune(smc_batch* b, int iters, double* ms_per_iteration);
+/* One cycle of every unfinished run; SMC_EDONE when all are done. */
+smc_status smc_batch_cycle(smc_batch* b, int* n_active);
+smc_status smc_batch_run(smc_batch* b, int max_cycles, int* ncycles);
+/* Restarts every run from new prior draws (device [d][P] when on_device);
+ * run i gets seed + i. */
+smc_status smc_batch_reset(smc_batch* b, const double* const* theta0s, int theta0_on_device, uint64_t seed);
+/* Sums over runs of M-phase particle x observation evaluations and Metropolis
+ * iterations, and batched cycles so far (host outputs, nullable). */
+smc_status smc_batch_totals(smc_batch* b, double* evals, int64_t* metropolis_steps, int* cycles);
+/* Run i's context, for smc_log_ml, smc_moments, smc_get_particles,
+ * smc_run_totals (owned by the batch). */
+smc_ctx* smc_batch_member(smc_batch* b, int i);
+int smc_batch_tile(const smc_batch* b);
+const char* smc_batch_last_error(const smc_batch* b);
+void smc_batch_free(smc_batch* b);
+
+/* ---------------------------------------------------------------------------
  * Stateless entry points on caller-owned device memory (for tests, autograd
  * and custom drivers).  All enqueue on `stream`; temporaries they need are
  * allocated stream-ordered (cudaMallocAsync) and released before return.

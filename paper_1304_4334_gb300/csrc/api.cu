@@ -6,10 +6,8 @@
 // phases (the power reached, RSS) and one after the M phase (acceptance), so
 // the host decides the number of Metropolis iterations exactly as the paper's
 // rules state.
-#include "../../include/smc.h"
-#include "kernels.cuh"
-#include "mala.cuh"
-#include "phase.cuh"
+
+#include "ctx.h"
 
 #include <atomic>
 #include <cmath>
@@ -155,58 +153,6 @@ __global__ void k_init_data_tempering(ModelDev m, const double* __restrict__ the
 }  // namespace smc
 
 using namespace smc;
-
-// ================================================================ context
-struct smc_ctx {
-    smc_model model;
-    smc_config cfg;
-    ModelDev mdev;
-    int T = 0, P = 0, d = 0, ns = 0, W = 1;
-    cudaStream_t stream = nullptr;
-    // observations
-    void* obs = nullptr;             // float[T] (FP32 EGARCH) or double[T*W]
-    // particles, double-buffered for the S-phase gather
-    double* theta[2] = {nullptr, nullptr};
-    double* ll[2] = {nullptr, nullptr};
-    double* lp[2] = {nullptr, nullptr};
-    double* state[2] = {nullptr, nullptr};
-    double* grad[2] = {nullptr, nullptr};  // MALA: likelihood gradient [d][P]
-    void* ckpt = nullptr;                  // MALA: recursion checkpoints
-    int cur = 0;
-    double* thp = nullptr;           // proposal scratch [d][P]
-    double* logw = nullptr;          // [P] data tempering log weights
-    double* g = nullptr;             // [3][P] test functions
-    // per-group estimators
-    double* a = nullptr;             // [J]
-    double* lw = nullptr;            // [J]
-    double* gstat = nullptr;         // [J][3]
-    int32_t* idx = nullptr;          // [P]
-    double* cov_part = nullptr;
-    int cov_G = 0;
-    double* search_part = nullptr;
-    double* cd_part = nullptr;       // [G][kCdataChunk][3] data-tempering statistics
-    double* mom_part = nullptr;      // [nf][J][2]
-    double* mom_out = nullptr;       // [nf][4]
-    double* ml_out = nullptr;        // [3]
-    double* L = nullptr;             // [d][d]
-    double** gather_ptrs = nullptr;  // [2][nrows] device row-pointer tables
-    int gather_rows = 0;
-    Ctl* ctl = nullptr;
-    Ctl* ctl_host = nullptr;         // pinned
-    // run state
-    int cycle = 0, t_prev = 0, done = 0;
-    double phi = 0.0;
-    int64_t msteps = 0;
-    double evals = 0.0;
-    uint64_t h2d = 0, d2h = 0;
-    // profiling
-    int profile = 0;
-    double mutate_ms = 0.0;
-    uint64_t mutate_launches = 0;
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
-    std::string err;
-};
 
 static smc_status set_err(smc_ctx* c, smc_status st, const char* fmt, ...)
 {
@@ -595,6 +541,77 @@ static smc_status s_phase(smc_ctx* ctx, int mode)
 
 static smc_status start_run(smc_ctx* ctx, const double* theta0, int theta0_on_device);
 
+// ------------------------------------------------------------ driver steps
+smc_status smc_internal_enqueue_cs(smc_ctx* ctx)
+{
+    const smc_config& c = ctx->cfg;
+    ctx->cycle += 1;
+    // C phase: next power by k-ary bisection on RSS
+    CU(launch_power_search(ctx->ll[ctx->cur], ctx->P, c.d1, c.search_passes, ctx->search_part, ctx->ctl,
+                           ctx->stream));
+    // S phase (weights dphi * l_n), then pooled RSS, log wtilde and phi
+    smc_status st = s_phase(ctx, 0);
+    if (st != SMC_OK) return st;
+    CU(launch_cycle_close(ctx->gstat, ctx->lw, c.J, c.N, 1, ctx->ctl, ctx->stream));
+    return SMC_OK;
+}
+
+smc_status smc_internal_enqueue_ctl_readback(smc_ctx* ctx)
+{
+    CU(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->d2h += sizeof(Ctl);
+    return SMC_OK;
+}
+
+smc_status smc_internal_check(smc_ctx* ctx) { return check_device_error(ctx); }
+
+void smc_internal_after_cs(smc_ctx* ctx, double* rss, int* forced)
+{
+    ctx->phi = ctx->ctl_host->phi;
+    *rss = ctx->ctl_host->rss;
+    *forced = ctx->ctl_host->last;
+}
+
+int smc_internal_R(const smc_ctx* ctx, double rss)
+{
+    const smc_config& c = ctx->cfg;
+    return c.stop_rule == SMC_STOP_DET ? (rss < c.d2 ? c.kappa * c.rbar : c.rbar) : c.rmax;
+}
+
+smc_status smc_internal_enqueue_adapt(smc_ctx* ctx)
+{
+    const smc_config& c = ctx->cfg;
+    CU(launch_adapt_h(ctx->ctl, ctx->P, c.acc_target, c.hmin_tenths, c.hmax_tenths, ctx->stream));
+    return SMC_OK;
+}
+
+smc_status smc_internal_after_m(smc_ctx* ctx, int t_l, int R, int Tm, double phim, double rss,
+                                smc_cycle_info* info)
+{
+    const smc_config& c = ctx->cfg;
+    const int P = ctx->P;
+    if (ctx->profile) {
+        smc_status st = fold_profile(ctx);
+        if (st != SMC_OK) return st;
+    }
+    ctx->t_prev = t_l;
+    ctx->msteps += R;
+    ctx->evals += (double)R * (double)P * (double)Tm;
+    if (c.tempering == SMC_POWER ? ctx->ctl_host->last : (t_l >= ctx->T)) ctx->done = 1;
+    if (info) {
+        info->cycle = ctx->cycle;
+        info->t = t_l;
+        info->phi = phim;
+        info->rss = rss;
+        info->R = R;
+        info->h_tenths = ctx->ctl_host->h_tenths;
+        info->acc_rate = ctx->ctl_host->acc_n ? ctx->ctl_host->acc_sum / ctx->ctl_host->acc_n : 0.0;
+        info->evals = (double)R * (double)P * (double)Tm;
+        info->done = ctx->done;
+    }
+    return SMC_OK;
+}
+
 extern "C" {
 
 smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, const double* X,
@@ -855,24 +872,17 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
     if (ctx->done) return set_err(ctx, SMC_EDONE, "the run has reached the full posterior");
     const smc_config& c = ctx->cfg;
     const int P = ctx->P;
-    ctx->cycle += 1;
+    if (c.tempering != SMC_POWER) ctx->cycle += 1;
     int t_l = ctx->T;
     double rss = 1.0;
     int forced = 0;
     smc_status st;
     if (c.tempering == SMC_POWER) {
-        // ---- C phase: next power by k-ary bisection on RSS ----
-        CU(launch_power_search(ctx->ll[ctx->cur], P, c.d1, c.search_passes, ctx->search_part, ctx->ctl,
-                               ctx->stream));
-        // ---- S phase (weights dphi * l_n) ----
-        st = s_phase(ctx, 0);
+        st = smc_internal_enqueue_cs(ctx);
         if (st != SMC_OK) return st;
-        CU(launch_cycle_close(ctx->gstat, ctx->lw, c.J, c.N, 1, ctx->ctl, ctx->stream));
         st = sync_ctl(ctx);
         if (st != SMC_OK) return st;
-        ctx->phi = ctx->ctl_host->phi;
-        rss = ctx->ctl_host->rss;
-        forced = ctx->ctl_host->last;
+        smc_internal_after_cs(ctx, &rss, &forced);
     } else {
         // ---- C phase: add observations until RSS < D1 (Algorithm 1, 2(a)) ----
         CU(cudaMemsetAsync(ctx->logw, 0, (size_t)P * sizeof(double), ctx->stream));
@@ -929,7 +939,7 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
         st = refresh_gradient(ctx, Tm);
         if (st != SMC_OK) return st;
     }
-    int R = c.stop_rule == SMC_STOP_DET ? (rss < c.d2 ? c.kappa * c.rbar : c.rbar) : c.rmax;
+    const int R = smc_internal_R(ctx, rss);
     const double E = forced ? c.e2 : c.e1;
     int r = 0;
     for (; r < R; ++r) {
@@ -946,29 +956,11 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
             }
         }
     }
-    CU(launch_adapt_h(ctx->ctl, P, c.acc_target, c.hmin_tenths, c.hmax_tenths, ctx->stream));
+    st = smc_internal_enqueue_adapt(ctx);
+    if (st != SMC_OK) return st;
     st = sync_ctl(ctx);
     if (st != SMC_OK) return st;
-    if (ctx->profile) {
-        st = fold_profile(ctx);
-        if (st != SMC_OK) return st;
-    }
-    ctx->t_prev = t_l;
-    ctx->msteps += r;
-    ctx->evals += (double)r * (double)P * (double)Tm;
-    if (c.tempering == SMC_POWER ? ctx->ctl_host->last : (t_l >= ctx->T)) ctx->done = 1;
-    if (info) {
-        info->cycle = ctx->cycle;
-        info->t = t_l;
-        info->phi = phim;
-        info->rss = rss;
-        info->R = r;
-        info->h_tenths = ctx->ctl_host->h_tenths;
-        info->acc_rate = ctx->ctl_host->acc_n ? ctx->ctl_host->acc_sum / ctx->ctl_host->acc_n : 0.0;
-        info->evals = (double)r * (double)P * (double)Tm;
-        info->done = ctx->done;
-    }
-    return SMC_OK;
+    return smc_internal_after_m(ctx, t_l, r, Tm, phim, rss, info);
 }
 
 smc_status smc_run(smc_ctx* ctx, int max_cycles, smc_cycle_info* info, int* ncycles)

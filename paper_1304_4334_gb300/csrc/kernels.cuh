@@ -115,26 +115,33 @@ __device__ __forceinline__ double tempered_target(double lp, double ll, double p
     return phi > 0.0 ? lp + phi * ll : lp;
 }
 
+// Shared memory of one mutation tile.
 template <class Pol>
-__global__ void __launch_bounds__(kMutThreads) k_mutate(MutateArgs a)
+struct MutateSmem {
+    __align__(16) typename Pol::Obs obuf[2 * Pol::kChunk];
+    __align__(8) uint64_t bars[2];
+    typename Pol::Real Ls[kMaxD * kMaxD];
+    unsigned int acc_s;
+};
+
+// One block's tile of particles p0 + threadIdx.x: proposal, likelihood
+// recursion over the staged observations, Metropolis-Hastings decision.
+// Every thread of the block must call it (block barriers inside).
+template <class Pol>
+__device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, int p0, MutateSmem<Pol>& sm)
 {
     using Real = typename Pol::Real;
     using Obs = typename Pol::Obs;
-    __shared__ __align__(16) Obs obuf[2 * Pol::kChunk];
-    __shared__ __align__(8) uint64_t bars[2];
-    __shared__ Real Ls[kMaxD * kMaxD];
-    __shared__ unsigned int acc_s;
-
     const int d = a.m.d;
-    for (int i = threadIdx.x; i < d * d; i += blockDim.x) Ls[i] = (Real)a.L[i];
-    if (threadIdx.x == 0) acc_s = 0;
+    for (int i = threadIdx.x; i < d * d; i += blockDim.x) sm.Ls[i] = (Real)a.L[i];
+    if (threadIdx.x == 0) sm.acc_s = 0;
 
     const int64_t nelem = (int64_t)a.T * a.W;
-    ObsPipe<Obs, Pol::kChunk> pipe{obuf, bars, (const Obs*)a.obs, nelem,
+    ObsPipe<Obs, Pol::kChunk> pipe{sm.obuf, sm.bars, (const Obs*)a.obs, nelem,
                                    (int)((nelem + Pol::kChunk - 1) / Pol::kChunk)};
     pipe.start();   // contains a block barrier: Ls and acc_s are visible below
 
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = p0 + (int)threadIdx.x;
     const bool active = p < a.P;
     const int pp = active ? p : a.P - 1;
     const size_t P = (size_t)a.P;
@@ -143,10 +150,10 @@ __global__ void __launch_bounds__(kMutThreads) k_mutate(MutateArgs a)
     double thn[kMaxD];
     {
         Real z[kMaxD];
-        proposal_normals<Real>(a.seed, (uint64_t)pp, a.iter, a.cycle, d, z);
+        proposal_normals<Real>(a.seed, (uint64_t)pp, iter, a.cycle, d, z);
         for (int i = 0; i < d; ++i) {
             Real s = 0;
-            for (int k = 0; k <= i; ++k) s += Ls[i * d + k] * z[k];
+            for (int k = 0; k <= i; ++k) s += sm.Ls[i * d + k] * z[k];
             thn[i] = a.theta[i * P + pp] + (double)s;
             if (active) a.thp[i * P + p] = thn[i];
         }
@@ -167,7 +174,7 @@ __global__ void __launch_bounds__(kMutThreads) k_mutate(MutateArgs a)
     if (active) {
         const double log_alpha = tempered_target(lp_new, ll_new, a.phi) -
                                  tempered_target(a.lp[p], a.ll[p], a.phi);
-        const double log_u = log_uniform_mh(a.seed, (uint64_t)p, a.iter, a.cycle);
+        const double log_u = log_uniform_mh(a.seed, (uint64_t)p, iter, a.cycle);
         acc = log_u < log_alpha;
         if (acc) {
             for (int i = 0; i < d; ++i) a.theta[i * P + p] = a.thp[i * P + p];
@@ -181,10 +188,18 @@ __global__ void __launch_bounds__(kMutThreads) k_mutate(MutateArgs a)
         }
     }
     const unsigned int nacc = __popc(__ballot_sync(0xffffffffu, acc));
-    if ((threadIdx.x & 31) == 0 && nacc) atomicAdd(&acc_s, nacc);
+    if ((threadIdx.x & 31) == 0 && nacc) atomicAdd(&sm.acc_s, nacc);
     __syncthreads();
-    if (threadIdx.x == 0 && acc_s) atomicAdd(a.acc_count, (unsigned long long)acc_s);
-    if (blockIdx.x == 0 && threadIdx.x == 0 && a.pending) *a.pending = 1;
+    if (threadIdx.x == 0 && sm.acc_s) atomicAdd(a.acc_count, (unsigned long long)sm.acc_s);
+    if (p0 == 0 && threadIdx.x == 0 && a.pending) *a.pending = 1;
+    pipe.finish();
+}
+
+template <class Pol>
+__global__ void __launch_bounds__(kMutThreads) k_mutate(MutateArgs a)
+{
+    __shared__ MutateSmem<Pol> sm;
+    mutate_tile<Pol>(a, a.iter, blockIdx.x * blockDim.x, sm);
 }
 
 template <class Pol>

@@ -226,7 +226,7 @@ cudaError_t launch_grad_t(const GradArgs& a, cudaStream_t s)
 {
     const size_t sm = GP::smem_bytes(kMalaThreads);
     static bool attr = false;
-    if (!attr && sm > 48 * 1024) {
+    if (!attr && sm > 0) {   // static + dynamic shared memory may pass the 48 KB default
         cudaFuncSetAttribute(k_loglik_grad<GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         attr = true;
     }
@@ -239,7 +239,7 @@ cudaError_t launch_mala_t(const MalaArgs& a, cudaStream_t s)
 {
     const size_t sm = GP::smem_bytes(kMalaThreads);
     static bool attr = false;
-    if (!attr && sm > 48 * 1024) {
+    if (!attr && sm > 0) {   // static + dynamic shared memory may pass the 48 KB default
         cudaFuncSetAttribute(k_mutate_mala<GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         attr = true;
     }

@@ -48,8 +48,8 @@ __device__ __forceinline__ void unpack_pair(int e, int& i, int& k)
     k = e - ii * (ii + 1) / 2;
 }
 
-__global__ void __launch_bounds__(kCovThreads) k_cov_partial(const double* __restrict__ theta, int d,
-                                                            int P, double* __restrict__ part)
+__device__ void cov_partial_body(const double* __restrict__ theta, int d, int P,
+                                 double* __restrict__ part, int bidx, int G)
 {
     __shared__ float tile[kMaxD][kCovTile + 1];
     __shared__ double shift[kMaxD];
@@ -62,8 +62,8 @@ __global__ void __launch_bounds__(kCovThreads) k_cov_partial(const double* __res
     double acc[kCovMaxAcc];
 #pragma unroll
     for (int r = 0; r < kCovMaxAcc; ++r) acc[r] = 0.0;
-    const int per = (P + gridDim.x - 1) / gridDim.x;
-    const int n0 = blockIdx.x * per;
+    const int per = (P + G - 1) / G;
+    const int n0 = bidx * per;
     const int n1 = min(P, n0 + per);
     __syncthreads();
     for (int base = n0; base < n1; base += kCovTile) {
@@ -92,8 +92,14 @@ __global__ void __launch_bounds__(kCovThreads) k_cov_partial(const double* __res
 #pragma unroll
     for (int r = 0; r < kCovMaxAcc; ++r) {
         const int e = threadIdx.x + r * blockDim.x;
-        if (e < nacc) part[(size_t)blockIdx.x * nacc + e] = acc[r];
+        if (e < nacc) part[(size_t)bidx * nacc + e] = acc[r];
     }
+}
+
+__global__ void __launch_bounds__(kCovThreads) k_cov_partial(const double* __restrict__ theta, int d,
+                                                            int P, double* __restrict__ part)
+{
+    cov_partial_body(theta, d, P, part, blockIdx.x, gridDim.x);
 }
 
 __device__ void apply_h_update(Ctl* ctl, int P, double target, int hmin, int hmax)
@@ -117,25 +123,27 @@ __global__ void k_adapt_h(Ctl* ctl, int P, double target, int hmin, int hmax)
 
 // Sum of the G block partials of each accumulator entry: one block per entry,
 // fixed combination order.  Result in part[G * nacc + e].
-__global__ void __launch_bounds__(128) k_cov_combine(double* part, int G, int nacc)
+__device__ void cov_combine_body(double* part, int G, int nacc, int e)
 {
     __shared__ double red[32];
-    const int e = blockIdx.x;
     double s = 0.0;
     for (int g = threadIdx.x; g < G; g += blockDim.x) s += part[(size_t)g * nacc + e];
     s = block_sum(s, red);
     if (threadIdx.x == 0) part[(size_t)G * nacc + e] = s;
 }
 
+__global__ void __launch_bounds__(128) k_cov_combine(double* part, int G, int nacc)
+{
+    cov_combine_body(part, G, nacc, blockIdx.x);
+}
+
 // Combines the partial sums, updates h from the previous iteration's
 // acceptance (when a control block is given) and factors Sigma = h^2 V by a
 // right-looking Cholesky in shared memory; a non-positive pivot zeroes its
 // column, as in the oracle.
-__global__ void __launch_bounds__(kCovThreads) k_cov_final(const double* __restrict__ part, int G, int d,
-                                                          int P, const double* __restrict__ theta,
-                                                          Ctl* ctl, int fixed_h, double target,
-                                                          int hmin, int hmax, double* mean_out,
-                                                          double* cov_out, double* L_out)
+__device__ void cov_final_body(const double* __restrict__ part, int G, int d, int P,
+                               const double* __restrict__ theta, Ctl* ctl, int fixed_h, double target,
+                               int hmin, int hmax, double* mean_out, double* cov_out, double* L_out)
 {
     __shared__ double S1[kMaxD];
     __shared__ double A[kMaxD][kMaxD + 1];
@@ -195,6 +203,50 @@ __global__ void __launch_bounds__(kCovThreads) k_cov_final(const double* __restr
             const int i = e / d, k = e % d;
             L_out[e] = k <= i ? A[i][k] : 0.0;
         }
+}
+
+__global__ void __launch_bounds__(kCovThreads) k_cov_final(const double* __restrict__ part, int G, int d,
+                                                          int P, const double* __restrict__ theta,
+                                                          Ctl* ctl, int fixed_h, double target,
+                                                          int hmin, int hmax, double* mean_out,
+                                                          double* cov_out, double* L_out)
+{
+    cov_final_body(part, G, d, P, theta, ctl, fixed_h, target, hmin, hmax, mean_out, cov_out, L_out);
+}
+
+// ----- batched covariance: one launch per stage for many particle sets -----
+__global__ void __launch_bounds__(kCovThreads) k_cov_partial_batch(const CovJob* __restrict__ jobs,
+                                                                  const int* iter)
+{
+    const CovJob& j = jobs[blockIdx.y];
+    if ((int)blockIdx.x >= j.G || *iter >= j.R) return;
+    cov_partial_body(j.theta, j.d, j.P, j.part, blockIdx.x, j.G);
+}
+
+__global__ void __launch_bounds__(128) k_cov_combine_batch(const CovJob* __restrict__ jobs, const int* iter)
+{
+    const CovJob& j = jobs[blockIdx.y];
+    const int nacc = j.d + j.d * (j.d + 1) / 2;
+    if ((int)blockIdx.x >= nacc || *iter >= j.R) return;
+    cov_combine_body(j.part, j.G, nacc, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kCovThreads) k_cov_final_batch(const CovJob* __restrict__ jobs, const int* iter)
+{
+    const CovJob& j = jobs[blockIdx.x];
+    if (*iter >= j.R) return;
+    cov_final_body(j.part, j.G, j.d, j.P, j.theta, j.ctl, 0, j.target, j.hmin, j.hmax, nullptr, nullptr, j.L);
+}
+
+cudaError_t launch_cov_batch(const CovJob* jobs, int n, int Gmax, int dmax, const int* iter, cudaStream_t s)
+{
+    k_cov_partial_batch<<<dim3(Gmax, n), kCovThreads, 0, s>>>(jobs, iter);
+    count_launch();
+    k_cov_combine_batch<<<dim3(dmax + dmax * (dmax + 1) / 2, n), 128, 0, s>>>(jobs, iter);
+    count_launch();
+    k_cov_final_batch<<<n, kCovThreads, 0, s>>>(jobs, iter);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cov(const double* theta, int d, int P, double* part, int G, Ctl* ctl,

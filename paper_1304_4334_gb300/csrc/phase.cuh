@@ -38,6 +38,21 @@ int cov_grid(int P);
 cudaError_t launch_cov(const double* theta, int d, int P, double* part, int G, Ctl* ctl,
                        int fixed_h_tenths, double acc_target, int hmin, int hmax, double* mean,
                        double* cov, double* L, cudaStream_t s);
+// Batched form: one covariance job per particle set, skipped once the
+// device iteration counter reaches the job's iteration count R.
+struct CovJob {
+    const double* theta;
+    int d, P;
+    double* part;     // (G + 1) x (d + d(d+1)/2)
+    int G;
+    Ctl* ctl;
+    double* L;
+    double target;
+    int hmin, hmax;
+    int R;
+};
+cudaError_t launch_cov_batch(const CovJob* jobs, int n, int Gmax, int dmax, const int* iter, cudaStream_t s);
+
 // Applies a pending acceptance count to h (end of an M phase).
 cudaError_t launch_adapt_h(Ctl* ctl, int P, double acc_target, int hmin, int hmax, cudaStream_t s);
 

@@ -472,6 +472,18 @@ struct ObsPipe {
         }
     }
 
+    // Block-collective end of use: invalidates the barriers so that the same
+    // shared memory can host a new pipeline (persistent kernels).
+    __device__ __forceinline__ void finish()
+    {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(&bar[0])) : "memory");
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(&bar[1])) : "memory");
+        }
+        __syncthreads();
+    }
+
     // After an abandoned wait: give chunks still in flight a bounded chance to
     // land before the block exits.
     __device__ __forceinline__ void drain(int c)

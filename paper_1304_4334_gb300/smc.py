@@ -94,6 +94,20 @@ def _declare(L):
     L.smc_transfer_bytes.argtypes = [vp, P(C.c_uint64), P(C.c_uint64)]
     L.smc_free.argtypes = [vp]
     L.smc_free.restype = None
+    L.smc_batch_init.argtypes = [C.c_int, P(smc_model), P(smc_config), P(dp), P(C.c_int), P(dp), vp, P(vp)]
+    L.smc_batch_autotune.argtypes = [vp, C.c_int, dp]
+    L.smc_batch_cycle.argtypes = [vp, P(C.c_int)]
+    L.smc_batch_run.argtypes = [vp, C.c_int, P(C.c_int)]
+    L.smc_batch_reset.argtypes = [vp, P(dp), C.c_int, C.c_uint64]
+    L.smc_batch_totals.argtypes = [vp, dp, P(C.c_int64), P(C.c_int)]
+    L.smc_batch_member.argtypes = [vp, C.c_int]
+    L.smc_batch_member.restype = vp
+    L.smc_batch_tile.argtypes = [vp]
+    L.smc_batch_tile.restype = C.c_int
+    L.smc_batch_last_error.argtypes = [vp]
+    L.smc_batch_last_error.restype = C.c_char_p
+    L.smc_batch_free.argtypes = [vp]
+    L.smc_batch_free.restype = None
     L.smc_last_error.argtypes = [vp]
     L.smc_last_error.restype = C.c_char_p
     L.smc_status_str.argtypes = [C.c_int]
@@ -291,6 +305,97 @@ class Ctx:
     def close(self):
         if getattr(self, "h", None):
             lib().smc_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _MemberView(Ctx):
+    """A batch member's context (owned by the batch: close() does nothing)."""
+
+    def __init__(self, handle, model, cfg):
+        self.h = handle
+        self.model, self.cfg = model, cfg
+        self.d = model.d
+        self.P = cfg.J * cfg.N
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """Many runs advanced together (wraps smc_batch)."""
+
+    def __init__(self, models, cfgs, ys, theta0s, stream=None):
+        n = len(models)
+        self.models, self.cfgs = list(models), list(cfgs)
+        self._ys = [_f64(y) for y in ys]
+        self._th = [_f64(t) for t in theta0s]
+        M = (smc_model * n)(*self.models)
+        Cf = (smc_config * n)(*self.cfgs)
+        Y = (dp * n)(*[_dptr(y) for y in self._ys])
+        Ts = (C.c_int * n)(*[len(y) for y in self._ys])
+        TH = (dp * n)(*[_dptr(t) for t in self._th])
+        self._keep = (M, Cf, Y, Ts, TH)
+        h = C.c_void_p()
+        st = lib().smc_batch_init(n, M, Cf, Y, Ts, TH, _stream(stream), C.byref(h))
+        self.h = h
+        self.n = n
+        if st != OK:
+            msg = lib().smc_batch_last_error(h).decode() if h else ""
+            self.close()
+            raise SMCError(st, msg)
+
+    def _chk(self, st):
+        if st != OK:
+            raise SMCError(st, lib().smc_batch_last_error(self.h).decode())
+
+    def autotune(self, iters=2):
+        ms = C.c_double()
+        self._chk(lib().smc_batch_autotune(self.h, iters, C.byref(ms)))
+        return ms.value
+
+    @property
+    def tile(self):
+        return lib().smc_batch_tile(self.h)
+
+    def cycle(self):
+        n = C.c_int()
+        st = lib().smc_batch_cycle(self.h, C.byref(n))
+        if st == EDONE:
+            return None
+        self._chk(st)
+        return n.value
+
+    def run(self, max_cycles=0):
+        n = C.c_int()
+        self._chk(lib().smc_batch_run(self.h, max_cycles, C.byref(n)))
+        return n.value
+
+    def reset(self, theta0s, seed, on_device=True):
+        if on_device:
+            ptrs = [C.cast(C.c_void_p(t.data_ptr()), dp) for t in theta0s]
+        else:
+            self._th = [_f64(t) for t in theta0s]
+            ptrs = [_dptr(t) for t in self._th]
+        arr = (dp * self.n)(*ptrs)
+        self._chk(lib().smc_batch_reset(self.h, arr, int(bool(on_device)), seed))
+
+    def totals(self):
+        e, ms, cy = C.c_double(), C.c_int64(), C.c_int()
+        self._chk(lib().smc_batch_totals(self.h, C.byref(e), C.byref(ms), C.byref(cy)))
+        return e.value, ms.value, cy.value
+
+    def member(self, i):
+        return _MemberView(lib().smc_batch_member(self.h, i), self.models[i], self.cfgs[i])
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().smc_batch_free(self.h)
             self.h = None
 
     def __del__(self):
