@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cycles", type=int, default=0, help="cap on cycles per run (0 = full run; profiling only)")
+    ap.add_argument("--no-equal-nse", action="store_true")
+    ap.add_argument("--equal-nse-seeds", type=int, default=3)
     return ap.parse_args()
 
 
@@ -205,6 +207,46 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------- wall time at equal NSE
+def equal_nse_comparison(S, w, y, th0, stream, seeds):
+    """The paper's efficiency measure, precision / time = 1 / (NSE^2 t)
+    (Section 5.2, Table 3), for the log marginal likelihood: whole runs of the
+    plain FP64 random-walk form against the FP32 random-walk and FP32 MALA
+    forms on the same GPU, same data and prior draws.  Reported per form: mean
+    run time, mean NSE^2, and the wall time it needs to reach the FP64
+    random-walk form's NSE (t * NSE^2 / NSE_ref^2), relative to that form."""
+    import torch
+    m = S.model_egarch(w.K, w.I, w.gamma)
+    forms = [("fp64_rw", S.FP64, S.RW, 0.25), ("fp32_rw", S.FP32, S.RW, 0.25),
+             ("fp32_mala", S.FP32, S.MALA, 0.5)]
+    out = {}
+    for name, prec, mut, target in forms:
+        ts, nse2, lml = [], [], []
+        for k in range(seeds):
+            cfg = S.config_default(J=w.J, N=w.N, precision=prec, mutation=mut, acc_target=target,
+                                   rbar=w.rbar, kappa=w.kappa, seed=500 + k)
+            ctx = S.init(m, cfg, y, th0, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.run()
+            lm, nse, _ = ctx.log_ml()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ctx.close()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+            nse2.append(nse * nse)
+            lml.append(lm)
+        out[name] = {"seconds": statistics.mean(ts), "nse2": statistics.mean(nse2),
+                     "log_ml": statistics.mean(lml), "runs": seeds}
+    ref = out["fp64_rw"]
+    for v in out.values():
+        v["wall_time_at_ref_nse_rel"] = (v["seconds"] * v["nse2"] / ref["nse2"]) / ref["seconds"]
+        v["precision_per_second"] = 1.0 / (v["nse2"] * v["seconds"])
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -329,6 +371,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_rate(w, y)
+    eq = None
+    if rank == 0 and not args.no_equal_nse and args.cycles == 0:
+        eq = equal_nse_comparison(S, w, y, th0, stream, args.equal_nse_seeds)
 
     if rank == 0:
         line = {"metric": "M-phase particle*obs lik evals/s", "value": value,
@@ -343,7 +388,7 @@ def main():
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                 "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
                 "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
-                "wall_s": wall}
+                "equal_nse": eq, "wall_s": wall}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
