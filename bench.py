@@ -276,7 +276,9 @@ def main():
     mean, sd, lo = S.model_prior(m)
     th0 = I.draw_prior(mean, sd, lo, w.P, seed=w.prior_seed + 1000 * rank)
     prec = S.FP32 if w.precision == "f32" else S.FP64
-    cfg = S.config_default(J=w.J, N=w.N, precision=prec, rbar=w.rbar, kappa=w.kappa, seed=1 + rank)
+    mala = w.mutation == "mala"
+    cfg = S.config_default(J=w.J, N=w.N, precision=prec, rbar=w.rbar, kappa=w.kappa, seed=1 + rank,
+                           mutation=S.MALA if mala else S.RW, acc_target=0.5 if mala else 0.25)
     stream = torch.cuda.Stream()
     th0_dev = torch.as_tensor(np.ascontiguousarray(th0.T), device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -360,10 +362,13 @@ def main():
     avg_launch_s = (mut_ms / mut_n) / 1e3 if mut_n else float("nan")
     achieved = w.P * w.T / avg_launch_s if mut_n else float("nan")
     fp32_ops, mufu_ops = alu_ops_per_eval(w.K, w.I, w.gamma)
+    # For MALA the kernel also recomputes and reverses the recursion; its frac is
+    # stated against the forward recursion's bound (likelihood evaluations/s).
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
             "frac": achieved / peak, "traffic": None, "pipe": pipe, "peak_source": f"{src} SM clock {mhz:.0f} MHz x {SM_COUNT_GB300} SMs",
             "ops_per_eval": {"fp32": fp32_ops, "mufu": mufu_ops},
-            "kernel": "k_mutate<PolicyEgarchF32<2,2>>", "avg_launch_ms": avg_launch_s * 1e3,
+            "kernel": (f"k_mutate_mala<GradEgarch<float,{w.K},{w.I}>>" if mala
+                       else f"k_mutate<PolicyEgarchF32<{w.K},{w.I}>>"), "avg_launch_ms": avg_launch_s * 1e3,
             "launches": mut_n, "share_of_step": (mut_ms / 1e3) / t_total if t_total else None}
     if clk.get("sm_mhz"):
         roof["frac_at_median_clock"] = achieved / alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, clk["sm_mhz"])[0]
@@ -372,7 +377,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_rate(w, y)
     eq = None
-    if rank == 0 and not args.no_equal_nse and args.cycles == 0:
+    if rank == 0 and not args.no_equal_nse and args.cycles == 0 and w.name == "egarch22_T5000":
         eq = equal_nse_comparison(S, w, y, th0, stream, args.equal_nse_seeds)
 
     if rank == 0:
@@ -383,7 +388,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": w.name, "K": w.K, "I": w.I, "T": w.T, "J": w.J, "N": w.N,
                            "precision": "fp32 recursion, fp64 accumulators", "tempering": "power",
-                           "sampler": "rw", "stop_rule": f"deterministic Rbar={w.rbar} kappa={w.kappa}",
+                           "sampler": w.mutation, "stop_rule": f"deterministic Rbar={w.rbar} kappa={w.kappa}",
                            "cycles_per_run": cycles, "metropolis_steps_per_run": msteps,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
                 "clocks": {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
