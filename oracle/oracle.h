@@ -166,6 +166,19 @@ typedef struct {
     uint64_t seed;
     int max_cycles;
     int nthreads;
+    /* Algorithm 3 (hybrid).  Recording (rec_L non-NULL, capacity rec_L_cap
+     * iterations): the Cholesky factor of every Metropolis iteration's
+     * Sigma_lr is stored, d*d each, in order.  Replay (replay = 1): cycle l ends
+     * at design_x[l] (t_l in data tempering, phi_l in power tempering), runs
+     * design_R[l] iterations with the stored factors design_L in order; no
+     * adaptation.  n_design cycles. */
+    int replay;
+    int n_design;
+    const double *design_x;
+    const int *design_R;
+    const double *design_L;
+    double *rec_L;
+    int rec_L_cap;
 } or_run_cfg;
 
 typedef struct {

@@ -72,7 +72,9 @@ class RunCfg(C.Structure):
                 ("hmin_tenths", C.c_int), ("hmax_tenths", C.c_int), ("acc_target", C.c_double),
                 ("h_reset_each_cycle", C.c_int), ("force_dates", ip), ("n_force", C.c_int),
                 ("bisect_iters", C.c_int), ("seed", C.c_uint64), ("max_cycles", C.c_int),
-                ("nthreads", C.c_int)]
+                ("nthreads", C.c_int), ("replay", C.c_int), ("n_design", C.c_int),
+                ("design_x", dp), ("design_R", ip), ("design_L", dp), ("rec_L", dp),
+                ("rec_L_cap", C.c_int)]
 
 
 class RunOut(C.Structure):
@@ -375,16 +377,30 @@ DEFAULT_RUN = dict(tempering=1, mutation=0, resid=1, d1=0.5, d2=0.2, stop_rule=0
                    seed=1, max_cycles=10000, nthreads=1)
 
 
-def smc_run(spec, y, theta0, J, N, X=None, force_dates=(), **kw):
-    """Full adaptive run (Algorithm 2 with the Section 3.3 specifics)."""
+def smc_run(spec, y, theta0, J, N, X=None, force_dates=(), design=None, record=False, **kw):
+    """Full adaptive run (Algorithm 2 with the Section 3.3 specifics).
+
+    record=True also returns the design of Algorithm 3 (end of each cycle, its
+    iteration count and every iteration's proposal Cholesky factor);
+    design=<that dict> replays it non-adaptively (Algorithm 3, step 2)."""
     o = dict(DEFAULT_RUN)
     o.update(kw)
     fd = np.ascontiguousarray(force_dates, dtype=np.int32)
+    cap = 20000
+    rec_L = np.zeros((cap, spec.d, spec.d)) if record else None
+    if design is not None:
+        dx = np.ascontiguousarray(design["x"], dtype=np.float64)
+        dR = np.ascontiguousarray(design["R"], dtype=np.int32)
+        dL = np.ascontiguousarray(design["L"], dtype=np.float64)
+        rep = (1, len(dx), dx.ctypes.data_as(dp), dR.ctypes.data_as(ip), dL.ctypes.data_as(dp))
+    else:
+        rep = (0, 0, None, None, None)
     cfg = RunCfg(J, N, o["tempering"], o["mutation"], o["resid"], o["d1"], o["d2"],
                  o["stop_rule"], o["rbar"], o["kappa"], o["rmax"], o["e1"], o["e2"],
                  o["h0_tenths"], o["hmin_tenths"], o["hmax_tenths"], o["acc_target"],
                  o["h_reset_each_cycle"], fd.ctypes.data_as(ip) if len(fd) else None, len(fd),
-                 o["bisect_iters"], o["seed"], o["max_cycles"], o["nthreads"])
+                 o["bisect_iters"], o["seed"], o["max_cycles"], o["nthreads"], *rep,
+                 rec_L.ctypes.data_as(dp) if record else None, cap if record else 0)
     P = J * N
     theta0 = _f64(theta0)
     assert theta0.shape == (P, spec.d)
@@ -401,7 +417,11 @@ def smc_run(spec, y, theta0, J, N, X=None, force_dates=(), **kw):
                        t_rec.ctypes.data_as(ip), _d(phi_rec), r_rec.ctypes.data_as(ip),
                        _d(rss_rec), C.byref(out))
     L = out.cycles
-    return dict(status=out.status, cycles=L, metropolis_steps=out.metropolis_steps,
+    res_design = None
+    if record:
+        x = phi_rec[:L].copy() if o["tempering"] == 1 else t_rec[:L].astype(np.float64)
+        res_design = dict(x=x, R=r_rec[:L].copy(), L=rec_L[:out.metropolis_steps].copy())
+    return dict(status=out.status, cycles=L, metropolis_steps=out.metropolis_steps, design=res_design,
                 evals=out.particle_obs_evals, log_ml=out.log_ml, log_ml_nse=out.log_ml_nse,
                 log_ml_tilde=out.log_ml_tilde, h_final=out.h_final_tenths, theta=theta,
                 loglik=ll, logprior=lp, state=state, a=a, t=t_rec[:L].copy(),

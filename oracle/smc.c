@@ -470,13 +470,30 @@ int or_smc_run(const or_model *m, const double *y, const double *X, int T,
 
     double phi = 0.0, ltilde = 0.0;
     int t_prev = 0, h = cfg->h0_tenths, l = 0, status = 0;
+    long replay_iter = 0;
     while ((power ? phi < 1.0 : t_prev < T) && l < cfg->max_cycles) {
         ++l;
         double rss = 1.0;
         int t_l = T, forced = 0;
         /* ---- C phase ---- */
         if (power) {
-            double dphi = or_power_search(loglik, P, phi, cfg->d1, cfg->bisect_iters, &rss);
+            double dphi;
+            if (cfg->replay) {
+                if (l > cfg->n_design) { status = -3; break; }
+                dphi = cfg->design_x[l - 1] >= 1.0 ? 1.0 - phi : cfg->design_x[l - 1] - phi;
+                double llmax = -INFINITY;
+                for (int n = 0; n < P; ++n) if (loglik[n] > llmax) llmax = loglik[n];
+                double s1 = 0.0, s2 = 0.0;
+                for (int n = 0; n < P; ++n) {
+                    if (loglik[n] == -INFINITY) continue;
+                    double wv = exp(dphi * (loglik[n] - llmax));
+                    s1 += wv;
+                    s2 += wv * wv;
+                }
+                rss = s1 * s1 / (s2 * P);
+            } else {
+                dphi = or_power_search(loglik, P, phi, cfg->d1, cfg->bisect_iters, &rss);
+            }
             int last = dphi >= 1.0 - phi;
             for (int n = 0; n < P; ++n)
                 logw[n] = loglik[n] == -INFINITY ? -INFINITY : dphi * loglik[n];
@@ -495,6 +512,10 @@ int or_smc_run(const or_model *m, const double *y, const double *X, int T,
                     loglik[n] += inc;
                 }
                 rss = or_ess_log(logw, P) / P;
+                if (cfg->replay) {
+                    if (s >= (int)cfg->design_x[l - 1]) { forced = s == T; break; }
+                    continue;
+                }
                 if (rss < cfg->d1) break;
                 if (s == T || is_forced(cfg, s)) { forced = 1; break; }
             }
@@ -533,15 +554,23 @@ int or_smc_run(const or_model *m, const double *y, const double *X, int T,
                 or_loglik_grad(m, y, X, Tm, theta + (size_t)n * d, grad + (size_t)n * d);
         if (cfg->h_reset_each_cycle) h = cfg->h0_tenths;
         int R;
-        if (cfg->stop_rule == 0) R = rss < cfg->d2 ? cfg->kappa * cfg->rbar : cfg->rbar;
+        if (cfg->replay) R = cfg->design_R[l - 1];
+        else if (cfg->stop_rule == 0) R = rss < cfg->d2 ? cfg->kappa * cfg->rbar : cfg->rbar;
         else R = cfg->rmax;
         const double E = forced ? cfg->e2 : cfg->e1;
         int r;
         for (r = 0; r < R; ++r) {
-            or_mean_cov(theta, P, d, mean, V);
-            double hh = (h / 10.0) * (h / 10.0);
-            for (int i = 0; i < d * d; ++i) Sig[i] = hh * V[i];      /* Sigma = h^2 V */
-            or_cholesky(Sig, d, L);
+            if (cfg->replay) {
+                memcpy(L, cfg->design_L + (size_t)replay_iter * d * d, sizeof(double) * (size_t)d * d);
+                ++replay_iter;
+            } else {
+                or_mean_cov(theta, P, d, mean, V);
+                double hh = (h / 10.0) * (h / 10.0);
+                for (int i = 0; i < d * d; ++i) Sig[i] = hh * V[i];      /* Sigma = h^2 V */
+                or_cholesky(Sig, d, L);
+            }
+            if (cfg->rec_L && out->metropolis_steps < cfg->rec_L_cap)
+                memcpy(cfg->rec_L + (size_t)out->metropolis_steps * d * d, L, sizeof(double) * (size_t)d * d);
             long acc = cfg->mutation == 1
                 ? or_mutate_mala(m, y, X, Tm, theta, loglik, logprior, grad, state, P, L,
                                  phim, cfg->seed, (uint64_t)l, (uint64_t)r, NULL, cfg->nthreads)
@@ -553,7 +582,7 @@ int or_smc_run(const or_model *m, const double *y, const double *X, int T,
             h = rate > cfg->acc_target ? h + 1 : h - 1;
             if (h < cfg->hmin_tenths) h = cfg->hmin_tenths;
             if (h > cfg->hmax_tenths) h = cfg->hmax_tenths;
-            if (cfg->stop_rule == 1 && mean_rne(m, theta, state, J, N, gbuf) >= E) { ++r; break; }
+            if (!cfg->replay && cfg->stop_rule == 1 && mean_rne(m, theta, state, J, N, gbuf) >= E) { ++r; break; }
         }
         if (r_rec) r_rec[l - 1] = r;
         t_prev = t_l;

@@ -301,3 +301,43 @@ def test_resample_large_group_many_residual_draws():
     others = np.delete(c, 5)
     exp_other = N * wt[0] - np.floor(N * wt[0])
     assert abs(others.mean() - (N * wt[0])) < 0.1 + 4 * np.sqrt(exp_other / (N - 1))
+
+
+# ---------------------------------------------------------- Algorithm 3 (hybrid)
+@pytest.mark.parametrize("tempering", [1, 0])
+def test_hybrid_replay_same_seed_reproduces_the_adaptive_run(tempering):
+    """Replaying the recorded design with the same random numbers is the
+    adaptive run itself: same cycle ends, iterations and proposal scales."""
+    spec, X, y, lml, mn, Vn, (m0, s0) = _linreg_problem()
+    J, N = 8, 256
+    th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), J * N, seed=31)
+    a = O.smc_run(spec, y, th0, J, N, X=X, tempering=tempering, seed=9, record=True)
+    dsg = a["design"]
+    assert len(dsg["x"]) == a["cycles"] and dsg["L"].shape[0] == a["metropolis_steps"]
+    b = O.smc_run(spec, y, th0, J, N, X=X, tempering=tempering, seed=9, design=dsg)
+    assert b["cycles"] == a["cycles"] and np.array_equal(b["R"], a["R"])
+    assert b["log_ml"] == pytest.approx(a["log_ml"], abs=1e-9)
+    np.testing.assert_allclose(b["theta"], a["theta"], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("tempering", [1, 0])
+def test_hybrid_second_run_matches_closed_form(tempering):
+    """Algorithm 3: keep the design of an adaptive run, rerun non-adaptively
+    with a new seed; the second run's estimates satisfy Condition 5."""
+    spec, X, y, lml, mn, Vn, (m0, s0) = _linreg_problem()
+    J, N = 8, 512
+    th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), J * N, seed=32)
+    a = O.smc_run(spec, y, th0, J, N, X=X, tempering=tempering, seed=10, record=True)
+    th1 = I.draw_prior(m0, s0, np.full(3, -np.inf), J * N, seed=33)
+    b = O.smc_run(spec, y, th1, J, N, X=X, tempering=tempering, seed=11, design=a["design"])
+    assert b["status"] == 0 and b["cycles"] == a["cycles"]
+    if tempering == 1:
+        np.testing.assert_allclose(b["phi"], a["phi"], rtol=0, atol=1e-12)
+    else:
+        assert np.array_equal(b["t"], a["t"])
+    # J = 8 groups: standardized errors are t(7) (Proposition 1); 4.0 is its
+    # two-sided 99.5% point
+    assert abs(b["log_ml"] - lml) < 4.0 * b["log_ml_nse"] + 0.02
+    for i in range(3):
+        mean, sd, nse, rne = O.moment(b["theta"][:, i], J, N)
+        assert abs(mean - mn[i]) < 4.0 * nse + 1e-4
