@@ -197,6 +197,23 @@ smc_status smc_moments(smc_ctx* ctx, double* out, int* nf);
 smc_status smc_get_particles(smc_ctx* ctx, double* theta, double* loglik, double* logprior,
                              double* state);
 
+/* Algorithm 3 (hybrid).  Step 1 runs the adaptive simulator while recording
+ * its design: for each cycle its end x_l (t_l in data tempering, phi_l in
+ * power tempering) and iteration count R_l, and for each Metropolis iteration
+ * the lower Cholesky factor of Sigma_lr = h^2 V (Section 3.3 lists these as
+ * the design elements to keep).  Step 2 replays that design in a new context
+ * (new prior draws and seed): no RSS search, covariance or step-size
+ * adaptation, so the run is Algorithm 1 with fixed {t_l, lambda_l}.
+ * smc_design_record: call before the first cycle; max_iterations bounds the
+ * number of iterations recorded (device memory d*d doubles each).
+ * smc_design_get: x[ncycles], R[ncycles], L[niterations][d][d] (host,
+ * nullable), sizes from smc_design_size.  smc_design_replay: host arrays of
+ * the same layout; call before the first cycle (random-walk runs only). */
+smc_status smc_design_record(smc_ctx* ctx, int max_iterations);
+smc_status smc_design_size(smc_ctx* ctx, int* ncycles, int* niterations);
+smc_status smc_design_get(smc_ctx* ctx, double* x, int* R, double* L);
+smc_status smc_design_replay(smc_ctx* ctx, int ncycles, const double* x, const int* R, const double* L);
+
 /* Number of kernel launches this library has issued in this process. */
 uint64_t smc_launch_count(void);
 

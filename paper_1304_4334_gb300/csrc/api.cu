@@ -330,7 +330,7 @@ static void release(smc_ctx* c)
 {
     if (!c) return;
     void* ptrs[] = {c->obs, c->theta[0], c->theta[1], c->ll[0], c->ll[1], c->lp[0], c->lp[1],
-                    c->grad[0], c->grad[1], c->ckpt,
+                    c->grad[0], c->grad[1], c->ckpt, c->design_L,
                     c->state[0], c->state[1], c->thp, c->logw, c->g, c->a, c->lw, c->gstat,
                     c->idx, c->cov_part, c->search_part, c->cd_part, c->mom_part, c->mom_out, c->ml_out,
                     c->L, c->gather_ptrs, c->ctl};
@@ -398,8 +398,24 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
     const smc_config& c = ctx->cfg;
     const int P = ctx->P, d = ctx->d;
     double* th = ctx->theta[ctx->cur];
-    CU(launch_cov(th, d, P, ctx->cov_part, ctx->cov_G, ctx->ctl, 0, c.acc_target, c.hmin_tenths,
-                  c.hmax_tenths, nullptr, nullptr, ctx->L, ctx->stream));
+    const size_t dd = (size_t)d * d;
+    if (ctx->replay) {
+        if (ctx->replay_iter >= ctx->design_iters)
+            return set_err(ctx, SMC_EINVAL, "the replayed design has only %d iterations", ctx->design_iters);
+        CU(cudaMemcpyAsync(ctx->L, ctx->design_L + (size_t)ctx->replay_iter * dd, dd * sizeof(double),
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+        ctx->replay_iter += 1;
+    } else {
+        CU(launch_cov(th, d, P, ctx->cov_part, ctx->cov_G, ctx->ctl, 0, c.acc_target, c.hmin_tenths,
+                      c.hmax_tenths, nullptr, nullptr, ctx->L, ctx->stream));
+    }
+    if (ctx->record) {
+        if (ctx->design_iters >= ctx->design_cap)
+            return set_err(ctx, SMC_ENOMEM, "design record is full (%d iterations)", ctx->design_cap);
+        CU(cudaMemcpyAsync(ctx->design_L + (size_t)ctx->design_iters * dd, ctx->L, dd * sizeof(double),
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+        ctx->design_iters += 1;
+    }
     if (c.mutation == SMC_MALA) {
         MalaArgs a;
         a.m = ctx->mdev;
@@ -546,9 +562,16 @@ smc_status smc_internal_enqueue_cs(smc_ctx* ctx)
 {
     const smc_config& c = ctx->cfg;
     ctx->cycle += 1;
-    // C phase: next power by k-ary bisection on RSS
-    CU(launch_power_search(ctx->ll[ctx->cur], ctx->P, c.d1, c.search_passes, ctx->search_part, ctx->ctl,
-                           ctx->stream));
+    if (ctx->replay) {
+        // C phase of Algorithm 1 with the recorded schedule
+        if (ctx->cycle > (int)ctx->design_x.size())
+            return set_err(ctx, SMC_EINVAL, "the replayed design has only %d cycles", (int)ctx->design_x.size());
+        CU(launch_set_power(ctx->ctl, ctx->design_x[ctx->cycle - 1], ctx->stream));
+    } else {
+        // C phase: next power by k-ary bisection on RSS
+        CU(launch_power_search(ctx->ll[ctx->cur], ctx->P, c.d1, c.search_passes, ctx->search_part, ctx->ctl,
+                               ctx->stream));
+    }
     // S phase (weights dphi * l_n), then pooled RSS, log wtilde and phi
     smc_status st = s_phase(ctx, 0);
     if (st != SMC_OK) return st;
@@ -593,6 +616,10 @@ smc_status smc_internal_after_m(smc_ctx* ctx, int t_l, int R, int Tm, double phi
     if (ctx->profile) {
         smc_status st = fold_profile(ctx);
         if (st != SMC_OK) return st;
+    }
+    if (ctx->record) {
+        ctx->design_x.push_back(c.tempering == SMC_POWER ? ctx->ctl_host->phi : (double)t_l);
+        ctx->design_R.push_back(R);
     }
     ctx->t_prev = t_l;
     ctx->msteps += R;
@@ -815,6 +842,12 @@ static smc_status start_run(smc_ctx* ctx, const double* theta0, int theta0_on_de
     ctx->phi = 0.0;
     ctx->msteps = 0;
     ctx->evals = 0.0;
+    ctx->replay_iter = 0;
+    if (ctx->record) {
+        ctx->design_x.clear();
+        ctx->design_R.clear();
+        ctx->design_iters = 0;
+    }
     return sync_ctl(ctx);
 }
 
@@ -841,6 +874,74 @@ smc_status smc_transfer_bytes(smc_ctx* ctx, uint64_t* h2d, uint64_t* d2h)
     if (!ctx) return SMC_EINVAL;
     if (h2d) *h2d = ctx->h2d;
     if (d2h) *d2h = ctx->d2h;
+    return SMC_OK;
+}
+
+smc_status smc_design_record(smc_ctx* ctx, int max_iterations)
+{
+    if (!ctx || max_iterations < 1) return SMC_EINVAL;
+    if (ctx->replay) return set_err(ctx, SMC_EINVAL, "a replaying context cannot record");
+    if (ctx->cycle > 0) return set_err(ctx, SMC_EINVAL, "start recording before the first cycle");
+    if (ctx->design_L) cudaFree(ctx->design_L);
+    ctx->design_L = nullptr;
+    CU(cudaMalloc(&ctx->design_L, (size_t)max_iterations * ctx->d * ctx->d * sizeof(double)));
+    ctx->design_cap = max_iterations;
+    ctx->design_iters = 0;
+    ctx->design_x.clear();
+    ctx->design_R.clear();
+    ctx->record = 1;
+    return SMC_OK;
+}
+
+smc_status smc_design_size(smc_ctx* ctx, int* ncycles, int* niterations)
+{
+    if (!ctx) return SMC_EINVAL;
+    if (ncycles) *ncycles = (int)ctx->design_x.size();
+    if (niterations) *niterations = ctx->design_iters;
+    return SMC_OK;
+}
+
+smc_status smc_design_get(smc_ctx* ctx, double* x, int* R, double* L)
+{
+    if (!ctx) return SMC_EINVAL;
+    const int nc = (int)ctx->design_x.size();
+    if (x) std::memcpy(x, ctx->design_x.data(), nc * sizeof(double));
+    if (R) std::memcpy(R, ctx->design_R.data(), nc * sizeof(int));
+    if (L && ctx->design_iters) {
+        CU(cudaMemcpyAsync(L, ctx->design_L, (size_t)ctx->design_iters * ctx->d * ctx->d * sizeof(double),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return SMC_OK;
+}
+
+smc_status smc_design_replay(smc_ctx* ctx, int ncycles, const double* x, const int* R, const double* L)
+{
+    if (!ctx || ncycles < 1 || !x || !R || !L) return SMC_EINVAL;
+    if (ctx->cycle > 0) return set_err(ctx, SMC_EINVAL, "load the design before the first cycle");
+    if (ctx->cfg.mutation != SMC_RW) return set_err(ctx, SMC_EINVAL, "replay takes random-walk runs");
+    long iters = 0;
+    for (int l = 0; l < ncycles; ++l) {
+        if (R[l] < 0) return set_err(ctx, SMC_EINVAL, "negative iteration count");
+        iters += R[l];
+        if (ctx->cfg.tempering == SMC_DATA && (x[l] < 1 || x[l] > ctx->T || (l && x[l] <= x[l - 1])))
+            return set_err(ctx, SMC_EINVAL, "data-tempering design must be increasing dates in 1..T");
+        if (ctx->cfg.tempering == SMC_POWER && (!(x[l] > 0.0) || x[l] > 1.0 || (l && x[l] <= x[l - 1])))
+            return set_err(ctx, SMC_EINVAL, "power design must be increasing powers in (0, 1]");
+    }
+    if (ctx->design_L) cudaFree(ctx->design_L);
+    ctx->design_L = nullptr;
+    const size_t bytes = (size_t)(iters > 0 ? iters : 1) * ctx->d * ctx->d * sizeof(double);
+    CU(cudaMalloc(&ctx->design_L, bytes));
+    if (iters) CU(cudaMemcpy(ctx->design_L, L, (size_t)iters * ctx->d * ctx->d * sizeof(double), cudaMemcpyHostToDevice));
+    ctx->h2d += (uint64_t)iters * ctx->d * ctx->d * sizeof(double);
+    ctx->design_x.assign(x, x + ncycles);
+    ctx->design_R.assign(R, R + ncycles);
+    ctx->design_iters = (int)iters;
+    ctx->design_cap = (int)iters;
+    ctx->replay_iter = 0;
+    ctx->record = 0;
+    ctx->replay = 1;
     return SMC_OK;
 }
 
@@ -888,8 +989,17 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
         CU(cudaMemsetAsync(ctx->logw, 0, (size_t)P * sizeof(double), ctx->stream));
         ForceDates fd;
         std::memset(&fd, 0, sizeof fd);
-        fd.n = c.n_force;
-        for (int i = 0; i < c.n_force; ++i) fd.t[i] = c.force_dates[i];
+        double d1 = c.d1;
+        if (ctx->replay) {
+            if (ctx->cycle > (int)ctx->design_x.size())
+                return set_err(ctx, SMC_EINVAL, "the replayed design has only %d cycles", (int)ctx->design_x.size());
+            fd.n = 1;
+            fd.t[0] = (int)ctx->design_x[ctx->cycle - 1];
+            d1 = -1.0;   // the recorded end, not RSS, closes the cycle
+        } else {
+            fd.n = c.n_force;
+            for (int i = 0; i < c.n_force; ++i) fd.t[i] = c.force_dates[i];
+        }
         const int G = (P + kMutThreads - 1) / kMutThreads;
         int s0 = ctx->t_prev;
         for (;;) {
@@ -910,7 +1020,7 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
             ca.stop = &ctx->ctl->cd_stop;
             ca.commit = 0;
             CU(launch_cdata(ca, c.precision, ctx->stream));
-            CU(launch_cdata_select(ctx->cd_part, G, ca.B, s0, ctx->T, P, c.d1, fd, ctx->ctl, ctx->stream));
+            CU(launch_cdata_select(ctx->cd_part, G, ca.B, s0, ctx->T, P, d1, fd, ctx->ctl, ctx->stream));
             ca.commit = 1;
             CU(launch_cdata(ca, c.precision, ctx->stream));
             st = sync_ctl(ctx);
@@ -939,7 +1049,7 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
         st = refresh_gradient(ctx, Tm);
         if (st != SMC_OK) return st;
     }
-    const int R = smc_internal_R(ctx, rss);
+    const int R = ctx->replay ? ctx->design_R[ctx->cycle - 1] : smc_internal_R(ctx, rss);
     const double E = forced ? c.e2 : c.e1;
     int r = 0;
     for (; r < R; ++r) {

@@ -55,6 +55,14 @@ struct smc_ctx {
     int64_t msteps = 0;
     double evals = 0.0;
     uint64_t h2d = 0, d2h = 0;
+    // Algorithm 3 (hybrid): design recording / replay
+    int record = 0, replay = 0;
+    std::vector<double> design_x;        // t_l (data) or phi_l (power) per cycle
+    std::vector<int> design_R;           // Metropolis iterations per cycle
+    double* design_L = nullptr;          // device, [iterations][d][d]
+    int design_cap = 0;                  // capacity of design_L in iterations
+    int design_iters = 0;                // iterations recorded, or loaded for replay
+    int replay_iter = 0;                 // next factor to use in replay
     // profiling
     int profile = 0;
     double mutate_ms = 0.0;

@@ -412,6 +412,24 @@ __global__ void __launch_bounds__(1024) k_power_select(const double* part, int G
     }
 }
 
+// Replay of a recorded power: dphi = phi_l - phi (the rest of the power when
+// phi_l = 1), as the C phase of Algorithm 1 with a fixed schedule.
+__global__ void k_set_power(Ctl* ctl, double phi_target)
+{
+    if (threadIdx.x != 0) return;
+    const bool last = !(phi_target < 1.0);
+    ctl->dphi = last ? 1.0 - ctl->phi : phi_target - ctl->phi;
+    ctl->last = last ? 1 : 0;
+    ctl->done = 1;
+}
+
+cudaError_t launch_set_power(Ctl* ctl, double phi_target, cudaStream_t s)
+{
+    k_set_power<<<1, 32, 0, s>>>(ctl, phi_target);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_power_search(const double* ll, int P, double d1, int passes, double* part,
                                 Ctl* ctl, cudaStream_t s)
 {

@@ -62,6 +62,9 @@ size_t search_part_len(int P);
 cudaError_t launch_power_search(const double* ll, int P, double d1, int passes, double* part,
                                 Ctl* ctl, cudaStream_t s);
 
+// Replay (Algorithm 3): set the increment to reach a recorded power.
+cudaError_t launch_set_power(Ctl* ctl, double phi_target, cudaStream_t s);
+
 // S phase: per group weights, log-mean weight (a_j, lw_j), resampling, then gather.
 // mode 0: weights from ctl->dphi * ll; mode 1: from logw; mode 2: w given directly.
 struct SelectArgs {

@@ -94,6 +94,10 @@ def _declare(L):
     L.smc_transfer_bytes.argtypes = [vp, P(C.c_uint64), P(C.c_uint64)]
     L.smc_free.argtypes = [vp]
     L.smc_free.restype = None
+    L.smc_design_record.argtypes = [vp, C.c_int]
+    L.smc_design_size.argtypes = [vp, P(C.c_int), P(C.c_int)]
+    L.smc_design_get.argtypes = [vp, dp, P(C.c_int), dp]
+    L.smc_design_replay.argtypes = [vp, C.c_int, dp, P(C.c_int), dp]
     L.smc_batch_init.argtypes = [C.c_int, P(smc_model), P(smc_config), P(dp), P(C.c_int), P(dp), vp, P(vp)]
     L.smc_batch_autotune.argtypes = [vp, C.c_int, dp]
     L.smc_batch_cycle.argtypes = [vp, P(C.c_int)]
@@ -292,6 +296,28 @@ class Ctx:
         _check(lib().smc_get_particles(self.h, _dptr(th), _dptr(ll), _dptr(lp),
                                        _dptr(st) if ns else None), self.h)
         return th, ll, lp, st[:, :ns]
+
+    # Algorithm 3 (hybrid)
+    def record_design(self, max_iterations=4096):
+        _check(lib().smc_design_record(self.h, max_iterations), self.h)
+
+    def design(self):
+        nc, ni = C.c_int(), C.c_int()
+        _check(lib().smc_design_size(self.h, C.byref(nc), C.byref(ni)), self.h)
+        x = np.zeros(nc.value)
+        R = np.zeros(nc.value, dtype=np.int32)
+        L = np.zeros((ni.value, self.d, self.d))
+        _check(lib().smc_design_get(self.h, _dptr(x), R.ctypes.data_as(C.POINTER(C.c_int)),
+                                    _dptr(L) if ni.value else None), self.h)
+        return {"x": x, "R": R, "L": L}
+
+    def replay_design(self, design):
+        x = _f64(design["x"])
+        R = np.ascontiguousarray(design["R"], dtype=np.int32)
+        L = _f64(design["L"])
+        self._design = (x, R, L)
+        _check(lib().smc_design_replay(self.h, len(x), _dptr(x), R.ctypes.data_as(C.POINTER(C.c_int)),
+                                       _dptr(L)), self.h)
 
     def profile(self, enable=True):
         _check(lib().smc_profile(self.h, int(enable)), self.h)
