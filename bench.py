@@ -61,7 +61,7 @@ def alu_ops_per_eval(K, I, gamma):
     FP32 lane operations and SFU (MUFU) operations.  See the roofline section of
     the design notes for the derivation."""
     fp32 = 1 + (3 if gamma else 2) * K + K + 1 + 2
-    fp32 += {1: 1, 2: 8}.get(I, 7 * I)
+    fp32 += {1: 1, 2: 8}.get(I, 5 * I)
     mufu = 1 + {1: 0, 2: 1}.get(I, I)
     return fp32, mufu
 

@@ -80,7 +80,7 @@ __global__ void k_iter_inc(int* iter)
 // LPT cost of a dataset: T x this.
 static double obs_cost(int K, int I, int gamma)
 {
-    const int fp32 = 1 + (gamma ? 3 : 2) * K + K + 1 + 2 + (I == 1 ? 1 : I == 2 ? 8 : 7 * I);
+    const int fp32 = 1 + (gamma ? 3 : 2) * K + K + 1 + 2 + (I == 1 ? 1 : I == 2 ? 8 : 5 * I);
     const int sfu = 1 + (I == 1 ? 0 : I == 2 ? 1 : I);
     return (double)(fp32 + sfu);
 }
