@@ -284,6 +284,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     with torch.cuda.stream(stream):
         ctx = S.init(m, cfg, y, th0, stream=stream.cuda_stream)
+    shape = ctx.autotune(iters=2) if not mala else (1, 128, None)
     seed_of = lambda k: 1 + rank + 7919 * k
 
     def one_run(k):
@@ -345,6 +346,7 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             c2 = S.init(m, cfg, y, th0, stream=stream.cuda_stream)
+            c2.set_launch_shape(shape[0], shape[1])
             c2.run(args.cycles)
             c2.log_ml()
             cyc2, ms2, evl2 = c2.totals()
@@ -369,7 +371,9 @@ def main():
             "ops_per_eval": {"fp32": fp32_ops, "mufu": mufu_ops},
             "kernel": (f"k_mutate_mala<GradEgarch<float,{w.K},{w.I}>>" if mala
                        else f"k_mutate<PolicyEgarchF32<{w.K},{w.I}>>"), "avg_launch_ms": avg_launch_s * 1e3,
-            "launches": mut_n, "share_of_step": (mut_ms / 1e3) / t_total if t_total else None}
+            "launches": mut_n, "share_of_step": (mut_ms / 1e3) / t_total if t_total else None,
+            "launch_shape": {"particles_per_thread": shape[0], "threads_per_block": shape[1],
+                             "autotune_ms_per_iteration": shape[2]}}
     if clk.get("sm_mhz"):
         roof["frac_at_median_clock"] = achieved / alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, clk["sm_mhz"])[0]
 

@@ -214,6 +214,17 @@ smc_status smc_design_size(smc_ctx* ctx, int* ncycles, int* niterations);
 smc_status smc_design_get(smc_ctx* ctx, double* x, int* R, double* L);
 smc_status smc_design_replay(smc_ctx* ctx, int ncycles, const double* x, const int* R, const double* L);
 
+/* Launch shape of the M-phase mutation kernel.  For FP32 EGARCH random-walk
+ * runs a thread can carry two particles (their recursions interleave, hiding
+ * each other's dependency latency when particles per scheduler are few).
+ * smc_autotune times `iters` Metropolis iterations of each candidate shape
+ * (1 particle x 128 threads; 2 x 64; 2 x 128) on a snapshot of the particles,
+ * restores them, and keeps the fastest; outputs (host, nullable): the shape and
+ * its time per iteration.  Results do not depend on the shape.
+ * smc_set_launch_shape sets one directly. */
+smc_status smc_autotune(smc_ctx* ctx, int iters, int* ppt, int* threads, double* ms_per_iteration);
+smc_status smc_set_launch_shape(smc_ctx* ctx, int ppt, int threads);
+
 /* Number of kernel launches this library has issued in this process. */
 uint64_t smc_launch_count(void);
 

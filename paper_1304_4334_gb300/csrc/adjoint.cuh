@@ -130,6 +130,25 @@ struct EgarchNat {
         eps = Real(0);
     }
 
+    // One observation's state update only: (v, eps) and exp(-s_t).
+    template <bool kFirst>
+    __device__ __forceinline__ void step_state(Real y, Real& inv)
+    {
+        if constexpr (kFirst) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = v0[k];
+        } else {
+            const Real ae = fabs(eps) - (Real)kSqrt2OverPi;
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = al[k] * v[k] + be[k] * ae + ga[k] * eps;
+        }
+        Real vs = v[0];
+#pragma unroll
+        for (int k = 1; k < K; ++k) vs += v[k];
+        inv = nexp<Real>(-(lsy + Real(0.5) * vs));
+        eps = (y - mu) * inv;
+    }
+
     // One observation: updates (v, eps), returns l_t + (1/2) log 2pi and exp(-s_t).
     template <bool kFirst>
     __device__ __forceinline__ Real step(Real y, Real& inv)
@@ -230,6 +249,40 @@ __device__ double adj_forward(EgarchNat<Real, K, I>& m, const Real* __restrict__
     return acc + (double)T * (-0.5 * kLog2Pi);
 }
 
+// FP32 forward pass through the base-2 recursion of the random-walk kernel
+// (EgarchF32), writing the same natural-unit checkpoints as adj_forward.
+template <int K, int I, int kSeg>
+__device__ double adj_forward_fast(const float* th, int has_gamma, int eps0_zero, const float* __restrict__ y,
+                                   int T, float* ckpt, size_t P, int p)
+{
+    static_assert(kSeg == 32, "one 32-observation partial per segment");
+    EgarchF32<K, I> f;
+    f.setup(th, has_gamma, eps0_zero);
+    const int nseg = (T + kSeg - 1) / kSeg;
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int t0 = sg * kSeg, n = min(kSeg, T - t0);
+        if (sg > 0) {
+            double st[K + 1];
+            f.state_out(st);
+            float* c = ckpt + (size_t)(sg - 1) * (K + 1) * P + p;
+#pragma unroll
+            for (int k = 0; k <= K; ++k) c[k * P] = (float)st[k];
+        }
+        if (n == kSeg && t0 > 0) {
+#pragma unroll 8
+            for (int r = 0; r < kSeg; ++r) f.template step<false>(y[t0 + r]);
+        } else {
+            for (int r = 0; r < n; ++r) {
+                if (t0 + r == 0) f.template step<true>(y[0]);
+                else f.template step<false>(y[t0 + r]);
+            }
+        }
+        f.flush();
+        if ((sg & 7) == 7) f.flush_fp64();
+    }
+    return f.finish(T);
+}
+
 // Reverse sweep over all segments; gn (double, kNp) receives d l / d natural
 // parameters.  buf is this thread's shared-memory slab laid out
 // [kSeg][K + 2][stride] (v_k, eps, exp(-s)) with element (t, f) at
@@ -266,16 +319,29 @@ __device__ void adj_reverse(EgarchNat<Real, K, I> m, const Real* __restrict__ y,
 #pragma unroll
         for (int k = 0; k < K; ++k) m.v[k] = vprev[k];
         m.eps = eprev;
-        for (int r = 0; r < n; ++r) {
-            Real inv;
-            if (t0 + r == 0) m.template step<true>(y[0], inv);
-            else m.template step<false>(y[t0 + r], inv);
+        auto put = [&](int r, Real inv) {
 #pragma unroll
             for (int k = 0; k < K; ++k) buf[(r * W + k) * stride] = m.v[k];
             buf[(r * W + K) * stride] = m.eps;
             buf[(r * W + K + 1) * stride] = inv;
+        };
+        if (n == kSeg && t0 > 0) {
+#pragma unroll 8
+            for (int r = 0; r < kSeg; ++r) {
+                Real inv;
+                m.template step_state<false>(y[t0 + r], inv);
+                put(r, inv);
+            }
+        } else {
+            for (int r = 0; r < n; ++r) {
+                Real inv;
+                if (t0 + r == 0) m.template step_state<true>(y[0], inv);
+                else m.template step_state<false>(y[t0 + r], inv);
+                put(r, inv);
+            }
         }
         // reverse through the segment
+#pragma unroll 1
         for (int r = n - 1; r >= 0; --r) {
             const int t = t0 + r;
             const Real eps = buf[(r * W + K) * stride];

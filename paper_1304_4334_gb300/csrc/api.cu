@@ -45,6 +45,22 @@ cudaError_t launch_cdata_f64_k2(const CdataArgs& a, cudaStream_t s);
 cudaError_t launch_cdata_f64_k3(const CdataArgs& a, cudaStream_t s);
 cudaError_t launch_cdata_f64_k4(const CdataArgs& a, cudaStream_t s);
 cudaError_t launch_cdata_linreg(const CdataArgs& a, cudaStream_t s);
+cudaError_t launch_mutate_x2_f32_k1(const MutateArgs& a, int threads, cudaStream_t s);
+cudaError_t launch_mutate_x2_f32_k2(const MutateArgs& a, int threads, cudaStream_t s);
+cudaError_t launch_mutate_x2_f32_k3(const MutateArgs& a, int threads, cudaStream_t s);
+cudaError_t launch_mutate_x2_f32_k4(const MutateArgs& a, int threads, cudaStream_t s);
+
+cudaError_t launch_mutate_x2(const MutateArgs& a, int threads, cudaStream_t s)
+{
+    count_launch();
+    switch (a.m.K) {
+    case 1: return launch_mutate_x2_f32_k1(a, threads, s);
+    case 2: return launch_mutate_x2_f32_k2(a, threads, s);
+    case 3: return launch_mutate_x2_f32_k3(a, threads, s);
+    case 4: return launch_mutate_x2_f32_k4(a, threads, s);
+    }
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_cdata(const CdataArgs& a, int precision, cudaStream_t s)
 {
@@ -478,7 +494,8 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
         e1 = take_event(ctx);
         CU(cudaEventRecord(e0, ctx->stream));
     }
-    CU(launch_mutate(a, c.precision, ctx->stream));
+    if (ctx->ppt == 2) CU(launch_mutate_x2(a, ctx->mut_threads, ctx->stream));
+    else CU(launch_mutate(a, c.precision, ctx->stream));
     if (ctx->profile) {
         CU(cudaEventRecord(e1, ctx->stream));
         ctx->ev_pending.push_back({e0, e1});
@@ -874,6 +891,93 @@ smc_status smc_transfer_bytes(smc_ctx* ctx, uint64_t* h2d, uint64_t* d2h)
     if (!ctx) return SMC_EINVAL;
     if (h2d) *h2d = ctx->h2d;
     if (d2h) *d2h = ctx->d2h;
+    return SMC_OK;
+}
+
+// Mutation launch-shape autotuner: times `iters` Metropolis iterations of each
+// candidate shape on a snapshot of the particles (restored afterwards, with
+// the control block) and keeps the fastest.
+smc_status smc_autotune(smc_ctx* ctx, int iters, int* ppt, int* threads, double* ms_per_iteration)
+{
+    if (!ctx) return SMC_EINVAL;
+    if (iters < 1) iters = 2;
+    const bool fp32_egarch = ctx->model.model == SMC_EGARCH && ctx->cfg.precision == SMC_FP32 &&
+                             ctx->cfg.mutation == SMC_RW;
+    const int P = ctx->P, d = ctx->d;
+    const size_t Ps = (size_t)P;
+    const int from = ctx->cur, to = from ^ 1;
+    CU(cudaMemcpyAsync(ctx->theta[to], ctx->theta[from], Ps * d * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->ll[to], ctx->ll[from], Ps * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->lp[to], ctx->lp[from], Ps * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    if (ctx->ns)
+        CU(cudaMemcpyAsync(ctx->state[to], ctx->state[from], Ps * ctx->ns * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const Ctl saved = *ctx->ctl_host;
+    struct Shape { int ppt, threads; };
+    std::vector<Shape> cand = {{1, kMutThreads}};
+    if (fp32_egarch) {
+        cand.push_back({2, 64});
+        cand.push_back({2, 128});
+    }
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    const int rec = ctx->record, prof = ctx->profile;
+    ctx->record = 0;
+    ctx->profile = 0;
+    double best = 1e30;
+    Shape pick = cand[0];
+    const double phi = ctx->cfg.tempering == SMC_POWER ? ctx->phi : 1.0;
+    const int Tm = ctx->cfg.tempering == SMC_POWER ? ctx->T : (ctx->t_prev > 0 ? ctx->t_prev : ctx->T);
+    for (const Shape& sh : cand) {
+        ctx->ppt = sh.ppt;
+        ctx->mut_threads = sh.threads;
+        smc_status st = m_iteration(ctx, 0, Tm, phi);   // warm-up
+        if (st != SMC_OK) return st;
+        CU(cudaEventRecord(e0, ctx->stream));
+        for (int k = 0; k < iters; ++k) {
+            st = m_iteration(ctx, k + 1, Tm, phi);
+            if (st != SMC_OK) return st;
+        }
+        CU(cudaEventRecord(e1, ctx->stream));
+        CU(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            pick = sh;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->record = rec;
+    ctx->profile = prof;
+    ctx->ppt = pick.ppt;
+    ctx->mut_threads = pick.threads;
+    CU(cudaMemcpyAsync(ctx->theta[from], ctx->theta[to], Ps * d * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->ll[from], ctx->ll[to], Ps * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->lp[from], ctx->lp[to], Ps * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    if (ctx->ns)
+        CU(cudaMemcpyAsync(ctx->state[from], ctx->state[to], Ps * ctx->ns * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    *ctx->ctl_host = saved;
+    CU(cudaMemcpyAsync(ctx->ctl, ctx->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (ppt) *ppt = pick.ppt;
+    if (threads) *threads = pick.threads;
+    if (ms_per_iteration) *ms_per_iteration = best / iters;
+    return SMC_OK;
+}
+
+smc_status smc_set_launch_shape(smc_ctx* ctx, int ppt, int threads)
+{
+    if (!ctx || (ppt != 1 && ppt != 2) || (threads != 64 && threads != 128)) return SMC_EINVAL;
+    if (ppt == 2 && !(ctx->model.model == SMC_EGARCH && ctx->cfg.precision == SMC_FP32 &&
+                      ctx->cfg.mutation == SMC_RW))
+        return set_err(ctx, SMC_EINVAL, "two particles per thread needs the FP32 EGARCH random walk");
+    if (ppt == 1 && threads != kMutThreads) return set_err(ctx, SMC_EINVAL, "one particle per thread uses 128 threads");
+    ctx->ppt = ppt;
+    ctx->mut_threads = threads;
     return SMC_OK;
 }
 

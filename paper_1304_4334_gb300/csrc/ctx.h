@@ -63,6 +63,8 @@ struct smc_ctx {
     int design_cap = 0;                  // capacity of design_L in iterations
     int design_iters = 0;                // iterations recorded, or loaded for replay
     int replay_iter = 0;                 // next factor to use in replay
+    // mutation launch shape (FP32 EGARCH): particles per thread and block size
+    int ppt = 1, mut_threads = kMutThreads;
     // profiling
     int profile = 0;
     double mutate_ms = 0.0;

@@ -22,6 +22,21 @@ cudaError_t launch_mutate_k(const MutateArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// ppt = particles per thread (1 or 2; 2 only for the FP32 policy)
+template <int K>
+cudaError_t launch_mutate_x2_k(const MutateArgs& a, int threads, cudaStream_t s)
+{
+    const int g = (a.P + 2 * threads - 1) / (2 * threads);
+    switch (a.m.I) {
+    case 1: k_mutate_x2<K, 1><<<g, threads, 0, s>>>(a); break;
+    case 2: k_mutate_x2<K, 2><<<g, threads, 0, s>>>(a); break;
+    case 3: k_mutate_x2<K, 3><<<g, threads, 0, s>>>(a); break;
+    case 4: k_mutate_x2<K, 4><<<g, threads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <template <int, int> class Pol, int K>
 cudaError_t launch_loglik_k(const LoglikArgs& a, cudaStream_t s)
 {

@@ -202,6 +202,84 @@ __global__ void __launch_bounds__(kMutThreads) k_mutate(MutateArgs a)
     mutate_tile<Pol>(a, a.iter, blockIdx.x * blockDim.x, sm);
 }
 
+// Two particles per thread (FP32 EGARCH): particles p0 + threadIdx.x and
+// p0 + blockDim.x + threadIdx.x; same proposal, acceptance and outputs as
+// mutate_tile, particle by particle.
+template <int K, int I>
+__device__ __forceinline__ void mutate_tile_x2(const MutateArgs& a, uint64_t iter, int p0,
+                                               MutateSmem<PolicyEgarchF32<K, I>>& sm)
+{
+    using Pol = PolicyEgarchF32<K, I>;
+    const int d = a.m.d;
+    for (int i = threadIdx.x; i < d * d; i += blockDim.x) sm.Ls[i] = a.L[i];
+    if (threadIdx.x == 0) sm.acc_s = 0;
+    ObsPipe<float, kChunkF32> pipe{sm.obuf, sm.bars, (const float*)a.obs, (int64_t)a.T,
+                                   (a.T + kChunkF32 - 1) / kChunkF32};
+    pipe.start();
+    const size_t P = (size_t)a.P;
+    int pq[2];
+    bool act[2];
+    double lpn[2];
+    EgarchF32<K, I> mdl[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int p = p0 + h * (int)blockDim.x + (int)threadIdx.x;
+        act[h] = p < a.P;
+        pq[h] = act[h] ? p : a.P - 1;
+        double thn[kMaxD];
+        float z[kMaxD];
+        proposal_normals<float>(a.seed, (uint64_t)pq[h], iter, a.cycle, d, z);
+        for (int i = 0; i < d; ++i) {
+            float s = 0;
+            for (int k = 0; k <= i; ++k) s += sm.Ls[i * d + k] * z[k];
+            thn[i] = a.theta[i * P + pq[h]] + (double)s;
+            if (act[h]) a.thp[i * P + p] = thn[i];
+        }
+        lpn[h] = log_prior(a.m, thn);
+        float full[kMaxD];
+        full_theta<float>(a.m, thn, full);
+        Pol::setup(mdl[h], a.m, full);
+    }
+    const bool ok = run_egarch_f32_x2<K, I>(mdl[0], mdl[1], pipe, a.T);
+    if (!ok && threadIdx.x == 0) raise_error(a.err, kErrTimeout);
+    unsigned int nacc = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        double ll_new = ok ? mdl[h].finish(a.T) : -INFINITY;
+        if (isnan(ll_new)) ll_new = -INFINITY;
+        bool acc = false;
+        const int p = pq[h];
+        if (act[h]) {
+            const double log_alpha = tempered_target(lpn[h], ll_new, a.phi) -
+                                     tempered_target(a.lp[p], a.ll[p], a.phi);
+            acc = log_uniform_mh(a.seed, (uint64_t)p, iter, a.cycle) < log_alpha;
+            if (acc) {
+                for (int i = 0; i < d; ++i) a.theta[i * P + p] = a.thp[i * P + p];
+                a.ll[p] = ll_new;
+                a.lp[p] = lpn[h];
+                if (a.state) {
+                    double st[kMaxState];
+                    mdl[h].state_out(st);
+                    for (int k = 0; k < Pol::kNs; ++k) a.state[k * P + p] = st[k];
+                }
+            }
+        }
+        nacc += __popc(__ballot_sync(0xffffffffu, acc));
+    }
+    if ((threadIdx.x & 31) == 0 && nacc) atomicAdd(&sm.acc_s, nacc);
+    __syncthreads();
+    if (threadIdx.x == 0 && sm.acc_s) atomicAdd(a.acc_count, (unsigned long long)sm.acc_s);
+    if (p0 == 0 && threadIdx.x == 0 && a.pending) *a.pending = 1;
+    pipe.finish();
+}
+
+template <int K, int I>
+__global__ void __launch_bounds__(kMutThreads) k_mutate_x2(MutateArgs a)
+{
+    __shared__ MutateSmem<PolicyEgarchF32<K, I>> sm;
+    mutate_tile_x2<K, I>(a, a.iter, blockIdx.x * 2 * blockDim.x, sm);
+}
+
 template <class Pol>
 __global__ void __launch_bounds__(kMutThreads) k_loglik(LoglikArgs a)
 {

@@ -64,7 +64,25 @@ struct GradEgarch {
         EgarchNat<Real, K, I> mdl;
         mdl.setup(full, m.gamma, m.eps0_zero);
         const Real* y = (const Real*)obs;
-        double ll = adj_forward<Real, K, I, kSeg>(mdl, y, T, (Real*)ckpt, P, p, true);
+        double ll;
+        if constexpr (sizeof(Real) == 4) {
+            ll = adj_forward_fast<K, I, kSeg>(full, m.gamma, m.eps0_zero, y, T, (Real*)ckpt, P, p);
+            // end state: recompute the last segment's tail from its checkpoint
+            const int nseg = (T + kSeg - 1) / kSeg;
+            if (nseg > 1) {
+                const Real* c = (const Real*)ckpt + (size_t)(nseg - 2) * (K + 1) * P + p;
+#pragma unroll
+                for (int k = 0; k < K; ++k) mdl.v[k] = c[k * P];
+                mdl.eps = c[K * P];
+            }
+            for (int t = (nseg - 1) * kSeg; t < T; ++t) {
+                Real inv;
+                if (t == 0) mdl.template step_state<true>(y[0], inv);
+                else mdl.template step_state<false>(y[t], inv);
+            }
+        } else {
+            ll = adj_forward<Real, K, I, kSeg>(mdl, y, T, (Real*)ckpt, P, p, true);
+        }
 #pragma unroll
         for (int k = 0; k < K; ++k) st[k] = (double)mdl.v[k];
         st[K] = (double)mdl.eps;

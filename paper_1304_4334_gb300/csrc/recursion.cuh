@@ -556,6 +556,86 @@ __device__ __forceinline__ bool run_egarch_f32(EgarchF32<K, I>& mdl, ObsPipe<flo
     return true;
 }
 
+// Two particles per thread: the two recursions are independent, so the
+// compiler interleaves their instruction streams and each hides the other's
+// dependency latency.
+template <int K, int I>
+__device__ __forceinline__ bool run_egarch_f32_x2(EgarchF32<K, I>& ma, EgarchF32<K, I>& mb,
+                                                  ObsPipe<float, kChunkF32>& pipe, int T)
+{
+    for (int c = 0; c < pipe.nchunks; ++c) {
+        if (!pipe.wait(c)) {
+            pipe.drain(c);
+            return false;
+        }
+        const float* yb = pipe.buf + (c & 1) * kChunkF32;
+        const int cnt = min(kChunkF32, T - c * kChunkF32);
+        const int nunits = cnt >> 5;
+        for (int u = 0; u < nunits; ++u) {
+            const float4* y4 = reinterpret_cast<const float4*>(yb + 32 * u);
+            if (c == 0 && u == 0) {
+                float4 q = y4[0];
+                ma.template step<true>(q.x);
+                mb.template step<true>(q.x);
+                ma.template step<false>(q.y);
+                mb.template step<false>(q.y);
+                ma.template step<false>(q.z);
+                mb.template step<false>(q.z);
+                ma.template step<false>(q.w);
+                mb.template step<false>(q.w);
+#pragma unroll
+                for (int j = 1; j < 8; ++j) {
+                    q = y4[j];
+                    ma.template step<false>(q.x);
+                    mb.template step<false>(q.x);
+                    ma.template step<false>(q.y);
+                    mb.template step<false>(q.y);
+                    ma.template step<false>(q.z);
+                    mb.template step<false>(q.z);
+                    ma.template step<false>(q.w);
+                    mb.template step<false>(q.w);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float4 q = y4[j];
+                    ma.template step<false>(q.x);
+                    mb.template step<false>(q.x);
+                    ma.template step<false>(q.y);
+                    mb.template step<false>(q.y);
+                    ma.template step<false>(q.z);
+                    mb.template step<false>(q.z);
+                    ma.template step<false>(q.w);
+                    mb.template step<false>(q.w);
+                }
+            }
+            ma.flush();
+            mb.flush();
+            if ((u & 7) == 7) {
+                ma.flush_fp64();
+                mb.flush_fp64();
+            }
+        }
+        const int rem = cnt & 31;
+        if (rem) {
+            for (int r = 0; r < rem; ++r) {
+                const int tl = 32 * nunits + r;
+                if (c == 0 && tl == 0) {
+                    ma.template step<true>(yb[tl]);
+                    mb.template step<true>(yb[tl]);
+                } else {
+                    ma.template step<false>(yb[tl]);
+                    mb.template step<false>(yb[tl]);
+                }
+            }
+            ma.flush();
+            mb.flush();
+        }
+        pipe.release(c);
+    }
+    return true;
+}
+
 template <int K, int I>
 __device__ __forceinline__ bool run_egarch_f64(EgarchF64<K, I>& mdl, ObsPipe<double, kChunkF64>& pipe,
                                                int T)

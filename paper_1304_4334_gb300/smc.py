@@ -94,6 +94,8 @@ def _declare(L):
     L.smc_transfer_bytes.argtypes = [vp, P(C.c_uint64), P(C.c_uint64)]
     L.smc_free.argtypes = [vp]
     L.smc_free.restype = None
+    L.smc_autotune.argtypes = [vp, C.c_int, P(C.c_int), P(C.c_int), dp]
+    L.smc_set_launch_shape.argtypes = [vp, C.c_int, C.c_int]
     L.smc_design_record.argtypes = [vp, C.c_int]
     L.smc_design_size.argtypes = [vp, P(C.c_int), P(C.c_int)]
     L.smc_design_get.argtypes = [vp, dp, P(C.c_int), dp]
@@ -296,6 +298,15 @@ class Ctx:
         _check(lib().smc_get_particles(self.h, _dptr(th), _dptr(ll), _dptr(lp),
                                        _dptr(st) if ns else None), self.h)
         return th, ll, lp, st[:, :ns]
+
+    def autotune(self, iters=2):
+        """Pick the mutation kernel's launch shape by timing (smc_autotune)."""
+        ppt, thr, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(lib().smc_autotune(self.h, iters, C.byref(ppt), C.byref(thr), C.byref(ms)), self.h)
+        return ppt.value, thr.value, ms.value
+
+    def set_launch_shape(self, ppt, threads):
+        _check(lib().smc_set_launch_shape(self.h, ppt, threads), self.h)
 
     # Algorithm 3 (hybrid)
     def record_design(self, max_iterations=4096):

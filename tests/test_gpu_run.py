@@ -200,3 +200,31 @@ def test_rne_stopping_rule_run(S):
     lm, nse, _ = ctx.log_ml()
     assert abs(lm - lml) < 4 * nse + 0.02
     ctx.close()
+
+
+def test_launch_shapes_give_identical_runs(S):
+    """Two particles per thread (either block size) computes every particle's
+    proposal, recursion and decision exactly as one particle per thread."""
+    truth = I.WORKLOADS["egarch22_T5000"].truth
+    y = I.simulate_egarch(truth, 700, seed=8)
+    m = S.model_egarch(2, 2, True)
+    mean, sd, lo = S.model_prior(m)
+    J, N = 16, 300   # P = 4800: ragged against 64/128/256-particle tiles
+    th0 = I.draw_prior(mean, sd, lo, J * N, seed=9)
+    out = []
+    for ppt, thr in [(1, 128), (2, 64), (2, 128)]:
+        ctx = S.init(m, S.config_default(J=J, N=N, precision=S.FP32, seed=5), y, th0)
+        ctx.set_launch_shape(ppt, thr)
+        ctx.run()
+        out.append((ctx.log_ml(), ctx.particles()))
+        ctx.close()
+    for (lm, (th, ll, lp, st)) in out[1:]:
+        assert lm[0] == pytest.approx(out[0][0][0], rel=1e-12, abs=1e-9)
+        np.testing.assert_allclose(th, out[0][1][0], rtol=0, atol=1e-10)
+        np.testing.assert_allclose(ll, out[0][1][1], rtol=1e-12)
+    ctx = S.init(m, S.config_default(J=J, N=N, precision=S.FP32, seed=5), y, th0)
+    ppt, thr, ms = ctx.autotune(iters=1)
+    assert (ppt, thr) in [(1, 128), (2, 64), (2, 128)] and ms > 0
+    ctx.run()
+    assert ctx.log_ml()[0] == pytest.approx(out[0][0][0], rel=1e-12, abs=1e-9)
+    ctx.close()
