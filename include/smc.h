@@ -67,7 +67,7 @@ enum { SMC_EGARCH = 0, SMC_LINREG = 1 };
 enum { SMC_FP64 = 0, SMC_FP32 = 1 };
 enum { SMC_DATA = 0, SMC_POWER = 1 };
 enum { SMC_RW = 0, SMC_MALA = 1 };
-enum { SMC_RESIDUAL = 0, SMC_MULTINOMIAL = 1 };
+enum { SMC_RESIDUAL = 0, SMC_MULTINOMIAL = 1, SMC_STRATIFIED = 2, SMC_SYSTEMATIC = 3 };
 enum { SMC_STOP_DET = 0, SMC_STOP_RNE = 1 };
 
 /* Model description (plain data).
@@ -119,7 +119,8 @@ typedef struct {
                                  log weights and estimators; SMC_FP64: all FP64 */
     int tempering;            /* SMC_POWER | SMC_DATA */
     int mutation;             /* SMC_RW | SMC_MALA (Langevin proposal using the adjoint gradient) */
-    int resampler;            /* SMC_RESIDUAL | SMC_MULTINOMIAL */
+    int resampler;            /* SMC_RESIDUAL (default) | SMC_MULTINOMIAL, or the paper's
+                                 experimental SMC_STRATIFIED | SMC_SYSTEMATIC */
     double d1, d2;
     int stop_rule;            /* SMC_STOP_DET | SMC_STOP_RNE */
     int rbar, kappa, rmax;
@@ -338,7 +339,10 @@ smc_status smc_power_search(const double* ll, int P, double phi, double d1, int 
                             double* dphi, double* rss, void* stream);
 
 /* S phase within each of J groups of N (Section 3.3): residual
- * (SMC_RESIDUAL) or multinomial resampling from weights w (device [J*N],
+ * (SMC_RESIDUAL), multinomial, stratified or systematic resampling (the last
+ * two: slot k takes the particle whose inclusive prefix of q first exceeds
+ * floor((k Q + U_k) / N), U_k = mulhi64(x, Q), with one Philox draw per group
+ * (systematic, draw index 0) or per slot (stratified)) from weights w (device [J*N],
  * non-negative, any scale per group).  Integer fixed point: q_n =
  * floor(2^40 w_n / max w), counts floor(N q_n / Q), residual draws by
  * upper_bound on the integer residual prefix with mulhi64(x, R), x from

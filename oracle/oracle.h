@@ -120,6 +120,11 @@ void or_log_ml(const double *a, int J, double *log_ml, double *nse_log);
 int or_resample(const double *w, int J, int N, int resid, uint64_t seed,
                 uint64_t cycle, int32_t *idx);
 
+/* Resampling by scheme: 0 residual, 1 multinomial, 2 stratified, 3 systematic
+ * (the last two are the paper's experimental alternatives). */
+int or_resample_scheme(const double *w, int J, int N, int scheme, uint64_t seed,
+                       uint64_t cycle, int32_t *idx);
+
 /* ---- covariance & Cholesky (Section 3.3 "Metropolis steps") ---------------- */
 void or_mean_cov(const double *theta, int P, int d, double *mean, double *cov);
 int or_cholesky(const double *A, int d, double *L); /* lower, row-major */
@@ -153,7 +158,7 @@ typedef struct {
     int J, N;
     int tempering;      /* 0 = data (paper), 1 = power                          */
     int mutation;       /* 0 = random walk, 1 = MALA                            */
-    int resid;          /* 1 residual, 0 multinomial                            */
+    int resid;          /* 1 residual, 0 multinomial, 2 stratified, 3 systematic */
     double d1, d2;
     int stop_rule;      /* 0 deterministic, 1 RNE                               */
     int rbar, kappa, rmax;

@@ -112,6 +112,8 @@ def _declare(L):
     L.or_log_ml.argtypes = [dp, C.c_int, dp, dp]
     L.or_resample.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, i32p]
     L.or_resample.restype = C.c_int
+    L.or_resample_scheme.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, i32p]
+    L.or_resample_scheme.restype = C.c_int
     L.or_mean_cov.argtypes = [dp, C.c_int, C.c_int, dp, dp]
     L.or_cholesky.argtypes = [dp, C.c_int, dp]
     L.or_cholesky.restype = C.c_int
@@ -318,6 +320,18 @@ def resample(w, J, N, resid=True, seed=0, cycle=0):
     w = _f64(w)
     idx = np.zeros(J * N, dtype=np.int32)
     st = _load().or_resample(_d(w), J, N, int(resid), seed, cycle, idx.ctypes.data_as(i32p))
+    if st != 0:
+        raise ValueError("degenerate group (all weights zero)")
+    return idx.reshape(J, N)
+
+
+RESIDUAL, MULTINOMIAL, STRATIFIED, SYSTEMATIC = 0, 1, 2, 3
+
+
+def resample_scheme(w, J, N, scheme, seed=0, cycle=0):
+    w = _f64(w)
+    idx = np.zeros(J * N, dtype=np.int32)
+    st = _load().or_resample_scheme(_d(w), J, N, scheme, seed, cycle, idx.ctypes.data_as(i32p))
     if st != 0:
         raise ValueError("degenerate group (all weights zero)")
     return idx.reshape(J, N)

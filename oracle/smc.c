@@ -142,6 +142,63 @@ static uint64_t mulhi64(uint64_t a, uint64_t b)
     return (uint64_t)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
 }
 
+/* Stratified (scheme 2) and systematic (scheme 3) resampling, Section 3.3's
+ * experimental alternatives, in the same fixed point: with q_n and Q as for
+ * residual resampling, output slot k takes the particle whose inclusive prefix
+ * of q first exceeds pos_k = floor((k Q + U_k) / N), U_k = mulhi64(x_k, Q);
+ * systematic uses one draw x_0 for all k (counter (group, 0, cycle, 3<<32)),
+ * stratified one draw per slot (counter (group, k, cycle, 3<<32)). */
+static void resample_strat_sys(const uint64_t *q, uint64_t Q, int N, int systematic, uint64_t seed,
+                               uint64_t group, uint64_t cycle, int32_t *idx)
+{
+    const uint64_t key[2] = {seed, 0};
+    uint64_t U0 = 0;
+    if (systematic) {
+        uint64_t ctr[4] = {group, 0, cycle, (uint64_t)OR_TAG_S_RESID << 32}, out[4];
+        or_philox4x64(ctr, key, out);
+        U0 = mulhi64(out[0], Q);
+    }
+    for (int k = 0; k < N; ++k) {
+        uint64_t U = U0;
+        if (!systematic) {
+            uint64_t ctr[4] = {group, (uint64_t)k, cycle, (uint64_t)OR_TAG_S_RESID << 32}, out[4];
+            or_philox4x64(ctr, key, out);
+            U = mulhi64(out[0], Q);
+        }
+        const uint64_t pos = ((uint64_t)k * Q + U) / (uint64_t)N;
+        uint64_t acc = 0;
+        int pick = N - 1;
+        for (int n = 0; n < N; ++n) {
+            acc += q[n];
+            if (acc > pos) { pick = n; break; }
+        }
+        idx[k] = pick;
+    }
+}
+
+int or_resample_scheme(const double *w, int J, int N, int scheme, uint64_t seed, uint64_t cycle,
+                       int32_t *idx)
+{
+    if (scheme <= 1) return or_resample(w, J, N, scheme == 1 ? 0 : 1, seed, cycle, idx);
+    uint64_t *q = malloc(sizeof(uint64_t) * (size_t)N);
+    int status = 0;
+    for (int j = 0; j < J; ++j) {
+        const double *wj = w + (size_t)j * N;
+        double wmax = 0.0;
+        for (int n = 0; n < N; ++n) if (wj[n] > wmax) wmax = wj[n];
+        if (!(wmax > 0.0) || !isfinite(wmax)) { status = -1; continue; }
+        uint64_t Q = 0;
+        for (int n = 0; n < N; ++n) {
+            double wn = wj[n] > 0.0 ? wj[n] / wmax : 0.0;
+            q[n] = (uint64_t)floor(ldexp(wn, 32));
+            Q += q[n];
+        }
+        resample_strat_sys(q, Q, N, scheme == 3, seed, (uint64_t)j, cycle, idx + (size_t)j * N);
+    }
+    free(q);
+    return status;
+}
+
 int or_resample(const double *w, int J, int N, int resid, uint64_t seed,
                 uint64_t cycle, int32_t *idx)
 {
@@ -537,7 +594,8 @@ int or_smc_run(const or_model *m, const double *y, const double *X, int T,
             for (int n = 0; n < N; ++n)
                 w[(size_t)j * N + n] = mx == -INFINITY ? 0.0 : exp(logw[(size_t)j * N + n] - mx);
         }
-        if (or_resample(w, J, N, cfg->resid, cfg->seed, (uint64_t)l, idx) != 0) {
+        const int scheme = cfg->resid == 1 ? 0 : cfg->resid == 0 ? 1 : cfg->resid;
+        if (or_resample_scheme(w, J, N, scheme, cfg->seed, (uint64_t)l, idx) != 0) {
             status = -2;                                        /* degenerate group */
             break;
         }

@@ -550,7 +550,7 @@ static smc_status s_phase(smc_ctx* ctx, int mode)
     s.logw = ctx->logw;
     s.J = c.J;
     s.N = c.N;
-    s.resid = c.resampler == SMC_RESIDUAL;
+    s.scheme = c.resampler;
     s.seed = c.seed;
     s.cycle = (uint64_t)ctx->cycle;
     s.a = ctx->a;

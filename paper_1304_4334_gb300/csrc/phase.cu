@@ -553,12 +553,40 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
         for (int n = tid; n < N; n += blockDim.x) a.idx[base + n] = n;
         return;
     }
+    if (a.scheme >= 2) {
+        // Stratified / systematic: slot k takes the particle whose inclusive
+        // prefix of q first exceeds floor((k Q + U_k) / N), U_k = mulhi64(x, Q).
+        const uint64_t incl = block_inclusive_scan_u64(qloc, redu);
+        uint64_t run = incl - qloc;
+        for (int n = n0; n < n1; ++n) {
+            run += qs[n];
+            qs[n] = run;
+        }
+        __syncthreads();
+        const bool systematic = a.scheme == 3;
+        uint64_t U0 = 0;
+        if (systematic) {
+            const U64x4 x = philox4x64_10((uint64_t)j, 0, a.cycle, (uint64_t)kTagResample << 32, a.seed, 0);
+            U0 = __umul64hi(x.v0, Q);
+        }
+        for (int k = tid; k < N; k += blockDim.x) {
+            uint64_t U = U0;
+            if (!systematic) {
+                const U64x4 x = philox4x64_10((uint64_t)j, (uint64_t)k, a.cycle, (uint64_t)kTagResample << 32,
+                                              a.seed, 0);
+                U = __umul64hi(x.v0, Q);
+            }
+            const uint64_t pos = ((uint64_t)k * Q + U) / (uint64_t)N;
+            a.idx[base + k] = upper_bound_u64(qs, N, pos);
+        }
+        return;
+    }
     // ---- deterministic counts and residuals ----
     uint64_t placed = 0, rloc = 0;
     for (int n = n0; n < n1; ++n) {
         const uint64_t q = qs[n];
         uint64_t c = 0, r = q;
-        if (a.resid) {
+        if (a.scheme == 0) {
             c = ((uint64_t)N * q) / Q;                 // floor(N w~_n)
             r = (uint64_t)N * q - Q * c;
         }

@@ -73,7 +73,7 @@ struct SelectArgs {
     const double* logw;
     const double* w;
     int J, N;
-    int resid;
+    int scheme;       // 0 residual, 1 multinomial, 2 stratified, 3 systematic
     uint64_t seed, cycle;
     double* a;        // [J] += log wbar_j (modes 0, 1)
     double* lw;       // [J] log wbar_j of this cycle (modes 0, 1)

@@ -254,7 +254,7 @@ smc_status smc_power_search(const double* ll, int P, double phi, double d1, int 
         sa.ll = ll;
         sa.J = 1;
         sa.N = P;
-        sa.resid = 1;
+        sa.scheme = 0;
         sa.a = a;
         sa.lw = lw;
         sa.gstat = gstat;
@@ -294,7 +294,7 @@ smc_status smc_resample(const double* w, int J, int N, int resampler, uint64_t s
     sa.w = w;
     sa.J = J;
     sa.N = N;
-    sa.resid = resampler == SMC_RESIDUAL;
+    sa.scheme = resampler;
     sa.seed = seed;
     sa.cycle = cycle;
     sa.idx = idx;

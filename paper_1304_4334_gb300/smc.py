@@ -25,7 +25,7 @@ EGARCH, LINREG = 0, 1
 FP64, FP32 = 0, 1
 DATA, POWER = 0, 1
 RW, MALA = 0, 1
-RESIDUAL, MULTINOMIAL = 0, 1
+RESIDUAL, MULTINOMIAL, STRATIFIED, SYSTEMATIC = 0, 1, 2, 3
 STOP_DET, STOP_RNE = 0, 1
 
 

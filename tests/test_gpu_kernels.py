@@ -290,6 +290,20 @@ def test_resample_bit_exact(S, J, N, resid):
     assert np.array_equal(host(idx).reshape(J, N), idx_o)
 
 
+@pytest.mark.parametrize("J,N,scheme", [(64, 1024, 2), (64, 1024, 3), (3, 1000, 2), (5, 8192, 3),
+                                         (7, 333, 3), (2, 1, 2)])
+def test_stratified_systematic_bit_exact(S, J, N, scheme):
+    torch = torch_cuda()
+    rng = np.random.default_rng(J * N + scheme)
+    w = rng.gamma(0.3, size=J * N)
+    w[rng.random(J * N) < 0.1] = 0.0
+    w.reshape(J, N)[:, 0] += 1e-3
+    idx_o = O.resample_scheme(w, J, N, scheme, seed=5, cycle=2)
+    idx = torch.empty(J * N, dtype=torch.int32, device="cuda")
+    S.resample(dev(w), J, N, idx, scheme, seed=5, cycle=2)
+    assert np.array_equal(host(idx).reshape(J, N), idx_o)
+
+
 def test_resample_dominant_and_degenerate(S):
     torch = torch_cuda()
     N = 8192

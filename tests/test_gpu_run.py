@@ -36,14 +36,16 @@ def _linreg(T=60, seed=3):
 
 
 @pytest.mark.parametrize("resampler,tempering", [("residual", "power"), ("multinomial", "power"),
-                                                ("residual", "data")])
+                                                ("residual", "data"), ("stratified", "power"),
+                                                ("systematic", "data")])
 def test_linreg_run_matches_closed_form(S, resampler, tempering):
     X, y, m0, s0, lml, mn, Vn = _linreg()
     J, N = 16, 512
     m = S.model_linreg(3, 1.0, m0, s0)
     c = S.config_default(J=J, N=N, precision=S.FP64, seed=11,
                          tempering=S.POWER if tempering == "power" else S.DATA,
-                         resampler=S.RESIDUAL if resampler == "residual" else S.MULTINOMIAL)
+                         resampler={"residual": S.RESIDUAL, "multinomial": S.MULTINOMIAL,
+                                    "stratified": S.STRATIFIED, "systematic": S.SYSTEMATIC}[resampler])
     th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), J * N, seed=5)
     ctx = S.init(m, c, y, th0, X=X)
     n, info = ctx.run()

@@ -341,3 +341,37 @@ def test_hybrid_second_run_matches_closed_form(tempering):
     for i in range(3):
         mean, sd, nse, rne = O.moment(b["theta"][:, i], J, N)
         assert abs(mean - mn[i]) < 4.0 * nse + 1e-4
+
+
+# ----------------------------------------- stratified / systematic resampling
+@pytest.mark.parametrize("scheme", [O.STRATIFIED, O.SYSTEMATIC])
+def test_stratified_systematic_properties(scheme):
+    rng = np.random.default_rng(4)
+    N = 64
+    w = rng.gamma(0.7, size=N)
+    wt = w / w.sum()
+    reps = 3000
+    tot = np.zeros(N)
+    for cyc in range(reps):
+        idx = O.resample_scheme(w, 1, N, scheme, seed=3, cycle=cyc)[0]
+        assert np.all(np.diff(idx) >= 0)
+        c = np.bincount(idx, minlength=N)
+        # both schemes give floor(N w~) or ceil(N w~) copies of every particle
+        # (stratified up to one more or less where strata straddle)
+        lo = np.floor(N * wt) - (0 if scheme == O.SYSTEMATIC else 1)
+        hi = np.ceil(N * wt) + (0 if scheme == O.SYSTEMATIC else 1)
+        assert np.all(c >= lo - 1e-9) and np.all(c <= hi + 1e-9)
+        tot += c
+    # unbiased: E[count] = N w~
+    se = np.sqrt(np.maximum(N * wt * (1 - wt), 1e-3) / reps)
+    assert np.all(np.abs(tot / reps - N * wt) < 6 * se + 1e-3)
+
+
+@pytest.mark.parametrize("scheme", [2, 3])
+def test_full_run_with_stratified_and_systematic(scheme):
+    spec, X, y, lml, mn, Vn, (m0, s0) = _linreg_problem()
+    J, N = 8, 512
+    th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), J * N, seed=41)
+    r = O.smc_run(spec, y, th0, J, N, X=X, resid=scheme, seed=13)
+    assert r["status"] == 0
+    assert abs(r["log_ml"] - lml) < 4.0 * r["log_ml_nse"] + 0.02
