@@ -147,6 +147,16 @@ long or_mutate_mala(const or_model *m, const double *y, const double *X, int T,
                     uint64_t seed, uint64_t cycle, uint64_t iter, int *accept,
                     int nthreads);
 
+/* One independent Gaussian Metropolis step (Section 3.3's alternative
+ * sampler): theta' = mbar + L z with q = N(mbar, L L^T) the same for every
+ * particle; acceptance includes log q(theta) - log q(theta').  A zero pivot of
+ * L contributes nothing to log q (the oracle's singular-factor rule).         */
+long or_mutate_indep(const or_model *m, const double *y, const double *X, int T,
+                     double *theta, double *loglik, double *logprior, double *state,
+                     int P, const double *mbar, const double *L, double phi,
+                     uint64_t seed, uint64_t cycle, uint64_t iter, int *accept,
+                     int nthreads);
+
 /* ---- C phase ---------------------------------------------------------------- */
 /* Power tempering: find dphi in (0, 1-phi] with RSS(dphi) = D1 by bisection
  * (RSS(1-phi) >= D1 gives 1-phi).  Returns dphi; rss_out gets RSS(dphi).     */
@@ -157,7 +167,9 @@ double or_power_search(const double *loglik, int P, double phi, double d1,
 typedef struct {
     int J, N;
     int tempering;      /* 0 = data (paper), 1 = power                          */
-    int mutation;       /* 0 = random walk, 1 = MALA                            */
+    int mutation;       /* 0 = random walk, 1 = MALA, 2 = independent Gaussian
+                           (Sigma = V, the pooled variance; mean = pooled mean;
+                           no replay or recording)                           */
     int resid;          /* 1 residual, 0 multinomial, 2 stratified, 3 systematic */
     double d1, d2;
     int stop_rule;      /* 0 deterministic, 1 RNE                               */

@@ -123,6 +123,9 @@ def _declare(L):
     L.or_mutate_mala.argtypes = [C.POINTER(Model), dp, dp, C.c_int, dp, dp, dp, dp, dp, C.c_int,
                                  dp, C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, ip, C.c_int]
     L.or_mutate_mala.restype = C.c_long
+    L.or_mutate_indep.argtypes = [C.POINTER(Model), dp, dp, C.c_int, dp, dp, dp, dp, C.c_int, dp, dp,
+                                  C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, ip, C.c_int]
+    L.or_mutate_indep.restype = C.c_long
     L.or_power_search.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_int, dp]
     L.or_power_search.restype = C.c_double
     L.or_smc_run.argtypes = [C.POINTER(Model), dp, dp, C.c_int, C.POINTER(RunCfg), dp, dp, dp,
@@ -326,6 +329,7 @@ def resample(w, J, N, resid=True, seed=0, cycle=0):
 
 
 RESIDUAL, MULTINOMIAL, STRATIFIED, SYSTEMATIC = 0, 1, 2, 3
+RW, MALA, INDEP = 0, 1, 2
 
 
 def resample_scheme(w, J, N, scheme, seed=0, cycle=0):
@@ -363,6 +367,19 @@ def mutate_rw(spec, y, theta, ll, lp, state, Lmat, phi, seed, cycle, it, X=None,
     n = _load().or_mutate_rw(C.byref(spec.c), _d(_f64(y)), _d(_f64(X) if X is not None else None),
                              len(y), _d(theta), _d(ll), _d(lp), _d(state), P, _d(_f64(Lmat)),
                              phi, seed, cycle, it, acc.ctypes.data_as(ip), nthreads)
+    return theta, ll, lp, state, acc, n
+
+
+def mutate_indep(spec, y, theta, ll, lp, state, mbar, Lmat, phi, seed, cycle, it, X=None, nthreads=1):
+    """One independent Gaussian Metropolis step with proposal N(mbar, L L^T)
+    (Section 3.3's alternative sampler); returns new arrays."""
+    theta = _f64(theta).copy(); ll = _f64(ll).copy(); lp = _f64(lp).copy()
+    state = _f64(state).copy()
+    P = theta.shape[0]
+    acc = np.zeros(P, dtype=np.int32)
+    n = _load().or_mutate_indep(C.byref(spec.c), _d(_f64(y)), _d(_f64(X) if X is not None else None),
+                                len(y), _d(theta), _d(ll), _d(lp), _d(state), P, _d(_f64(mbar)),
+                                _d(_f64(Lmat)), phi, seed, cycle, it, acc.ctypes.data_as(ip), nthreads)
     return theta, ll, lp, state, acc, n
 
 

@@ -363,6 +363,54 @@ static double half_quad_inv(const double *L, int d, const double *r)
     return -0.5 * q;
 }
 
+/* Independent Gaussian sampler (Section 3.3, the alternative to the random
+ * walk): proposal theta' = mbar + L z, z ~ N(0, I), the same proposal for every
+ * particle's current value; accepted when log u is below
+ * [target(theta') - target(theta)] + [log q(theta) - log q(theta')], q the
+ * N(mbar, L L^T) density, whose normalising constant cancels.
+ * log q(theta') - const = -|z|^2 / 2 because theta' - mbar = L z. */
+long or_mutate_indep(const or_model *m, const double *y, const double *X, int T,
+                     double *theta, double *loglik, double *logprior, double *state,
+                     int P, const double *mbar, const double *L, double phi,
+                     uint64_t seed, uint64_t cycle, uint64_t iter, int *accept,
+                     int nthreads)
+{
+    const int d = m->d;
+    const int ns = m->model == OR_EGARCH ? m->K + 1 : 0;
+    long total = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : total) num_threads(nthreads > 0 ? nthreads : 1) if (nthreads > 1)
+    for (int n = 0; n < P; ++n) {
+        double z[64], prop[64], r[64], st[9] = {0};
+        double *th = theta + (size_t)n * d;
+        or_philox_normals(seed, (uint64_t)n, iter, cycle, d, z);
+        double zz = 0.0;
+        for (int i = 0; i < d; ++i) {
+            double s = 0.0;
+            for (int k = 0; k <= i; ++k) s += L[i * d + k] * z[k];
+            prop[i] = mbar[i] + s;
+            zz += z[i] * z[i];
+            r[i] = th[i] - mbar[i];
+        }
+        double lp = or_logprior(m, prop);
+        double ll = lp == -INFINITY ? -INFINITY : or_loglik(m, y, X, T, prop, st);
+        double lq_cur = half_quad_inv(L, d, r);            /* log q(theta)  + const */
+        double lq_prop = -0.5 * zz;                         /* log q(theta') + const */
+        double log_alpha = target(lp, ll, phi) - target(logprior[n], loglik[n], phi)
+                         + lq_cur - lq_prop;
+        double log_u = or_philox_log_uniform(seed, (uint64_t)n, iter, cycle);
+        int acc = log_u < log_alpha;
+        if (acc) {
+            memcpy(th, prop, sizeof(double) * (size_t)d);
+            loglik[n] = ll;
+            logprior[n] = lp;
+            if (state && ns) for (int k = 0; k < ns; ++k) state[(size_t)n * ns + k] = st[k];
+        }
+        if (accept) accept[n] = acc;
+        total += acc;
+    }
+    return total;
+}
+
 long or_mutate_mala(const or_model *m, const double *y, const double *X, int T,
                     double *theta, double *loglik, double *logprior, double *grad,
                     double *state, int P, const double *L, double phi,
@@ -503,6 +551,12 @@ int or_smc_run(const or_model *m, const double *y, const double *X, int T,
     const int J = cfg->J, N = cfg->N, P = J * N, d = m->d;
     const int ns = m->model == OR_EGARCH ? m->K + 1 : 1;
     const int power = cfg->tempering == 1;
+    if (cfg->mutation == 2 && (cfg->replay || cfg->rec_L)) {
+        /* a recorded design holds the factors L only, not the proposal means */
+        memset(out, 0, sizeof *out);
+        out->status = -4;
+        return -4;
+    }
     double *logw = calloc((size_t)P, sizeof(double));
     double *w = calloc((size_t)P, sizeof(double));
     double *tmp = calloc((size_t)P * (d > ns ? d : ns) + (size_t)P, sizeof(double));
@@ -623,8 +677,10 @@ int or_smc_run(const or_model *m, const double *y, const double *X, int T,
                 ++replay_iter;
             } else {
                 or_mean_cov(theta, P, d, mean, V);
-                double hh = (h / 10.0) * (h / 10.0);
-                for (int i = 0; i < d * d; ++i) Sig[i] = hh * V[i];      /* Sigma = h^2 V */
+                /* Sigma = h^2 V (random walk, MALA); V itself for the
+                 * independent sampler, which has no step size */
+                double hh = cfg->mutation == 2 ? 1.0 : (h / 10.0) * (h / 10.0);
+                for (int i = 0; i < d * d; ++i) Sig[i] = hh * V[i];
                 or_cholesky(Sig, d, L);
             }
             if (cfg->rec_L && out->metropolis_steps < cfg->rec_L_cap)
@@ -632,6 +688,9 @@ int or_smc_run(const or_model *m, const double *y, const double *X, int T,
             long acc = cfg->mutation == 1
                 ? or_mutate_mala(m, y, X, Tm, theta, loglik, logprior, grad, state, P, L,
                                  phim, cfg->seed, (uint64_t)l, (uint64_t)r, NULL, cfg->nthreads)
+                : cfg->mutation == 2
+                ? or_mutate_indep(m, y, X, Tm, theta, loglik, logprior, state, P, mean, L, phim,
+                                  cfg->seed, (uint64_t)l, (uint64_t)r, NULL, cfg->nthreads)
                 : or_mutate_rw(m, y, X, Tm, theta, loglik, logprior, state, P, L, phim,
                                cfg->seed, (uint64_t)l, (uint64_t)r, NULL, cfg->nthreads);
             out->metropolis_steps += 1;

@@ -375,3 +375,66 @@ def test_full_run_with_stratified_and_systematic(scheme):
     r = O.smc_run(spec, y, th0, J, N, X=X, resid=scheme, seed=13)
     assert r["status"] == 0
     assert abs(r["log_ml"] - lml) < 4.0 * r["log_ml_nse"] + 0.02
+
+
+# ------------------------------------------- independent Gaussian sampler
+def test_indep_with_exact_posterior_proposal_accepts_every_draw():
+    """With q equal to the (Gaussian) posterior the Metropolis ratio is exactly
+    1, so every proposal is accepted and lands at mbar + L z (Section 3.3's
+    independent sampler; a sign slip in the q correction rejects many)."""
+    spec, X, y, _, mn, Vn, _ = _linreg_problem()
+    rng = np.random.default_rng(31)
+    P = 3000
+    th = rng.multivariate_normal(mn + 0.3, 2.0 * Vn, size=P)
+    ll = O.loglik(spec, y, th, X=X)
+    lp = O.logprior(spec, th)
+    L = np.linalg.cholesky(Vn)
+    st = np.zeros((P, 1))
+    th2, ll2, lp2, _, acc, n = O.mutate_indep(spec, y, th, ll, lp, st, mn, L, 1.0, 7, 2, 3, X=X)
+    assert n == P and acc.all()
+    for p in (0, 17, P - 1):
+        z = O.philox_normals(7, p, 3, 2, 3)
+        np.testing.assert_allclose(th2[p], mn + L @ z, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(ll2, O.loglik(spec, y, th2, X=X), rtol=1e-13)
+    # phi = 0 targets the prior: the prior as proposal is accepted everywhere
+    m0, s0 = np.zeros(3), np.full(3, 2.0)
+    _, _, _, _, acc0, n0 = O.mutate_indep(spec, y, th, ll, lp, st, m0, np.diag(s0), 0.0, 7, 2, 4, X=X)
+    assert n0 == P
+    # a proposal off the posterior is not accepted everywhere
+    _, _, _, _, _, n1 = O.mutate_indep(spec, y, th, ll, lp, st, mn + 0.05, L, 1.0, 7, 2, 3, X=X)
+    assert n1 < P
+
+
+def test_indep_kernel_leaves_posterior_invariant():
+    """A proposal wider than and offset from the posterior still leaves the
+    posterior invariant (detailed balance needs the q correction)."""
+    spec, X, y, _, mn, Vn, _ = _linreg_problem()
+    rng = np.random.default_rng(32)
+    P = 20000
+    th = rng.multivariate_normal(mn, Vn, size=P)
+    ll = O.loglik(spec, y, th, X=X)
+    lp = O.logprior(spec, th)
+    L = np.linalg.cholesky(1.5 ** 2 * Vn)
+    mbar = mn + 0.5 * np.sqrt(np.diag(Vn))
+    st = np.zeros((P, 1))
+    for it in range(4):
+        th, ll, lp, st, acc, nacc = O.mutate_indep(spec, y, th, ll, lp, st, mbar, L, 1.0, 9, 1, it, X=X)
+    assert 0.2 < nacc / P < 0.9
+    se = np.sqrt(np.diag(Vn) / P) * 2
+    assert np.all(np.abs(th.mean(axis=0) - mn) < 4 * se)
+    np.testing.assert_allclose(np.cov(th.T), Vn, rtol=0.06, atol=0.03 * np.abs(Vn).max())
+
+
+@pytest.mark.parametrize("tempering", [0, 1])
+def test_full_run_independent_sampler_matches_closed_form(tempering):
+    spec, X, y, lml, mn, Vn, (m0, s0) = _linreg_problem()
+    J, N = 8, 512
+    th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), J * N, seed=43)
+    r = O.smc_run(spec, y, th0, J, N, X=X, tempering=tempering, mutation=O.INDEP, seed=17)
+    assert r["status"] == 0
+    assert abs(r["log_ml"] - lml) < 4.0 * r["log_ml_nse"] + 0.02
+    for i in range(3):
+        mean, sd, nse, rne = O.moment(r["theta"][:, i], J, N)
+        assert abs(mean - mn[i]) < 4 * nse + 1e-4
+    # a recorded design holds no proposal means: the independent sampler refuses it
+    assert O.smc_run(spec, y, th0, J, N, X=X, mutation=O.INDEP, record=True)["status"] == -4
