@@ -85,7 +85,7 @@ void or_egarch_transform(int K, int I, int gamma, const double *th, or_egarch_pa
     }
 }
 
-static void full_theta(const or_model *m, const double *theta, double *full)
+void or_full_theta(const or_model *m, const double *theta, double *full)
 {
     if (!m->free_idx) {
         memcpy(full, theta, sizeof(double) * (size_t)m->d_full);
@@ -191,7 +191,7 @@ double or_loglik_range(const or_model *m, const double *y, const double *X,
                        int t0, int t1, const double *theta, double *state)
 {
     double full[64];
-    full_theta(m, theta, full);
+    or_full_theta(m, theta, full);
     double s;
     if (m->model == OR_LINREG) {
         s = linreg_range(m, full, y, X, t0, t1, NULL);
@@ -217,7 +217,7 @@ void or_loglik_terms(const or_model *m, const double *y, const double *X, int T,
                      const double *theta, double *lt)
 {
     double full[64];
-    full_theta(m, theta, full);
+    or_full_theta(m, theta, full);
     if (m->model == OR_LINREG) {
         linreg_range(m, full, y, X, 0, T, lt);
     } else {
@@ -235,7 +235,7 @@ void or_loglik_terms(const or_model *m, const double *y, const double *X, int T,
 void or_egarch_testfn(const or_model *m, const double *theta, const double *state, double g[3])
 {
     double full[64];
-    full_theta(m, theta, full);
+    or_full_theta(m, theta, full);
     or_egarch_par q;
     or_egarch_transform(m->K, m->I, m->gamma, full, &q);
     const int K = m->K, I = m->I;
@@ -363,7 +363,7 @@ double or_loglik_grad(const or_model *m, const double *y, const double *X, int T
                       const double *theta, double *grad)
 {
     double full[64];
-    full_theta(m, theta, full);
+    or_full_theta(m, theta, full);
     double val = 0.0;
     for (int j = 0; j < m->d; ++j) {
         dual fd[64];

@@ -38,6 +38,7 @@ double or_philox_log_uniform(uint64_t seed, uint64_t p, uint64_t iter, uint64_t 
 #define OR_TAG_M_NORMAL  1u   /* Gaussian proposal normals (M phase)          */
 #define OR_TAG_M_UNIFORM 2u   /* Metropolis-Hastings uniform (M phase)        */
 #define OR_TAG_S_RESID   3u   /* residual / multinomial draws (S phase)       */
+#define OR_TAG_C_PIT     4u   /* PIT auxiliary draw Y_s (C phase, Section 4.1) */
 
 /* ---- model description ---------------------------------------------------- */
 enum { OR_EGARCH = 0, OR_LINREG = 1 };
@@ -69,6 +70,9 @@ typedef struct {
     double p[8], mu[8], sig[8];
 } or_egarch_par;
 void or_egarch_transform(int K, int I, int gamma, const double *theta_full, or_egarch_par *par);
+
+/* Full parameter vector from the free ones (fixed values fill the rest). */
+void or_full_theta(const or_model *m, const double *theta, double *full);
 
 /* Log prior density kernel over free parameters; -inf outside the support. */
 double or_logprior(const or_model *m, const double *theta);
@@ -124,6 +128,16 @@ int or_resample(const double *w, int J, int N, int resid, uint64_t seed,
  * (the last two are the paper's experimental alternatives). */
 int or_resample_scheme(const double *w, int J, int N, int scheme, uint64_t seed,
                        uint64_t cycle, int32_t *idx);
+
+/* ---- probability integral transform (Section 4.1) -------------------------- */
+/* Simulated standardized shock of Y_s ~ p(Y_s | y_{1:s-1}, theta) for particle
+ * `particle` (Philox counter (particle, s, 0, OR_TAG_C_PIT << 32)), and the
+ * observed one e_s (EGARCH: from the state after the step through y_s).
+ * Y_s <= y_s exactly when the simulated shock is <= e_s.                      */
+double or_pit_shock(const or_model *m, const double *theta, uint64_t seed,
+                    uint64_t particle, int s);
+double or_obs_shock(const or_model *m, const double *y, const double *X, int s,
+                    const double *theta, const double *state_after);
 
 /* ---- covariance & Cholesky (Section 3.3 "Metropolis steps") ---------------- */
 void or_mean_cov(const double *theta, int P, int d, double *mean, double *cov);
@@ -196,6 +210,13 @@ typedef struct {
     const double *design_L;
     double *rec_L;
     int rec_L_cap;
+    /* Section 4.1 (data tempering only).  burnin b > 0: a cycle ends at t = b
+     * and the log score log p(y_{b+1:T} | y_{1:b}) is the group-product
+     * estimator over the cycles after b.  pit_out[T] (nullable): at each s the
+     * weighted fraction of particles whose simulated Y_s is <= y_s, with the
+     * weights w(s-1) of the C phase. */
+    int burnin;
+    double *pit_out;
 } or_run_cfg;
 
 typedef struct {
@@ -205,6 +226,7 @@ typedef struct {
     double log_ml, log_ml_nse, log_ml_tilde;
     int h_final_tenths;
     int status;                   /* 0 ok; <0 error                             */
+    double log_score, log_score_nse;  /* NaN without a burn-in               */
 } or_run_out;
 
 /* Runs the simulator from prior draws theta0[P][d] to the full sample.  On

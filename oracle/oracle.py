@@ -74,14 +74,15 @@ class RunCfg(C.Structure):
                 ("bisect_iters", C.c_int), ("seed", C.c_uint64), ("max_cycles", C.c_int),
                 ("nthreads", C.c_int), ("replay", C.c_int), ("n_design", C.c_int),
                 ("design_x", dp), ("design_R", ip), ("design_L", dp), ("rec_L", dp),
-                ("rec_L_cap", C.c_int)]
+                ("rec_L_cap", C.c_int), ("burnin", C.c_int), ("pit_out", dp)]
 
 
 class RunOut(C.Structure):
     _fields_ = [("cycles", C.c_int), ("metropolis_steps", C.c_long),
                 ("particle_obs_evals", C.c_double), ("log_ml", C.c_double),
                 ("log_ml_nse", C.c_double), ("log_ml_tilde", C.c_double),
-                ("h_final_tenths", C.c_int), ("status", C.c_int)]
+                ("h_final_tenths", C.c_int), ("status", C.c_int),
+                ("log_score", C.c_double), ("log_score_nse", C.c_double)]
 
 
 def _declare(L):
@@ -126,6 +127,8 @@ def _declare(L):
     L.or_mutate_indep.argtypes = [C.POINTER(Model), dp, dp, C.c_int, dp, dp, dp, dp, C.c_int, dp, dp,
                                   C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, ip, C.c_int]
     L.or_mutate_indep.restype = C.c_long
+    L.or_pit_shock.argtypes = [C.POINTER(Model), dp, C.c_uint64, C.c_uint64, C.c_int]
+    L.or_pit_shock.restype = C.c_double
     L.or_power_search.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_int, dp]
     L.or_power_search.restype = C.c_double
     L.or_smc_run.argtypes = [C.POINTER(Model), dp, dp, C.c_int, C.POINTER(RunCfg), dp, dp, dp,
@@ -395,6 +398,11 @@ def mutate_mala(spec, y, theta, ll, lp, grad, state, Lmat, phi, seed, cycle, it,
     return theta, ll, lp, grad, state, acc, n
 
 
+def pit_shock(spec, theta, seed, particle, s):
+    """Simulated standardized shock of the PIT draw Y_s (Section 4.1)."""
+    return _load().or_pit_shock(C.byref(spec.c), _d(_f64(theta)), seed, particle, s)
+
+
 def power_search(ll, phi, d1=0.5, iters=60):
     ll = _f64(ll)
     r = C.c_double()
@@ -408,8 +416,13 @@ DEFAULT_RUN = dict(tempering=1, mutation=0, resid=1, d1=0.5, d2=0.2, stop_rule=0
                    seed=1, max_cycles=10000, nthreads=1)
 
 
-def smc_run(spec, y, theta0, J, N, X=None, force_dates=(), design=None, record=False, **kw):
+def smc_run(spec, y, theta0, J, N, X=None, force_dates=(), design=None, record=False, burnin=0,
+            pit=False, **kw):
     """Full adaptive run (Algorithm 2 with the Section 3.3 specifics).
+
+    burnin=b > 0 (data tempering) also returns the log score log p(y_{b+1:T} |
+    y_{1:b}) with its NSE; pit=True the probability integral transform of
+    every observation (Section 4.1).
 
     record=True also returns the design of Algorithm 3 (end of each cycle, its
     iteration count and every iteration's proposal Cholesky factor);
@@ -431,7 +444,11 @@ def smc_run(spec, y, theta0, J, N, X=None, force_dates=(), design=None, record=F
                  o["h0_tenths"], o["hmin_tenths"], o["hmax_tenths"], o["acc_target"],
                  o["h_reset_each_cycle"], fd.ctypes.data_as(ip) if len(fd) else None, len(fd),
                  o["bisect_iters"], o["seed"], o["max_cycles"], o["nthreads"], *rep,
-                 rec_L.ctypes.data_as(dp) if record else None, cap if record else 0)
+                 rec_L.ctypes.data_as(dp) if record else None, cap if record else 0,
+                 int(burnin), None)
+    pit_arr = np.full(len(y), np.nan) if pit else None
+    if pit:
+        cfg.pit_out = pit_arr.ctypes.data_as(dp)
     P = J * N
     theta0 = _f64(theta0)
     assert theta0.shape == (P, spec.d)
@@ -455,5 +472,6 @@ def smc_run(spec, y, theta0, J, N, X=None, force_dates=(), design=None, record=F
     return dict(status=out.status, cycles=L, metropolis_steps=out.metropolis_steps, design=res_design,
                 evals=out.particle_obs_evals, log_ml=out.log_ml, log_ml_nse=out.log_ml_nse,
                 log_ml_tilde=out.log_ml_tilde, h_final=out.h_final_tenths, theta=theta,
+                log_score=out.log_score, log_score_nse=out.log_score_nse, pit=pit_arr,
                 loglik=ll, logprior=lp, state=state, a=a, t=t_rec[:L].copy(),
                 phi=phi_rec[:L].copy(), R=r_rec[:L].copy(), rss=rss_rec[:L].copy())

@@ -70,6 +70,49 @@ double or_philox_log_uniform(uint64_t seed, uint64_t p, uint64_t iter, uint64_t 
     return log(u53(out[0]));
 }
 
+/* ------------------------ probability integral transform ------------------ */
+/* Section 4.1: Y_s ~ p(Y_s | y_{1:s-1}, theta) is location + scale * e with e the
+ * standardized shock (EGARCH: location mu_Y, scale h_s; LINREG: x_s'beta and
+ * sigma), so I[Y_s <= y_s] = I[e <= e_s].  The simulated e takes mixture
+ * component i when the uniform u_c falls in [p_1 + .. + p_{i-1}, p_1 + .. + p_i),
+ * then mu_i + sigma_i z (LINREG: z), z Box-Muller from the next two uniforms;
+ * all three come from the Philox block at counter (particle, s, 0, tag 4). */
+double or_pit_shock(const or_model *m, const double *theta, uint64_t seed,
+                    uint64_t particle, int s)
+{
+    const uint64_t key[2] = {seed, 0};
+    uint64_t ctr[4] = {particle, (uint64_t)s, 0, (uint64_t)OR_TAG_C_PIT << 32};
+    uint64_t out[4];
+    or_philox4x64(ctr, key, out);
+    double uc = u53(out[0]);
+    double z = sqrt(-2.0 * log(u53(out[1]))) * cos(2.0 * M_PI * u53(out[2]));
+    if (m->model == OR_LINREG) return z;
+    double full[64];
+    or_full_theta(m, theta, full);
+    or_egarch_par q;
+    or_egarch_transform(m->K, m->I, m->gamma, full, &q);
+    int comp = m->I - 1;
+    double cum = 0.0;
+    for (int i = 0; i < m->I; ++i) {
+        cum += q.p[i];
+        if (uc < cum) { comp = i; break; }
+    }
+    return q.mu[comp] + q.sig[comp] * z;
+}
+
+/* Observed standardized shock e_s: EGARCH reads eps_s from the state after the
+ * step through y_s; LINREG computes (y_s - x_s'beta) / sigma. */
+double or_obs_shock(const or_model *m, const double *y, const double *X, int s,
+                    const double *theta, const double *state_after)
+{
+    if (m->model == OR_EGARCH) return state_after[m->K];
+    double full[64];
+    or_full_theta(m, theta, full);
+    double mean = 0.0;
+    for (int i = 0; i < m->p; ++i) mean += X[(size_t)(s - 1) * m->p + i] * full[i];
+    return (y[s - 1] - mean) / m->sigma;
+}
+
 /* ------------------------------ estimators -------------------------------- */
 void or_moment(const double *g, int J, int N, double *mean, double *sd,
                double *nse, double *rne)
@@ -513,6 +556,7 @@ static void gather_rows(double *a, const int32_t *src, int J, int N, int width, 
 
 static int is_forced(const or_run_cfg *c, int s)
 {
+    if (c->burnin > 0 && s == c->burnin) return 1;    /* log score boundary */
     for (int i = 0; i < c->n_force; ++i) if (c->force_dates[i] == s) return 1;
     return 0;
 }
@@ -551,6 +595,12 @@ int or_smc_run(const or_model *m, const double *y, const double *X, int T,
     const int J = cfg->J, N = cfg->N, P = J * N, d = m->d;
     const int ns = m->model == OR_EGARCH ? m->K + 1 : 1;
     const int power = cfg->tempering == 1;
+    if (power && (cfg->burnin > 0 || cfg->pit_out)) {
+        /* the log score and PIT walk the observations: data tempering only */
+        memset(out, 0, sizeof *out);
+        out->status = -5;
+        return -5;
+    }
     if (cfg->mutation == 2 && (cfg->replay || cfg->rec_L)) {
         /* a recorded design holds the factors L only, not the proposal means */
         memset(out, 0, sizeof *out);
@@ -563,6 +613,7 @@ int or_smc_run(const or_model *m, const double *y, const double *X, int T,
     double *grad = calloc((size_t)P * d, sizeof(double));
     double *gbuf = calloc((size_t)P * (d > 3 ? d : 3), sizeof(double));
     double *lwj = calloc((size_t)J, sizeof(double));
+    double *a_score = calloc((size_t)J, sizeof(double));
     int32_t *idx = calloc((size_t)P, sizeof(int32_t));
     double V[64 * 64], Sig[64 * 64], L[64 * 64], mean[64];
     memset(out, 0, sizeof(*out));
@@ -616,12 +667,24 @@ int or_smc_run(const or_model *m, const double *y, const double *X, int T,
             int s = t_prev;
             for (;;) {
                 ++s;
+                double lwmax = -INFINITY, pit_num = 0.0, pit_den = 0.0;
+                if (cfg->pit_out)
+                    for (int n = 0; n < P; ++n) if (logw[n] > lwmax) lwmax = logw[n];
                 for (int n = 0; n < P; ++n) {                   /* (C_phase_compute) */
+                    /* w(s-1), the weight before y_s (Section 4.1 PIT) */
+                    double wprev = cfg->pit_out && logw[n] != -INFINITY ? exp(logw[n] - lwmax) : 0.0;
                     double inc = or_loglik_range(m, y, X, s - 1, s, theta + (size_t)n * d,
                                                  state + (size_t)n * ns);
                     logw[n] += inc;
                     loglik[n] += inc;
+                    if (cfg->pit_out) {
+                        double es = or_obs_shock(m, y, X, s, theta + (size_t)n * d, state + (size_t)n * ns);
+                        double ed = or_pit_shock(m, theta + (size_t)n * d, cfg->seed, (uint64_t)n, s);
+                        pit_den += wprev;
+                        if (ed <= es) pit_num += wprev;
+                    }
                 }
+                if (cfg->pit_out) cfg->pit_out[s - 1] = pit_num / pit_den;
                 rss = or_ess_log(logw, P) / P;
                 if (cfg->replay) {
                     if (s >= (int)cfg->design_x[l - 1]) { forced = s == T; break; }
@@ -639,6 +702,7 @@ int or_smc_run(const or_model *m, const double *y, const double *X, int T,
         for (int j = 0; j < J; ++j) {
             lwj[j] = logsumexp(logw + (size_t)j * N, N) - log((double)N);
             a_out[j] += lwj[j];
+            if (cfg->burnin > 0 && t_prev >= cfg->burnin) a_score[j] += lwj[j];  /* cycles after b */
         }
         ltilde += logsumexp(lwj, J) - log((double)J);
         /* ---- S phase ---- */
@@ -706,9 +770,11 @@ int or_smc_run(const or_model *m, const double *y, const double *X, int T,
     }
     out->cycles = l;
     or_log_ml(a_out, J, &out->log_ml, &out->log_ml_nse);
+    out->log_score = out->log_score_nse = NAN;
+    if (cfg->burnin > 0 && cfg->burnin < T) or_log_ml(a_score, J, &out->log_score, &out->log_score_nse);
     out->log_ml_tilde = ltilde;
     out->h_final_tenths = h;
     out->status = status;
-    free(logw); free(w); free(tmp); free(grad); free(gbuf); free(lwj); free(idx);
+    free(logw); free(w); free(tmp); free(grad); free(gbuf); free(lwj); free(idx); free(a_score);
     return status;
 }

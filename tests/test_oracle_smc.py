@@ -438,3 +438,69 @@ def test_full_run_independent_sampler_matches_closed_form(tempering):
         assert abs(mean - mn[i]) < 4 * nse + 1e-4
     # a recorded design holds no proposal means: the independent sampler refuses it
     assert O.smc_run(spec, y, th0, J, N, X=X, mutation=O.INDEP, record=True)["status"] == -4
+
+
+# ------------------------------------------ log score and PIT (Section 4.1)
+def _linreg_prefix_lml(X, y, m0, s0, t):
+    V0 = np.diag(s0 ** 2)
+    return stats.multivariate_normal(X[:t] @ m0, np.eye(t) + X[:t] @ V0 @ X[:t].T).logpdf(y[:t])
+
+
+def test_log_score_matches_closed_form():
+    """log p(y_{b+1:T} | y_{1:b}) = log p(y_{1:T}) - log p(y_{1:b}) for the
+    conjugate regression; the run ends a cycle at b."""
+    spec, X, y, lml, mn, Vn, (m0, s0) = _linreg_problem()
+    b = 20
+    exact = lml - _linreg_prefix_lml(X, y, m0, s0, b)
+    J, N = 8, 512
+    th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), J * N, seed=51)
+    r = O.smc_run(spec, y, th0, J, N, X=X, tempering=0, burnin=b, seed=19)
+    assert r["status"] == 0 and b in r["t"]
+    assert abs(r["log_score"] - exact) < 4 * r["log_score_nse"] + 0.02, (r["log_score"], exact)
+    assert abs(r["log_ml"] - lml) < 4 * r["log_ml_nse"] + 0.02
+    # the log score is the later factor of the log ML, and nothing without a burn-in
+    assert r["log_score"] > r["log_ml"]
+    r0 = O.smc_run(spec, y, th0, J, N, X=X, tempering=0, seed=19)
+    assert math.isnan(r0["log_score"])
+    assert O.smc_run(spec, y, th0, J, N, X=X, tempering=1, burnin=b)["status"] == -5
+
+
+def test_pit_matches_closed_form_predictive_cdf():
+    """PIT of y_s: the weighted share of simulated Y_s <= y_s tracks the exact
+    predictive CDF Phi((y_s - x_s'm_{s-1}) / (sigma^2 + x_s'V_{s-1}x_s)^{1/2})."""
+    spec, X, y, lml, mn, Vn, (m0, s0) = _linreg_problem()
+    J, N = 8, 1024
+    th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), J * N, seed=52)
+    r = O.smc_run(spec, y, th0, J, N, X=X, tempering=0, pit=True, seed=23)
+    assert r["status"] == 0
+    Vinv, b = np.diag(1 / s0 ** 2), np.diag(1 / s0 ** 2) @ m0
+    exact = np.zeros(len(y))
+    for s in range(len(y)):
+        V = np.linalg.inv(Vinv)
+        m = V @ b
+        x = X[s]
+        exact[s] = stats.norm.cdf((y[s] - x @ m) / math.sqrt(1.0 + x @ V @ x))
+        Vinv = Vinv + np.outer(x, x)
+        b = b + x * y[s]
+    err = np.abs(r["pit"] - exact)
+    assert err.max() < 0.08 and err.mean() < 0.02, (err.max(), err.mean())
+    # under the true model the transforms are uniform on (0, 1)
+    assert stats.kstest(exact, "uniform").pvalue > 1e-3
+
+
+def test_pit_shock_draws_the_mixture():
+    """The simulated standardized shock of an EGARCH particle follows its
+    normal mixture (Kolmogorov-Smirnov against the mixture CDF)."""
+    spec = O.ModelSpec(K=1, I=2, gamma=True)
+    mean, sd, lo = O.table1_prior(1, 2)
+    th = I.draw_prior(mean, sd, lo, 1, seed=4)[0]
+    par = O.egarch_transform(1, 2, True, th)
+    assert min(par["p"]) < 0.4 and abs(par["mu"][0]) > 0.05   # an uneven, shifted mixture
+    e = np.array([O.pit_shock(spec, th, 9, n, 3) for n in range(20000)])
+    p, mu, sg = par["p"][:2], par["mu"][:2], par["sig"][:2]
+    cdf = lambda x: sum(p[i] * stats.norm.cdf((x - mu[i]) / sg[i]) for i in range(2))
+    assert stats.kstest(e, cdf).pvalue > 1e-3
+    assert abs(e.mean()) < 0.03 and abs(e.var() - 1.0) < 0.05      # unit-variance mixture
+    spec1 = O.ModelSpec(K=1, I=1, gamma=False)
+    e1 = np.array([O.pit_shock(spec1, np.zeros(spec1.d), 9, n, 3) for n in range(20000)])
+    assert stats.kstest(e1, "norm").pvalue > 1e-3
