@@ -36,6 +36,11 @@ if ROOT not in sys.path:
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT_GB300 = 152
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per k_mutate launch, by
+# (workload, particles per thread, threads per block)
+MUTATE_TRAFFIC = {("egarch22_T5000", 1, 128): 8_751_872 + 55_296,
+                  ("egarch22_T5000", 1, 64): 8_746_496 + 80_896,
+                  ("egarch22_T5000", 1, 32): 8_752_128 + 73_984}
 SM_MAX_MHZ_FALLBACK = 2070.0
 L2_FLUSH_BYTES = 256 << 20
 
@@ -51,6 +56,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cycles", type=int, default=0, help="cap on cycles per run (0 = full run; profiling only)")
     ap.add_argument("--no-equal-nse", action="store_true")
+    ap.add_argument("--launch-shape", default="", help="PPT,THREADS: fixed mutation launch shape instead of autotuning")
     ap.add_argument("--equal-nse-seeds", type=int, default=3)
     return ap.parse_args()
 
@@ -284,7 +290,12 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     with torch.cuda.stream(stream):
         ctx = S.init(m, cfg, y, th0, stream=stream.cuda_stream)
-    shape = ctx.autotune(iters=2) if not mala else (1, 128, None)
+    if args.launch_shape:
+        ppt, thr = (int(v) for v in args.launch_shape.split(","))
+        ctx.set_launch_shape(ppt, thr)
+        shape = (ppt, thr, None)
+    else:
+        shape = ctx.autotune(iters=2) if not mala else (1, 128, None)
     seed_of = lambda k: 1 + rank + 7919 * k
 
     def one_run(k):
@@ -359,6 +370,10 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     # ---- roofline of the dominant kernel (fused RW mutate) ----
+    # DRAM bytes (read + write) of one mutate launch from an ncu capture of the
+    # same kernel, workload and launch shape (profiles/k_mutate_egarch22_T5000.md);
+    # None where no capture of the current kernel exists.
+    traffic = MUTATE_TRAFFIC.get((args.workload, shape[0], shape[1])) if not mala else None
     mhz, src = sm_max_mhz()
     peak, pipe = alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, mhz)
     avg_launch_s = (mut_ms / mut_n) / 1e3 if mut_n else float("nan")
@@ -367,7 +382,7 @@ def main():
     # For MALA the kernel also recomputes and reverses the recursion; its frac is
     # stated against the forward recursion's bound (likelihood evaluations/s).
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
-            "frac": achieved / peak, "traffic": None, "pipe": pipe, "peak_source": f"{src} SM clock {mhz:.0f} MHz x {SM_COUNT_GB300} SMs",
+            "frac": achieved / peak, "traffic": traffic, "pipe": pipe, "peak_source": f"{src} SM clock {mhz:.0f} MHz x {SM_COUNT_GB300} SMs",
             "ops_per_eval": {"fp32": fp32_ops, "mufu": mufu_ops},
             "kernel": (f"k_mutate_mala<GradEgarch<float,{w.K},{w.I}>>" if mala
                        else f"k_mutate<PolicyEgarchF32<{w.K},{w.I}>>"), "avg_launch_ms": avg_launch_s * 1e3,

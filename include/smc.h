@@ -66,7 +66,7 @@ typedef enum {
 enum { SMC_EGARCH = 0, SMC_LINREG = 1 };
 enum { SMC_FP64 = 0, SMC_FP32 = 1 };
 enum { SMC_DATA = 0, SMC_POWER = 1 };
-enum { SMC_RW = 0, SMC_MALA = 1 };
+enum { SMC_RW = 0, SMC_MALA = 1, SMC_INDEP = 2 };
 enum { SMC_RESIDUAL = 0, SMC_MULTINOMIAL = 1, SMC_STRATIFIED = 2, SMC_SYSTEMATIC = 3 };
 enum { SMC_STOP_DET = 0, SMC_STOP_RNE = 1 };
 
@@ -118,7 +118,10 @@ typedef struct {
     int precision;            /* SMC_FP32: recursion in FP32 with FP64 log-likelihood,
                                  log weights and estimators; SMC_FP64: all FP64 */
     int tempering;            /* SMC_POWER | SMC_DATA */
-    int mutation;             /* SMC_RW | SMC_MALA (Langevin proposal using the adjoint gradient) */
+    int mutation;             /* SMC_RW | SMC_MALA (Langevin proposal using the adjoint gradient)
+                                 | SMC_INDEP (Section 3.3's independent Gaussian sampler:
+                                 proposal N(mean, V) from the pooled mean and variance of
+                                 the population; no step size; no hybrid record/replay) */
     int resampler;            /* SMC_RESIDUAL (default) | SMC_MULTINOMIAL, or the paper's
                                  experimental SMC_STRATIFIED | SMC_SYSTEMATIC */
     double d1, d2;
@@ -132,6 +135,11 @@ typedef struct {
     int force_dates[SMC_MAX_FORCE];
     int search_passes;        /* power tempering: k-ary passes (32 candidates each) */
     uint64_t seed;
+    int burnin;               /* data tempering: b > 0 ends a cycle at t = b and makes
+                                 smc_log_score report log p(y_{b+1:T} | y_1:b) (Section 4.1;
+                                 0 = none, b < T) */
+    int pit;                  /* data tempering: 1 records the probability integral
+                                 transform of every observation (smc_pit) */
 } smc_config;
 
 void smc_config_default(smc_config* c);
@@ -219,12 +227,31 @@ smc_status smc_design_replay(smc_ctx* ctx, int ncycles, const double* x, const i
  * runs a thread can carry two particles (their recursions interleave, hiding
  * each other's dependency latency when particles per scheduler are few).
  * smc_autotune times `iters` Metropolis iterations of each candidate shape
- * (1 particle x 128 threads; 2 x 64; 2 x 128) on a snapshot of the particles,
+ * (random walk: 1 particle x 128, 64 or 32 threads per block; FP32 EGARCH
+ * also 2 x 64 and 2 x 128; MALA: 1 x 128 only) on a snapshot of the particles,
  * restores them, and keeps the fastest; outputs (host, nullable): the shape and
  * its time per iteration.  Results do not depend on the shape.
- * smc_set_launch_shape sets one directly. */
+ * Smaller blocks split P particles into more blocks, which evens the load over
+ * the SMs when P / threads is not a multiple of the SM count.
+ * smc_set_launch_shape sets one directly (SMC_EINVAL for any other shape). */
 smc_status smc_autotune(smc_ctx* ctx, int iters, int* ppt, int* threads, double* ms_per_iteration);
 smc_status smc_set_launch_shape(smc_ctx* ctx, int ppt, int threads);
+
+/* Log score log p(y_{b+1:T} | y_1:b) (Section 4.1, the predictive likelihood
+ * after the burn-in b of the config): the group-product estimator over the
+ * cycles that start at or after b, with its NSE by (ML_se).  Valid once the
+ * run is complete; SMC_EINVAL without a burn-in.  Synchronises. */
+smc_status smc_log_score(smc_ctx* ctx, double* log_score, double* nse);
+
+/* Probability integral transform of y_s, s = 1..T (Section 4.1), for a context
+ * created with pit = 1: the C-phase weighted share, weights w_jn(s-1), of
+ * auxiliary draws Y_s ~ p(Y_s | y_1:s-1, theta_jn) with Y_s <= y_s.  The draw
+ * of particle jn is its standardized shock from the Philox block at counter
+ * (particle, s, 0, 4 << 32): uniform 0 picks mixture component i (first i with
+ * u < p_1 + .. + p_i), uniforms 1 and 2 a Box-Muller normal z, shock
+ * mu_i + sigma_i z (LINREG: z).  out: host [T]; observations not yet reached
+ * are NaN.  Synchronises. */
+smc_status smc_pit(smc_ctx* ctx, double* out, int T);
 
 /* Number of kernel launches this library has issued in this process. */
 uint64_t smc_launch_count(void);
@@ -312,6 +339,19 @@ smc_status smc_mutate_rw(const smc_model* m, int precision, const void* obs, int
 smc_status smc_loglik_grad(const smc_model* m, int precision, const void* obs, int T,
                            const double* theta, int P, double* ll, double* grad, double* state,
                            void* stream);
+
+/* One independent Gaussian Metropolis iteration (Section 3.3's alternative
+ * sampler) on device particles in place: proposal mean + L z with z as in
+ * smc_mutate_rw, accepted with log u < [lp + phi l](theta*) - [lp + phi l](theta)
+ * + log q(theta) - log q(theta*), q = N(mean, L L'); log q(theta) is
+ * -|L^{-1}(theta - mean)|^2 / 2 by forward substitution in FP64, a zero pivot of
+ * L contributing nothing.  mean: device [d]; other arguments as smc_mutate_rw.
+ * The paper has no kernel for it; the acceptance rule is the standard
+ * Metropolis-Hastings ratio for an independence proposal. */
+smc_status smc_mutate_indep(const smc_model* m, int precision, const void* obs, int T,
+                            double* theta, double* ll, double* lp, double* state, int P,
+                            const double* mean, const double* L, double phi, uint64_t seed,
+                            uint64_t cycle, uint64_t iter, uint64_t* accepted, void* stream);
 
 /* One MALA iteration on device particles in place (an alternative Metropolis
  * update in the sense of Section 3.3): theta* = theta + (1/2) L L' g + L z,

@@ -24,7 +24,7 @@ static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 #define SMC_DECL_EGARCH(TAG, K)                                                 \
-    cudaError_t launch_mutate_##TAG##_k##K(const MutateArgs& a, cudaStream_t s); \
+    cudaError_t launch_mutate_##TAG##_k##K(const MutateArgs& a, int threads, cudaStream_t s); \
     cudaError_t launch_loglik_##TAG##_k##K(const LoglikArgs& a, cudaStream_t s);
 SMC_DECL_EGARCH(f32, 1)
 SMC_DECL_EGARCH(f32, 2)
@@ -34,7 +34,7 @@ SMC_DECL_EGARCH(f64, 1)
 SMC_DECL_EGARCH(f64, 2)
 SMC_DECL_EGARCH(f64, 3)
 SMC_DECL_EGARCH(f64, 4)
-cudaError_t launch_mutate_linreg(const MutateArgs& a, cudaStream_t s);
+cudaError_t launch_mutate_linreg(const MutateArgs& a, int threads, cudaStream_t s);
 cudaError_t launch_loglik_linreg(const LoglikArgs& a, cudaStream_t s);
 cudaError_t launch_cdata_f32_k1(const CdataArgs& a, cudaStream_t s);
 cudaError_t launch_cdata_f32_k2(const CdataArgs& a, cudaStream_t s);
@@ -52,6 +52,7 @@ cudaError_t launch_mutate_x2_f32_k4(const MutateArgs& a, int threads, cudaStream
 
 cudaError_t launch_mutate_x2(const MutateArgs& a, int threads, cudaStream_t s)
 {
+    if (a.qmean) return cudaErrorInvalidValue;   // random walk only
     count_launch();
     switch (a.m.K) {
     case 1: return launch_mutate_x2_f32_k1(a, threads, s);
@@ -84,23 +85,24 @@ cudaError_t launch_cdata(const CdataArgs& a, int precision, cudaStream_t s)
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_mutate(const MutateArgs& a, int precision, cudaStream_t s)
+cudaError_t launch_mutate(const MutateArgs& a, int precision, int threads, cudaStream_t s)
 {
     count_launch();
-    if (a.m.kind == SMC_LINREG) return launch_mutate_linreg(a, s);
+    if (threads != 32 && threads != 64 && threads != kMutThreads) return cudaErrorInvalidValue;
+    if (a.m.kind == SMC_LINREG) return launch_mutate_linreg(a, threads, s);
     if (precision == SMC_FP32) {
         switch (a.m.K) {
-        case 1: return launch_mutate_f32_k1(a, s);
-        case 2: return launch_mutate_f32_k2(a, s);
-        case 3: return launch_mutate_f32_k3(a, s);
-        case 4: return launch_mutate_f32_k4(a, s);
+        case 1: return launch_mutate_f32_k1(a, threads, s);
+        case 2: return launch_mutate_f32_k2(a, threads, s);
+        case 3: return launch_mutate_f32_k3(a, threads, s);
+        case 4: return launch_mutate_f32_k4(a, threads, s);
         }
     } else {
         switch (a.m.K) {
-        case 1: return launch_mutate_f64_k1(a, s);
-        case 2: return launch_mutate_f64_k2(a, s);
-        case 3: return launch_mutate_f64_k3(a, s);
-        case 4: return launch_mutate_f64_k4(a, s);
+        case 1: return launch_mutate_f64_k1(a, threads, s);
+        case 2: return launch_mutate_f64_k2(a, threads, s);
+        case 3: return launch_mutate_f64_k3(a, threads, s);
+        case 4: return launch_mutate_f64_k4(a, threads, s);
         }
     }
     return cudaErrorInvalidValue;
@@ -318,6 +320,8 @@ void smc_config_default(smc_config* c)
     c->n_force = 0;
     c->search_passes = 6;
     c->seed = 1;
+    c->burnin = 0;
+    c->pit = 0;
 }
 
 uint64_t smc_launch_count(void) { return g_launches.load(); }
@@ -349,7 +353,7 @@ static void release(smc_ctx* c)
                     c->grad[0], c->grad[1], c->ckpt, c->design_L,
                     c->state[0], c->state[1], c->thp, c->logw, c->g, c->a, c->lw, c->gstat,
                     c->idx, c->cov_part, c->search_part, c->cd_part, c->mom_part, c->mom_out, c->ml_out,
-                    c->L, c->gather_ptrs, c->ctl};
+                    c->L, c->qmean, c->lq, c->a_score, c->pit, c->gather_ptrs, c->ctl};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->ctl_host) cudaFreeHost(c->ctl_host);
@@ -422,8 +426,14 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
                            cudaMemcpyDeviceToDevice, ctx->stream));
         ctx->replay_iter += 1;
     } else {
-        CU(launch_cov(th, d, P, ctx->cov_part, ctx->cov_G, ctx->ctl, 0, c.acc_target, c.hmin_tenths,
-                      c.hmax_tenths, nullptr, nullptr, ctx->L, ctx->stream));
+        // Sigma = h^2 V; the independent sampler takes V itself (h pinned at
+        // 10 tenths for the factor, still updated from the acceptance rate)
+        // and the pooled mean.
+        const bool indep = c.mutation == SMC_INDEP;
+        CU(launch_cov(th, d, P, ctx->cov_part, ctx->cov_G, ctx->ctl, indep ? 10 : 0, c.acc_target,
+                      c.hmin_tenths, c.hmax_tenths, indep ? ctx->qmean : nullptr, nullptr, ctx->L,
+                      ctx->stream));
+        if (indep) CU(launch_indep_logq(th, d, P, ctx->L, ctx->qmean, ctx->lq, ctx->stream));
     }
     if (ctx->record) {
         if (ctx->design_iters >= ctx->design_cap)
@@ -481,6 +491,8 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
     a.P = P;
     a.ns = ctx->ns;
     a.L = ctx->L;
+    a.qmean = c.mutation == SMC_INDEP ? ctx->qmean : nullptr;
+    a.lq = ctx->lq;
     a.phi = phi;
     a.seed = c.seed;
     a.cycle = (uint64_t)ctx->cycle;
@@ -495,7 +507,7 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
         CU(cudaEventRecord(e0, ctx->stream));
     }
     if (ctx->ppt == 2) CU(launch_mutate_x2(a, ctx->mut_threads, ctx->stream));
-    else CU(launch_mutate(a, c.precision, ctx->stream));
+    else CU(launch_mutate(a, c.precision, ctx->mut_threads, ctx->stream));
     if (ctx->profile) {
         CU(cudaEventRecord(e1, ctx->stream));
         ctx->ev_pending.push_back({e0, e1});
@@ -554,6 +566,7 @@ static smc_status s_phase(smc_ctx* ctx, int mode)
     s.seed = c.seed;
     s.cycle = (uint64_t)ctx->cycle;
     s.a = ctx->a;
+    s.a_score = c.burnin > 0 && c.tempering == SMC_DATA && ctx->t_prev >= c.burnin ? ctx->a_score : nullptr;
     s.lw = ctx->lw;
     s.gstat = ctx->gstat;
     s.idx = ctx->idx;
@@ -675,7 +688,7 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
     if (T < 1 || !y) return set_err(ctx, SMC_EINVAL, "need T >= 1 observations");
     if (m->model == SMC_LINREG && !X) return set_err(ctx, SMC_EINVAL, "LINREG needs X");
     if (!theta0) return set_err(ctx, SMC_EINVAL, "theta0 is NULL");
-    if (c->mutation != SMC_RW && c->mutation != SMC_MALA)
+    if (c->mutation != SMC_RW && c->mutation != SMC_MALA && c->mutation != SMC_INDEP)
         return set_err(ctx, SMC_EINVAL, "unknown mutation %d", c->mutation);
     if (c->tempering != SMC_POWER && c->tempering != SMC_DATA)
         return set_err(ctx, SMC_EINVAL, "unknown tempering %d", c->tempering);
@@ -688,6 +701,10 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
         c->h0_tenths > c->hmax_tenths || c->search_passes < 1 || c->n_force < 0 ||
         c->n_force > SMC_MAX_FORCE)
         return set_err(ctx, SMC_EINVAL, "invalid simulator settings");
+    if ((c->burnin != 0 || c->pit != 0) && c->tempering != SMC_DATA)
+        return set_err(ctx, SMC_EINVAL, "the log score and the PIT need data tempering");
+    if (c->burnin < 0 || c->burnin >= T || (c->pit != 0 && c->pit != 1))
+        return set_err(ctx, SMC_EINVAL, "need 0 <= burnin < T and pit in {0, 1}");
     for (int t = 0; t < T; ++t)
         if (!std::isfinite(y[t])) return set_err(ctx, SMC_ENONFINITE, "y[%d] is not finite", t);
     if (X)
@@ -754,6 +771,8 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
     CU(dalloc(&ctx->logw, Ps));
     CU(dalloc(&ctx->g, Ps * 3));
     CU(dalloc(&ctx->a, J));
+    CU(dalloc(&ctx->a_score, J));
+    if (c->pit) CU(dalloc(&ctx->pit, (size_t)T));
     CU(dalloc(&ctx->lw, J));
     CU(dalloc(&ctx->gstat, (size_t)J * 3));
     CU(dalloc(&ctx->idx, Ps));
@@ -766,6 +785,8 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
     CU(dalloc(&ctx->mom_out, (size_t)nf_max * 4));
     CU(dalloc(&ctx->ml_out, 3));
     CU(dalloc(&ctx->L, (size_t)d * d));
+    CU(dalloc(&ctx->qmean, (size_t)d));
+    if (c->mutation == SMC_INDEP) CU(dalloc(&ctx->lq, Ps));
     CU(dalloc(&ctx->ctl, 1));
     CU(cudaMallocHost((void**)&ctx->ctl_host, sizeof(Ctl)));
 
@@ -828,6 +849,8 @@ static smc_status start_run(smc_ctx* ctx, const double* theta0, int theta0_on_de
     init.h_tenths = c->h0_tenths;
     CU(cudaMemcpyAsync(ctx->ctl, &init, sizeof init, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemsetAsync(ctx->a, 0, (size_t)J * sizeof(double), ctx->stream));
+    CU(cudaMemsetAsync(ctx->a_score, 0, (size_t)J * sizeof(double), ctx->stream));
+    if (ctx->pit) CU(cudaMemsetAsync(ctx->pit, 0xff, (size_t)ctx->T * sizeof(double), ctx->stream));  // NaN
     if (c->tempering == SMC_POWER) {
         LoglikArgs la;
         la.m = ctx->mdev;
@@ -916,6 +939,10 @@ smc_status smc_autotune(smc_ctx* ctx, int iters, int* ppt, int* threads, double*
     const Ctl saved = *ctx->ctl_host;
     struct Shape { int ppt, threads; };
     std::vector<Shape> cand = {{1, kMutThreads}};
+    if (ctx->cfg.mutation != SMC_MALA) {
+        cand.push_back({1, 64});
+        cand.push_back({1, 32});
+    }
     if (fp32_egarch) {
         cand.push_back({2, 64});
         cand.push_back({2, 128});
@@ -971,11 +998,12 @@ smc_status smc_autotune(smc_ctx* ctx, int iters, int* ppt, int* threads, double*
 
 smc_status smc_set_launch_shape(smc_ctx* ctx, int ppt, int threads)
 {
-    if (!ctx || (ppt != 1 && ppt != 2) || (threads != 64 && threads != 128)) return SMC_EINVAL;
+    if (!ctx || (ppt != 1 && ppt != 2) || (threads != 32 && threads != 64 && threads != kMutThreads))
+        return SMC_EINVAL;
     if (ppt == 2 && !(ctx->model.model == SMC_EGARCH && ctx->cfg.precision == SMC_FP32 &&
                       ctx->cfg.mutation == SMC_RW))
         return set_err(ctx, SMC_EINVAL, "two particles per thread needs the FP32 EGARCH random walk");
-    if (ppt == 1 && threads != kMutThreads) return set_err(ctx, SMC_EINVAL, "one particle per thread uses 128 threads");
+    if (ppt == 2 && threads == 32) return set_err(ctx, SMC_EINVAL, "two particles per thread use 64 or 128 threads");
     ctx->ppt = ppt;
     ctx->mut_threads = threads;
     return SMC_OK;
@@ -985,6 +1013,8 @@ smc_status smc_design_record(smc_ctx* ctx, int max_iterations)
 {
     if (!ctx || max_iterations < 1) return SMC_EINVAL;
     if (ctx->replay) return set_err(ctx, SMC_EINVAL, "a replaying context cannot record");
+    if (ctx->cfg.mutation == SMC_INDEP)
+        return set_err(ctx, SMC_EINVAL, "a design holds no proposal means: the independent sampler cannot record");
     if (ctx->cycle > 0) return set_err(ctx, SMC_EINVAL, "start recording before the first cycle");
     if (ctx->design_L) cudaFree(ctx->design_L);
     ctx->design_L = nullptr;
@@ -1103,6 +1133,7 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
         } else {
             fd.n = c.n_force;
             for (int i = 0; i < c.n_force; ++i) fd.t[i] = c.force_dates[i];
+            if (c.burnin > 0) fd.t[fd.n++] = c.burnin;   // the log score starts a cycle at b
         }
         const int G = (P + kMutThreads - 1) / kMutThreads;
         int s0 = ctx->t_prev;
@@ -1123,10 +1154,14 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
             ca.part = ctx->cd_part;
             ca.stop = &ctx->ctl->cd_stop;
             ca.commit = 0;
+            ca.pit = 0;
+            ca.seed = c.seed;
             CU(launch_cdata(ca, c.precision, ctx->stream));
             CU(launch_cdata_select(ctx->cd_part, G, ca.B, s0, ctx->T, P, d1, fd, ctx->ctl, ctx->stream));
             ca.commit = 1;
+            ca.pit = ctx->pit != nullptr;
             CU(launch_cdata(ca, c.precision, ctx->stream));
+            if (ctx->pit) CU(launch_pit_final(ctx->cd_part, G, ca.B, s0, ctx->ctl, ctx->pit, ctx->stream));
             st = sync_ctl(ctx);
             if (st != SMC_OK) return st;
             s0 += ctx->ctl_host->cd_stop;
@@ -1250,6 +1285,28 @@ smc_status smc_get_particles(smc_ctx* ctx, double* theta, double* loglik, double
         count_launch();
         CU(cudaMemcpyAsync(state, ctx->thp, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     }
+    CU(cudaStreamSynchronize(ctx->stream));
+    return SMC_OK;
+}
+
+smc_status smc_log_score(smc_ctx* ctx, double* log_score, double* nse)
+{
+    if (!ctx || !log_score) return SMC_EINVAL;
+    if (ctx->cfg.burnin <= 0) return set_err(ctx, SMC_EINVAL, "no burn-in was set");
+    CU(launch_ml(ctx->a_score, ctx->cfg.J, ctx->ctl, ctx->ml_out, ctx->stream));
+    double out[3];
+    CU(cudaMemcpyAsync(out, ctx->ml_out, sizeof out, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *log_score = out[0];
+    if (nse) *nse = out[1];
+    return SMC_OK;
+}
+
+smc_status smc_pit(smc_ctx* ctx, double* out, int T)
+{
+    if (!ctx || !out || T != ctx->T) return SMC_EINVAL;
+    if (!ctx->pit) return set_err(ctx, SMC_EINVAL, "the context was created without pit = 1");
+    CU(cudaMemcpyAsync(out, ctx->pit, (size_t)T * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     return SMC_OK;
 }

@@ -165,6 +165,8 @@ static void fill_descriptors(smc_batch* b, const std::vector<int>& R)
         a.P = c->P;
         a.ns = c->ns;
         a.L = c->L;
+        a.qmean = nullptr;
+        a.lq = nullptr;
         a.phi = c->phi;
         a.seed = c->cfg.seed;
         a.cycle = (uint64_t)c->cycle;

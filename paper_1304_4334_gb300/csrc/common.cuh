@@ -19,7 +19,7 @@ constexpr int kMaxI = 4;        // mixture components
 constexpr int kMaxState = kMaxK + 1;
 constexpr int kMaxN = 8192;      // particles per group (S-phase shared memory)
 
-enum : uint32_t { kTagNormal = 1u, kTagUniform = 2u, kTagResample = 3u };
+enum : uint32_t { kTagNormal = 1u, kTagUniform = 2u, kTagResample = 3u, kTagPit = 4u };
 
 // ------------------------------------------------------------------ Philox4x64
 struct U64x4 {

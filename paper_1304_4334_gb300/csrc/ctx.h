@@ -34,6 +34,8 @@ struct smc_ctx {
     double* g = nullptr;             // [3][P] test functions
     // per-group estimators
     double* a = nullptr;             // [J]
+    double* a_score = nullptr;       // [J] log score accumulators (cycles after the burn-in)
+    double* pit = nullptr;           // [T] probability integral transforms (nullable)
     double* lw = nullptr;            // [J]
     double* gstat = nullptr;         // [J][3]
     int32_t* idx = nullptr;          // [P]
@@ -45,6 +47,8 @@ struct smc_ctx {
     double* mom_out = nullptr;       // [nf][4]
     double* ml_out = nullptr;        // [3]
     double* L = nullptr;             // [d][d]
+    double* qmean = nullptr;         // [d] independent-sampler proposal mean
+    double* lq = nullptr;            // [P] independent sampler: log q of the current particles
     double** gather_ptrs = nullptr;  // [2][nrows] device row-pointer tables
     int gather_rows = 0;
     Ctl* ctl = nullptr;

@@ -6,17 +6,28 @@
 
 namespace smc {
 
-inline int mutate_grid(int P) { return (P + kMutThreads - 1) / kMutThreads; }
+inline int mutate_grid(int P, int threads = kMutThreads) { return (P + threads - 1) / threads; }
 
+// One particle per thread; threads = 32, 64 or 128 per block (the caller checks).
 template <template <int, int> class Pol, int K>
-cudaError_t launch_mutate_k(const MutateArgs& a, cudaStream_t s)
+cudaError_t launch_mutate_k(const MutateArgs& a, int threads, cudaStream_t s)
 {
-    const int g = mutate_grid(a.P);
+    const int g = mutate_grid(a.P, threads);
+    if (a.qmean) {   // independent sampler
+        switch (a.m.I) {
+        case 1: k_mutate<Pol<K, 1>, true><<<g, threads, 0, s>>>(a); break;
+        case 2: k_mutate<Pol<K, 2>, true><<<g, threads, 0, s>>>(a); break;
+        case 3: k_mutate<Pol<K, 3>, true><<<g, threads, 0, s>>>(a); break;
+        case 4: k_mutate<Pol<K, 4>, true><<<g, threads, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (a.m.I) {
-    case 1: k_mutate<Pol<K, 1>><<<g, kMutThreads, 0, s>>>(a); break;
-    case 2: k_mutate<Pol<K, 2>><<<g, kMutThreads, 0, s>>>(a); break;
-    case 3: k_mutate<Pol<K, 3>><<<g, kMutThreads, 0, s>>>(a); break;
-    case 4: k_mutate<Pol<K, 4>><<<g, kMutThreads, 0, s>>>(a); break;
+    case 1: k_mutate<Pol<K, 1>><<<g, threads, 0, s>>>(a); break;
+    case 2: k_mutate<Pol<K, 2>><<<g, threads, 0, s>>>(a); break;
+    case 3: k_mutate<Pol<K, 3>><<<g, threads, 0, s>>>(a); break;
+    case 4: k_mutate<Pol<K, 4>><<<g, threads, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -69,9 +80,9 @@ cudaError_t launch_cdata_k(const CdataArgs& a, cudaStream_t s)
 
 #define SMC_INSTANTIATE_EGARCH(TAG, POL, K)                                                     \
     namespace smc {                                                                             \
-    cudaError_t launch_mutate_##TAG##_k##K(const MutateArgs& a, cudaStream_t s)                 \
+    cudaError_t launch_mutate_##TAG##_k##K(const MutateArgs& a, int threads, cudaStream_t s)    \
     {                                                                                           \
-        return launch_mutate_k<POL, K>(a, s);                                                   \
+        return launch_mutate_k<POL, K>(a, threads, s);                                          \
     }                                                                                           \
     cudaError_t launch_loglik_##TAG##_k##K(const LoglikArgs& a, cudaStream_t s)                 \
     {                                                                                           \

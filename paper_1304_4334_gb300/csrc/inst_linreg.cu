@@ -3,9 +3,10 @@
 
 namespace smc {
 
-cudaError_t launch_mutate_linreg(const MutateArgs& a, cudaStream_t s)
+cudaError_t launch_mutate_linreg(const MutateArgs& a, int threads, cudaStream_t s)
 {
-    k_mutate<PolicyLinreg><<<mutate_grid(a.P), kMutThreads, 0, s>>>(a);
+    if (a.qmean) k_mutate<PolicyLinreg, true><<<mutate_grid(a.P, threads), threads, 0, s>>>(a);
+    else k_mutate<PolicyLinreg><<<mutate_grid(a.P, threads), threads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,10 @@ namespace smc {
 // Arguments of one M-phase Metropolis iteration (Section 3.3, "Metropolis
 // steps"): theta* = theta + L z with L L' = h^2 V, accepted with probability
 // min(1, exp{[lp(theta*) + phi l(theta*)] - [lp(theta) + phi l(theta)]}).
+// With qmean set, the independent Gaussian sampler of the same passage:
+// theta* = qmean + L z (L L' = V), and the ratio also carries
+// log q(theta) - log q(theta*) for q = N(qmean, L L'); log q(theta) comes
+// precomputed per particle (launch_indep_logq), log q(theta*) = -|z|^2 / 2.
 struct MutateArgs {
     ModelDev m;
     const void* obs;        // observation records (float for FP32 EGARCH, double otherwise)
@@ -27,6 +31,8 @@ struct MutateArgs {
     int P;
     int ns;
     const double* L;        // [d][d] lower Cholesky factor of h^2 V, row-major
+    const double* qmean;    // [d] independent-sampler mean (nullptr: random walk)
+    const double* lq;       // [P] independent sampler: log q(theta) of the current particles
     double phi;
     uint64_t seed, cycle, iter;
     unsigned long long* acc_count;   // += accepted proposals
@@ -48,6 +54,60 @@ struct LoglikArgs {
 
 constexpr int kMutThreads = 128;
 
+// Probability integral transform draw (Section 4.1): the standardized shock
+// of Y_s ~ p(Y_s | y_1:s-1, theta), location + scale * e, so that
+// I[Y_s <= y_s] = I[e <= e_s].  The Philox block at counter
+// (particle, s, 0, kTagPit << 32) gives a uniform that picks mixture component
+// i when it falls below p_1 + .. + p_i (first such i), and two uniforms for a
+// Box-Muller normal z; e = mu_i + sigma_i z.
+template <typename Real, int I>
+struct PitMixture {
+    double cum[I];
+    Real mu[I], sig[I];
+
+    __device__ __forceinline__ double shock(uint64_t seed, uint64_t p, int s) const
+    {
+        const U64x4 r = philox4x64_10(p, (uint64_t)s, 0, (uint64_t)kTagPit << 32, seed, 0);
+        const double uc = uniform53(r.v0);
+        Real z;
+        if constexpr (sizeof(Real) == 8) {
+            z = sqrt(-2.0 * log(uniform53(r.v1))) * cospi(2.0 * uniform53(r.v2));
+        } else {
+            const float ua = ((float)(uint32_t)(r.v1 >> 40) + 0.5f) * 0x1.0p-24f;
+            const float ub = ((float)(uint32_t)(r.v2 >> 40) + 0.5f) * 0x1.0p-24f;
+            z = sqrtf(-2.0f * logf(ua)) * cospif(2.0f * ub);
+        }
+        Real m = mu[I - 1], sg = sig[I - 1];
+        bool found = false;
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+            if (!found && uc < cum[i]) {
+                m = mu[i];
+                sg = sig[i];
+                found = true;
+            }
+        }
+        return (double)(m + sg * z);
+    }
+};
+
+template <typename Real, int K, int I>
+__device__ __forceinline__ void pit_setup_egarch(const ModelDev& m, const double* th, PitMixture<Real, I>& pm)
+{
+    Real full[kMaxD];
+    full_theta<Real>(m, th, full);
+    EgarchParams<Real, K, I> q;
+    egarch_transform<Real, K, I>(full, m.gamma, q);
+    double c = 0.0;
+#pragma unroll
+    for (int i = 0; i < I; ++i) {
+        c += (double)q.p[i];
+        pm.cum[i] = c;
+        pm.mu[i] = q.mu[i];
+        pm.sig[i] = q.sig[i];
+    }
+}
+
 template <int K, int I>
 struct PolicyEgarchF32 {
     using Real = float;
@@ -67,6 +127,10 @@ struct PolicyEgarchF32 {
         const Obs y = obs[s - 1];
         return s == 1 ? mdl.template logdens<true>(y) : mdl.template logdens<false>(y);
     }
+    using Pit = PitMixture<float, I>;
+    __device__ static void pit_setup(const ModelDev& m, const double* th, Pit& pm) { pit_setup_egarch<float, K, I>(m, th, pm); }
+    // observed standardized shock after logdens of observation s
+    __device__ static double obs_shock(const Model& mdl, const Obs*, int, int) { return (double)mdl.es * (1.0 / kSfac); }
 };
 
 template <int K, int I>
@@ -88,6 +152,9 @@ struct PolicyEgarchF64 {
         const Obs y = obs[s - 1];
         return s == 1 ? mdl.template logdens<true>(y) : mdl.template logdens<false>(y);
     }
+    using Pit = PitMixture<double, I>;
+    __device__ static void pit_setup(const ModelDev& m, const double* th, Pit& pm) { pit_setup_egarch<double, K, I>(m, th, pm); }
+    __device__ static double obs_shock(const Model& mdl, const Obs*, int, int) { return mdl.eps; }
 };
 
 struct PolicyLinreg {
@@ -107,6 +174,17 @@ struct PolicyLinreg {
     {
         return mdl.logdens(obs + (size_t)(s - 1) * W);
     }
+    using Pit = PitMixture<double, 1>;
+    __device__ static void pit_setup(const ModelDev&, const double*, Pit& pm)
+    {
+        pm.cum[0] = 1.0;
+        pm.mu[0] = 0.0;
+        pm.sig[0] = 1.0;
+    }
+    __device__ static double obs_shock(const Model& mdl, const Obs* obs, int s, int W)
+    {
+        return mdl.shock(obs + (size_t)(s - 1) * W);
+    }
 };
 
 __device__ __forceinline__ double tempered_target(double lp, double ll, double phi)
@@ -114,6 +192,7 @@ __device__ __forceinline__ double tempered_target(double lp, double ll, double p
     if (lp == -INFINITY) return -INFINITY;
     return phi > 0.0 ? lp + phi * ll : lp;
 }
+
 
 // Shared memory of one mutation tile.
 template <class Pol>
@@ -126,8 +205,10 @@ struct MutateSmem {
 
 // One block's tile of particles p0 + threadIdx.x: proposal, likelihood
 // recursion over the staged observations, Metropolis-Hastings decision.
-// Every thread of the block must call it (block barriers inside).
-template <class Pol>
+// Every thread of the block must call it (block barriers inside).  kIndep
+// selects the independent sampler (a.qmean, a.lq set) at compile time, so the
+// random-walk instantiation carries none of its code.
+template <class Pol, bool kIndep = false>
 __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, int p0, MutateSmem<Pol>& sm)
 {
     using Real = typename Pol::Real;
@@ -146,15 +227,22 @@ __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, 
     const int pp = active ? p : a.P - 1;
     const size_t P = (size_t)a.P;
 
-    // Proposal theta* = theta + L z (Section 3.3), written to the scratch rows.
+    // Proposal theta* = theta + L z, or qmean + L z for the independent
+    // sampler (Section 3.3), written to the scratch rows.
     double thn[kMaxD];
+    double zz = 0.0;
     {
         Real z[kMaxD];
         proposal_normals<Real>(a.seed, (uint64_t)pp, iter, a.cycle, d, z);
         for (int i = 0; i < d; ++i) {
             Real s = 0;
             for (int k = 0; k <= i; ++k) s += sm.Ls[i * d + k] * z[k];
-            thn[i] = a.theta[i * P + pp] + (double)s;
+            if constexpr (kIndep) {
+                thn[i] = a.qmean[i] + (double)s;
+                zz += (double)z[i] * (double)z[i];
+            } else {
+                thn[i] = a.theta[i * P + pp] + (double)s;
+            }
             if (active) a.thp[i * P + p] = thn[i];
         }
     }
@@ -172,8 +260,9 @@ __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, 
 
     bool acc = false;
     if (active) {
-        const double log_alpha = tempered_target(lp_new, ll_new, a.phi) -
-                                 tempered_target(a.lp[p], a.ll[p], a.phi);
+        double log_alpha = tempered_target(lp_new, ll_new, a.phi) -
+                           tempered_target(a.lp[p], a.ll[p], a.phi);
+        if constexpr (kIndep) log_alpha += a.lq[p] + 0.5 * zz;
         const double log_u = log_uniform_mh(a.seed, (uint64_t)p, iter, a.cycle);
         acc = log_u < log_alpha;
         if (acc) {
@@ -195,11 +284,11 @@ __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, 
     pipe.finish();
 }
 
-template <class Pol>
+template <class Pol, bool kIndep = false>
 __global__ void __launch_bounds__(kMutThreads) k_mutate(MutateArgs a)
 {
     __shared__ MutateSmem<Pol> sm;
-    mutate_tile<Pol>(a, a.iter, blockIdx.x * blockDim.x, sm);
+    mutate_tile<Pol, kIndep>(a, a.iter, blockIdx.x * blockDim.x, sm);
 }
 
 // Two particles per thread (FP32 EGARCH): particles p0 + threadIdx.x and
@@ -348,6 +437,11 @@ struct CdataArgs {
     double* part;          // [gridDim][B][3] statistics pass output
     const int* stop;       // commit pass: observations to absorb (device)
     int commit;
+    // Commit pass, probability integral transform (Section 4.1; nullable):
+    // part[block][q] gets (max log w(s-1), sum w(s-1), sum w(s-1) I[Y_s <= y_s])
+    // for s = s0 + q + 1, the auxiliary draws from Philox stream `seed`.
+    int pit;
+    uint64_t seed;
 };
 
 template <class Pol>
@@ -377,7 +471,45 @@ __global__ void __launch_bounds__(kMutThreads) k_cdata(CdataArgs a)
     if (a.commit) {
         const int n = *a.stop;
         double add = 0.0;
-        for (int q = 0; q < n; ++q) add += Pol::logdens(mdl, obs, a.s0 + q + 1, a.W);
+        if (a.pit) {
+            typename Pol::Pit pm;
+            Pol::pit_setup(a.m, th, pm);
+            for (int q = 0; q < n; ++q) {
+                const int sobs = a.s0 + q + 1;
+                const double lprev = lw + add;    // log w(s-1)
+                const double x = active && !isnan(lprev) ? lprev : -INFINITY;
+                const double mw = warp_max(x);
+                float w = 0.0f;
+                if (x != -INFINITY && mw != -INFINITY) w = ex2_approx((float)((x - mw) * kLog2e));
+                add += Pol::logdens(mdl, obs, sobs, a.W);
+                const bool below = pm.shock(a.seed, (uint64_t)pp, sobs) <= Pol::obs_shock(mdl, obs, sobs, a.W);
+                const float s1 = warp_sum(w);
+                const float s2 = warp_sum(below ? w : 0.0f);
+                if (lane == 0) {
+                    trip[warp][q][0] = mw;
+                    trip[warp][q][1] = s1;
+                    trip[warp][q][2] = s2;
+                }
+            }
+            __syncthreads();
+            for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                double M = -INFINITY;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = fmax(M, trip[w][q][0]);
+                double S1 = 0.0, S2 = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                    if (trip[w][q][0] == -INFINITY) continue;
+                    const double e = exp(trip[w][q][0] - M);
+                    S1 += trip[w][q][1] * e;
+                    S2 += trip[w][q][2] * e;
+                }
+                double* o = a.part + ((size_t)blockIdx.x * a.B + q) * 3;
+                o[0] = M;
+                o[1] = S1;
+                o[2] = S2;
+            }
+        } else {
+            for (int q = 0; q < n; ++q) add += Pol::logdens(mdl, obs, a.s0 + q + 1, a.W);
+        }
         if (isnan(add)) add = -INFINITY;
         if (active) {
             a.ll[p] += add;
@@ -423,7 +555,11 @@ __global__ void __launch_bounds__(kMutThreads) k_cdata(CdataArgs a)
 }
 
 // Host-side launchers (defined in the instantiation units).
-cudaError_t launch_mutate(const MutateArgs& a, int precision, cudaStream_t s);
+// lq[p] = -|L^{-1}(theta_p - qmean)|^2 / 2 by forward substitution in FP64, a
+// zero pivot contributing nothing (defined in phase.cu).
+cudaError_t launch_indep_logq(const double* theta, int d, int P, const double* L, const double* qmean,
+                              double* lq, cudaStream_t s);
+cudaError_t launch_mutate(const MutateArgs& a, int precision, int threads, cudaStream_t s);
 cudaError_t launch_loglik(const LoglikArgs& a, int precision, cudaStream_t s);
 cudaError_t launch_cdata(const CdataArgs& a, int precision, cudaStream_t s);
 

@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(128) k_cov_combine(double* part, int G, int na
 }
 
 // Combines the partial sums, updates h from the previous iteration's
-// acceptance (when a control block is given) and factors Sigma = h^2 V by a
+// acceptance (when a control block is given; a positive fixed_h still scales
+// Sigma in place of the adapted h) and factors Sigma = h^2 V by a
 // right-looking Cholesky in shared memory; a non-positive pivot zeroes its
 // column, as in the oracle.
 __device__ void cov_final_body(const double* __restrict__ part, int G, int d, int P,
@@ -156,7 +157,7 @@ __device__ void cov_final_body(const double* __restrict__ part, int G, int d, in
         int h = fixed_h;
         if (ctl) {
             apply_h_update(ctl, P, target, hmin, hmax);
-            h = ctl->h_tenths;
+            if (fixed_h <= 0) h = ctl->h_tenths;   // fixed_h > 0 overrides the adapted step size
         }
         hh = (h / 10.0) * (h / 10.0);
     }
@@ -260,6 +261,39 @@ cudaError_t launch_cov(const double* theta, int d, int P, double* part, int G, C
     count_launch();
     k_cov_final<<<1, kCovThreads, 0, s>>>(part, G, d, P, theta, ctl, fixed_h_tenths, acc_target,
                                           hmin, hmax, mean, cov, L);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Independent sampler (Section 3.3): log q of every current particle under
+// q = N(qmean, L L'), up to the constant, for the Metropolis-Hastings ratio.
+__global__ void __launch_bounds__(256) k_indep_logq(const double* __restrict__ theta, int d, int P,
+                                                   const double* __restrict__ L,
+                                                   const double* __restrict__ qmean, double* lq)
+{
+    __shared__ double Ls[kMaxD * kMaxD], ms[kMaxD];
+    for (int i = threadIdx.x; i < d * d; i += blockDim.x) Ls[i] = L[i];
+    for (int i = threadIdx.x; i < d; i += blockDim.x) ms[i] = qmean[i];
+    __syncthreads();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const size_t Ps = (size_t)P;
+    double u[kMaxD];
+    double q = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double r = theta[i * Ps + p] - ms[i];
+        for (int k = 0; k < i; ++k) r -= Ls[i * d + k] * u[k];
+        const double piv = Ls[i * d + i];
+        u[i] = piv > 0.0 ? r / piv : 0.0;
+        q += u[i] * u[i];
+    }
+    lq[p] = -0.5 * q;
+}
+
+cudaError_t launch_indep_logq(const double* theta, int d, int P, const double* L, const double* qmean,
+                              double* lq, cudaStream_t s)
+{
+    k_indep_logq<<<(P + 255) / 256, 256, 0, s>>>(theta, d, P, L, qmean, lq);
     count_launch();
     return cudaGetLastError();
 }
@@ -523,6 +557,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
             const double lwj = lmax + log(s1 / (double)N);
             a.lw[j] = lwj;
             a.a[j] += lwj;
+            if (a.a_score) a.a_score[j] += lwj;   // log score: cycles after the burn-in
             a.gstat[3 * j + 0] = lmax;
             a.gstat[3 * j + 1] = s1;
             a.gstat[3 * j + 2] = s2;
@@ -695,6 +730,34 @@ __global__ void k_cdata_select(const double* part, int G, int B, int s0, int T, 
         ctl->cd_forced = m ? forced_at : 0;
         ctl->rss = rss_at;
     }
+}
+
+// PIT of the committed observations s0 + 1 .. s0 + stop (Section 4.1): lane q
+// combines the blocks' (max log w(s-1), sum w, sum w I[Y_s <= y_s]) of
+// observation s0 + q + 1 into the weighted share.
+__global__ void k_pit_final(const double* part, int G, int B, int s0, const Ctl* ctl, double* pit)
+{
+    const int q = threadIdx.x;
+    if (q >= ctl->cd_stop || q >= B) return;
+    double M = -INFINITY;
+    for (int g = 0; g < G; ++g) M = fmax(M, part[((size_t)g * B + q) * 3]);
+    double S1 = 0.0, S2 = 0.0;
+    for (int g = 0; g < G; ++g) {
+        const double* o = part + ((size_t)g * B + q) * 3;
+        if (o[0] == -INFINITY) continue;
+        const double e = exp(o[0] - M);
+        S1 += o[1] * e;
+        S2 += o[2] * e;
+    }
+    pit[s0 + q] = S2 / S1;
+}
+
+cudaError_t launch_pit_final(const double* part, int G, int B, int s0, const Ctl* ctl, double* pit,
+                             cudaStream_t s)
+{
+    k_pit_final<<<1, 32, 0, s>>>(part, G, B, s0, ctl, pit);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cdata_select(const double* part, int G, int B, int s0, int T, int P, double d1,

@@ -76,6 +76,7 @@ struct SelectArgs {
     int scheme;       // 0 residual, 1 multinomial, 2 stratified, 3 systematic
     uint64_t seed, cycle;
     double* a;        // [J] += log wbar_j (modes 0, 1)
+    double* a_score;  // [J] += log wbar_j too (nullable: cycles before the burn-in)
     double* lw;       // [J] log wbar_j of this cycle (modes 0, 1)
     double* gstat;    // [J][3] (max log w, sum w, sum w^2) of this cycle (modes 0, 1)
     int32_t* idx;     // [J*N]
@@ -98,10 +99,12 @@ cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
 // the stopping observation (first s with RSS(s) < D1, a date of interest, or T).
 struct ForceDates {
     int n;
-    int t[64];
+    int t[65];   // dates of interest and the burn-in date
 };
 cudaError_t launch_cdata_select(const double* part, int G, int B, int s0, int T, int P, double d1,
                                 const ForceDates& fd, Ctl* ctl, cudaStream_t s);
+cudaError_t launch_pit_final(const double* part, int G, int B, int s0, const Ctl* ctl, double* pit,
+                             cudaStream_t s);
 
 // After the S phase: pooled RSS at the chosen power, log wtilde, phi update.
 cudaError_t launch_cycle_close(const double* gstat, const double* lw, int J, int N, int power,

@@ -663,7 +663,7 @@ __device__ __forceinline__ bool run_egarch_f64(EgarchF64<K, I>& mdl, ObsPipe<dou
 struct LinregF64 {
     double beta[8];
     int p;
-    double inv2s2, c0;
+    double inv2s2, c0, isig;
     double acc;
 
     __device__ __forceinline__ void setup(const double* th, int p_, double sigma)
@@ -671,6 +671,7 @@ struct LinregF64 {
         p = p_;
         for (int i = 0; i < p; ++i) beta[i] = th[i];
         inv2s2 = 0.5 / (sigma * sigma);
+        isig = 1.0 / sigma;
         c0 = -0.5 * kLog2Pi - log(sigma);
         acc = 0.0;
     }
@@ -691,6 +692,14 @@ struct LinregF64 {
         for (int i = 0; i < p; ++i) m += rec[i] * beta[i];
         const double r = rec[p] - m;
         return -r * r * inv2s2 + c0;
+    }
+
+    // standardized residual (y_t - x_t'beta) / sigma of one record
+    __device__ __forceinline__ double shock(const double* rec) const
+    {
+        double m = 0.0;
+        for (int i = 0; i < p; ++i) m += rec[i] * beta[i];
+        return (rec[p] - m) * isig;
     }
 };
 

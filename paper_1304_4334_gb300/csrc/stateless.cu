@@ -89,10 +89,10 @@ smc_status smc_loglik(const smc_model* m, int precision, const void* obs, int T,
     return from_cuda(launch_loglik(a, precision, (cudaStream_t)stream));
 }
 
-smc_status smc_mutate_rw(const smc_model* m, int precision, const void* obs, int T, double* theta,
-                         double* ll, double* lp, double* state, int P, const double* L, double phi,
-                         uint64_t seed, uint64_t cycle, uint64_t iter, uint64_t* accepted,
-                         void* stream)
+static smc_status mutate_impl(const smc_model* m, int precision, const void* obs, int T, double* theta,
+                              double* ll, double* lp, double* state, int P, const double* qmean,
+                              const double* L, double phi, uint64_t seed, uint64_t cycle, uint64_t iter,
+                              uint64_t* accepted, void* stream)
 {
     if (!model_ok(m, precision) || !obs || !theta || !ll || !lp || !L || T < 1 || P < 1 ||
         !aligned16(obs) || !(phi >= 0.0))
@@ -104,6 +104,11 @@ smc_status smc_mutate_rw(const smc_model* m, int precision, const void* obs, int
     CK(cudaMallocAsync((void**)&thp, (size_t)P * d * sizeof(double), s));
     CK(cudaMallocAsync((void**)&cnt, sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+    double* lq = nullptr;
+    if (qmean) {
+        CK(cudaMallocAsync((void**)&lq, (size_t)P * sizeof(double), s));
+        CK(launch_indep_logq(theta, d, P, L, qmean, lq, s));
+    }
     MutateArgs a;
     a.m = ModelDev{};
     model_dev(*m, a.m);
@@ -118,6 +123,8 @@ smc_status smc_mutate_rw(const smc_model* m, int precision, const void* obs, int
     a.P = P;
     a.ns = m->model == SMC_EGARCH ? m->K + 1 : 0;
     a.L = L;
+    a.qmean = qmean;
+    a.lq = lq;
     a.phi = phi;
     a.seed = seed;
     a.cycle = cycle;
@@ -125,7 +132,7 @@ smc_status smc_mutate_rw(const smc_model* m, int precision, const void* obs, int
     a.acc_count = cnt;
     a.pending = nullptr;
     a.err = nullptr;
-    cudaError_t e = launch_mutate(a, precision, s);
+    cudaError_t e = launch_mutate(a, precision, kMutThreads, s);
     unsigned long long h = 0;
     if (e == cudaSuccess && accepted) {
         e = cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, s);
@@ -134,7 +141,27 @@ smc_status smc_mutate_rw(const smc_model* m, int precision, const void* obs, int
     }
     cudaFreeAsync(thp, s);
     cudaFreeAsync(cnt, s);
+    if (lq) cudaFreeAsync(lq, s);
     return from_cuda(e);
+}
+
+smc_status smc_mutate_rw(const smc_model* m, int precision, const void* obs, int T, double* theta,
+                         double* ll, double* lp, double* state, int P, const double* L, double phi,
+                         uint64_t seed, uint64_t cycle, uint64_t iter, uint64_t* accepted,
+                         void* stream)
+{
+    return mutate_impl(m, precision, obs, T, theta, ll, lp, state, P, nullptr, L, phi, seed, cycle,
+                       iter, accepted, stream);
+}
+
+smc_status smc_mutate_indep(const smc_model* m, int precision, const void* obs, int T, double* theta,
+                            double* ll, double* lp, double* state, int P, const double* mean,
+                            const double* L, double phi, uint64_t seed, uint64_t cycle, uint64_t iter,
+                            uint64_t* accepted, void* stream)
+{
+    if (!mean) return SMC_EINVAL;
+    return mutate_impl(m, precision, obs, T, theta, ll, lp, state, P, mean, L, phi, seed, cycle,
+                       iter, accepted, stream);
 }
 
 smc_status smc_loglik_grad(const smc_model* m, int precision, const void* obs, int T,

@@ -24,7 +24,7 @@ OK, EINVAL, ENOMEM, ECUDA, EDEGENERATE, ENONFINITE, ETIMEOUT, EDONE = range(8)
 EGARCH, LINREG = 0, 1
 FP64, FP32 = 0, 1
 DATA, POWER = 0, 1
-RW, MALA = 0, 1
+RW, MALA, INDEP = 0, 1, 2
 RESIDUAL, MULTINOMIAL, STRATIFIED, SYSTEMATIC = 0, 1, 2, 3
 STOP_DET, STOP_RNE = 0, 1
 
@@ -55,7 +55,8 @@ class smc_config(C.Structure):
                 ("h0_tenths", C.c_int), ("hmin_tenths", C.c_int), ("hmax_tenths", C.c_int),
                 ("acc_target", C.c_double), ("h_reset_each_cycle", C.c_int),
                 ("n_force", C.c_int), ("force_dates", C.c_int * MAX_FORCE),
-                ("search_passes", C.c_int), ("seed", C.c_uint64)]
+                ("search_passes", C.c_int), ("seed", C.c_uint64), ("burnin", C.c_int),
+                ("pit", C.c_int)]
 
 
 class smc_cycle_info(C.Structure):
@@ -83,6 +84,8 @@ def _declare(L):
     L.smc_cycle.argtypes = [vp, P(smc_cycle_info)]
     L.smc_run.argtypes = [vp, C.c_int, P(smc_cycle_info), P(C.c_int)]
     L.smc_log_ml.argtypes = [vp, dp, dp, dp]
+    L.smc_log_score.argtypes = [vp, dp, dp]
+    L.smc_pit.argtypes = [vp, dp, C.c_int]
     L.smc_moments.argtypes = [vp, dp, P(C.c_int)]
     L.smc_get_particles.argtypes = [vp, dp, dp, dp, dp]
     L.smc_launch_count.argtypes = []
@@ -123,6 +126,8 @@ def _declare(L):
     L.smc_linreg_width.restype = C.c_int
     L.smc_mutate_rw.argtypes = [P(smc_model), C.c_int, vp, C.c_int, vp, vp, vp, vp, C.c_int, vp,
                                 C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, P(C.c_uint64), vp]
+    L.smc_mutate_indep.argtypes = [P(smc_model), C.c_int, vp, C.c_int, vp, vp, vp, vp, C.c_int, vp, vp,
+                                   C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, P(C.c_uint64), vp]
     L.smc_loglik_grad.argtypes = [P(smc_model), C.c_int, vp, C.c_int, vp, C.c_int, vp, vp, vp, vp]
     L.smc_mutate_mala.argtypes = [P(smc_model), C.c_int, vp, C.c_int, vp, vp, vp, vp, vp, C.c_int, vp,
                                   C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, P(C.c_uint64), vp]
@@ -230,6 +235,7 @@ class Ctx:
         self.d = model.d
         self.P = cfg.J * cfg.N
         self._y = _f64(y)
+        self.T = len(self._y)
         self._X = _f64(X) if X is not None else None
         h = C.c_void_p()
         if theta0_on_device:
@@ -282,6 +288,18 @@ class Ctx:
         a, b, c = C.c_double(), C.c_double(), C.c_double()
         _check(lib().smc_log_ml(self.h, C.byref(a), C.byref(b), C.byref(c)), self.h)
         return a.value, b.value, c.value
+
+    def log_score(self):
+        """(log p(y_{b+1:T} | y_1:b), NSE) for the configured burn-in b."""
+        a, b = C.c_double(), C.c_double()
+        _check(lib().smc_log_score(self.h, C.byref(a), C.byref(b)), self.h)
+        return a.value, b.value
+
+    def pit(self):
+        """Probability integral transform of every observation (NaN until reached)."""
+        out = np.zeros(self.T)
+        _check(lib().smc_pit(self.h, _dptr(out), self.T), self.h)
+        return out
 
     def moments(self):
         out = np.zeros((self.d + 3, 4))
@@ -471,6 +489,17 @@ def mutate_rw(model, precision, obs, theta, ll, lp, state, L, phi, seed, cycle, 
     _check(lib().smc_mutate_rw(C.byref(model), precision, _ptr(obs), T, _ptr(theta), _ptr(ll),
                                _ptr(lp), _ptr(state), P, _ptr(L), float(phi), seed, cycle, it,
                                C.byref(acc), _stream(stream)))
+    return acc.value
+
+
+def mutate_indep(model, precision, obs, theta, ll, lp, state, mean, L, phi, seed, cycle, it, stream=None):
+    """One independent Gaussian Metropolis iteration, proposal N(mean, L L')."""
+    T = obs.shape[0]
+    P = theta.shape[1]
+    acc = C.c_uint64()
+    _check(lib().smc_mutate_indep(C.byref(model), precision, _ptr(obs), T, _ptr(theta), _ptr(ll),
+                                  _ptr(lp), _ptr(state), P, _ptr(mean), _ptr(L), float(phi), seed, cycle,
+                                  it, C.byref(acc), _stream(stream)))
     return acc.value
 
 

@@ -193,6 +193,95 @@ def test_mutate_step_matches_oracle(S, precision):
     assert 0.05 < nacc / P < 0.95
 
 
+def _oracle_log_alpha_indep(spec, y, th, ll, lp, mbar, Lm, phi, seed, cycle, it):
+    """log alpha of the independent sampler for every particle, by the oracle's
+    likelihood and a triangular solve, for judging decisions near the threshold."""
+    from scipy.linalg import solve_triangular
+    P, d = th.shape
+    la = np.zeros(P)
+    lu = np.zeros(P)
+    for n in range(P):
+        z = O.philox_normals(seed, n, it, cycle, d)
+        prop = mbar + Lm @ z
+        lpn = O.logprior(spec, prop)[0]
+        lln = O.loglik(spec, y, prop)[0] if lpn > -np.inf else -np.inf
+        u = solve_triangular(Lm, th[n] - mbar, lower=True)
+        la[n] = (lpn + phi * lln) - (lp[n] + phi * ll[n]) - 0.5 * u @ u + 0.5 * z @ z
+        lu[n] = O.philox_log_uniform(seed, n, it, cycle)
+    return la, lu
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mutate_indep_step_matches_oracle(S, precision):
+    """Independent Gaussian sampler (Section 3.3): same proposals at
+    mean + L z, same log q correction and decisions as the oracle."""
+    torch = torch_cuda()
+    prec = S.FP64 if precision == "fp64" else S.FP32
+    K, I_, T, P = 2, 2, 300, 1111
+    truth = egarch_truth(K, I_)
+    y = I.simulate_egarch(truth, T, seed=19)
+    spec = O.ModelSpec(K=K, I=I_, gamma=True)
+    th = particles(spec.d, truth, K, I_, True, P, 13)
+    ll, st = O.loglik(spec, y, th, with_state=True, nthreads=4)
+    lp = O.logprior(spec, th)
+    mbar, V = O.mean_cov(th)
+    Lm, _ = O.cholesky(V)
+    phi, seed, cycle, it = 0.05, 78, 4, 1
+    th_o, ll_o, lp_o, st_o, acc_o, nacc_o = O.mutate_indep(spec, y, th, ll, lp, st, mbar, Lm, phi, seed,
+                                                           cycle, it, nthreads=4)
+    m = S.model_egarch(K, I_, True)
+    obs = dev(y, torch.float32 if prec == S.FP32 else torch.float64)
+    tg, llg, lpg, stg = soa(th), dev(ll), dev(lp), soa(st)
+    nacc = S.mutate_indep(m, prec, obs, tg, llg, lpg, stg, dev(mbar), dev(Lm), phi, seed, cycle, it)
+    th_g, ll_g, lp_g, st_g = host(tg).T, host(llg), host(lpg), host(stg).T
+    acc_g = np.any(th_g != th, axis=1)
+    assert nacc == acc_g.sum()
+    diff = acc_g != acc_o.astype(bool)
+    if diff.any():
+        idx = np.nonzero(diff)[0]
+        la_all, lu_all = _oracle_log_alpha_indep(spec, y, th, ll, lp, mbar, Lm, phi, seed, cycle, it)
+        margin = np.abs(la_all[idx] - lu_all[idx])
+        scale = phi * (np.abs(ll[idx]) + np.abs(ll_o[idx]))
+        bound = 1e-8 if prec == S.FP64 else 1e-5 * scale + 1e-5
+        assert np.all(margin < bound), (margin, bound)
+        assert diff.sum() <= max(2, P // 100)
+    same = ~diff
+    tol = 1e-9 if prec == S.FP64 else 1e-4
+    np.testing.assert_allclose(th_g[same], th_o[same], rtol=tol, atol=1e-6 if prec == S.FP32 else 1e-12)
+    np.testing.assert_allclose(ll_g[same], ll_o[same], rtol=tol)
+    np.testing.assert_allclose(lp_g[same], lp_o[same], rtol=tol, atol=tol)
+    np.testing.assert_allclose(st_g[same], st_o[same], rtol=2e-3 if prec == S.FP32 else 1e-9,
+                               atol=2e-3 if prec == S.FP32 else 1e-12)
+    assert 0.02 < nacc / P < 0.98
+
+
+def test_mutate_indep_exact_posterior_accepts_all(S):
+    """Conjugate regression with q the exact posterior: every proposal is
+    accepted at mean + L z, as the oracle's pin states."""
+    torch = torch_cuda()
+    beta = np.array([0.5, -1.0, 2.0])
+    X, y = I.linreg_data(60, beta, 1.0, seed=3)
+    m0, s0 = np.zeros(3), np.full(3, 2.0)
+    Vn = np.linalg.inv(np.diag(1 / s0 ** 2) + X.T @ X)
+    mn = Vn @ (X.T @ y)
+    spec = O.ModelSpec(model=O.LINREG, p=3, sigma=1.0, prior_mean=m0, prior_sd=s0)
+    m = S.model_linreg(3, 1.0, m0, s0)
+    rec = np.zeros((60, S.linreg_width(3)))
+    rec[:, :3] = X
+    rec[:, 3] = y
+    P = 2000
+    th = np.random.default_rng(4).multivariate_normal(mn, 3 * Vn, size=P)
+    ll = O.loglik(spec, y, th, X=X)
+    lp = O.logprior(spec, th)
+    Lm = np.linalg.cholesky(Vn)
+    tg, llg, lpg = soa(th), dev(ll), dev(lp)
+    nacc = S.mutate_indep(m, S.FP64, dev(rec), tg, llg, lpg, None, dev(mn), dev(Lm), 1.0, 3, 2, 5)
+    assert nacc == P
+    th_o, ll_o, *_ = O.mutate_indep(spec, y, th, ll, lp, np.zeros((P, 1)), mn, Lm, 1.0, 3, 2, 5, X=X)
+    np.testing.assert_allclose(host(tg).T, th_o, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(host(llg), ll_o, rtol=1e-11)
+
+
 def test_mutate_linreg_matches_oracle(S):
     torch = torch_cuda()
     beta = np.array([0.5, -1.0, 2.0])

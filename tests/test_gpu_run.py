@@ -62,6 +62,52 @@ def test_linreg_run_matches_closed_form(S, resampler, tempering):
     ctx.close()
 
 
+@pytest.mark.parametrize("tempering", ["power", "data"])
+def test_linreg_independent_sampler_matches_closed_form(S, tempering):
+    """Section 3.3's independent Gaussian sampler (proposal N(mean, V) of the
+    population) reaches the exact log ML and posterior means; the hybrid
+    design cannot be recorded for it."""
+    X, y, m0, s0, lml, mn, Vn = _linreg()
+    J, N = 16, 512
+    m = S.model_linreg(3, 1.0, m0, s0)
+    c = S.config_default(J=J, N=N, precision=S.FP64, seed=12, mutation=S.INDEP,
+                         tempering=S.POWER if tempering == "power" else S.DATA)
+    th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), J * N, seed=6)
+    ctx = S.init(m, c, y, th0, X=X)
+    n, info = ctx.run()
+    assert info["done"] == 1
+    lm, nse, lt = ctx.log_ml()
+    assert abs(lm - lml) < 3.5 * nse + 0.02, (lm, lml, nse)
+    mom = ctx.moments()
+    for i in range(3):
+        assert abs(mom[i, 0] - mn[i]) < 3.5 * mom[i, 2] + 1e-4
+    ctx.close()
+    ctx = S.init(m, c, y, th0, X=X)
+    with pytest.raises(S.SMCError):
+        ctx.record_design()
+    ctx.close()
+
+
+def test_independent_sampler_egarch_matches_oracle_run(S):
+    """FP64 EGARCH(1,1) run with the independent sampler: GPU and oracle agree
+    on log ML within combined NSE."""
+    w = I.WORKLOADS["egarch11_T500"]
+    y = w.data()[:300]
+    m = S.model_egarch(1, 1, False)
+    mean, sd, lo = S.model_prior(m)
+    J, N = 8, 256
+    th0 = I.draw_prior(mean, sd, lo, J * N, seed=71)
+    ctx = S.init(m, S.config_default(J=J, N=N, precision=S.FP64, seed=3, mutation=S.INDEP), y, th0)
+    ctx.run()
+    lm, nse, _ = ctx.log_ml()
+    ctx.close()
+    spec = O.ModelSpec(K=1, I=1, gamma=False)
+    r = O.smc_run(spec, y, th0, J, N, tempering=1, mutation=O.INDEP, seed=3, nthreads=8)
+    assert r["status"] == 0
+    comb = math.hypot(nse, r["log_ml_nse"])
+    assert abs(lm - r["log_ml"]) < 4 * comb + 0.02, (lm, r["log_ml"], comb)
+
+
 @pytest.mark.parametrize("precision,tempering", [("fp64", "power"), ("fp32", "power"), ("fp32", "data")])
 def test_one_parameter_egarch_matches_quadrature(S, precision, tempering):
     tr = I.EgarchTruth(0.0, 0.01, (0.95,), (0.12,), (-0.05,))
@@ -205,8 +251,9 @@ def test_rne_stopping_rule_run(S):
 
 
 def test_launch_shapes_give_identical_runs(S):
-    """Two particles per thread (either block size) computes every particle's
-    proposal, recursion and decision exactly as one particle per thread."""
+    """Every launch shape (32-, 64- or 128-thread blocks, one or two particles
+    per thread) computes each particle's proposal, recursion and decision
+    exactly as one particle per thread in 128-thread blocks."""
     truth = I.WORKLOADS["egarch22_T5000"].truth
     y = I.simulate_egarch(truth, 700, seed=8)
     m = S.model_egarch(2, 2, True)
@@ -214,7 +261,8 @@ def test_launch_shapes_give_identical_runs(S):
     J, N = 16, 300   # P = 4800: ragged against 64/128/256-particle tiles
     th0 = I.draw_prior(mean, sd, lo, J * N, seed=9)
     out = []
-    for ppt, thr in [(1, 128), (2, 64), (2, 128)]:
+    shapes = [(1, 128), (1, 64), (1, 32), (2, 64), (2, 128)]
+    for ppt, thr in shapes:
         ctx = S.init(m, S.config_default(J=J, N=N, precision=S.FP32, seed=5), y, th0)
         ctx.set_launch_shape(ppt, thr)
         ctx.run()
@@ -226,7 +274,121 @@ def test_launch_shapes_give_identical_runs(S):
         np.testing.assert_allclose(ll, out[0][1][1], rtol=1e-12)
     ctx = S.init(m, S.config_default(J=J, N=N, precision=S.FP32, seed=5), y, th0)
     ppt, thr, ms = ctx.autotune(iters=1)
-    assert (ppt, thr) in [(1, 128), (2, 64), (2, 128)] and ms > 0
+    assert (ppt, thr) in shapes and ms > 0
     ctx.run()
     assert ctx.log_ml()[0] == pytest.approx(out[0][0][0], rel=1e-12, abs=1e-9)
+    ctx.close()
+
+
+def test_small_blocks_fp64_and_invalid_shapes(S):
+    """FP64 runs give the same particles with 32-thread blocks; shapes outside
+    the supported set are rejected."""
+    truth = I.WORKLOADS["egarch11_T500"].truth
+    y = I.simulate_egarch(truth, 300, seed=2)
+    m = S.model_egarch(1, 1, False)
+    mean, sd, lo = S.model_prior(m)
+    th0 = I.draw_prior(mean, sd, lo, 4 * 100, seed=3)
+    out = []
+    for thr in (128, 32):
+        ctx = S.init(m, S.config_default(J=4, N=100, precision=S.FP64, seed=1), y, th0)
+        ctx.set_launch_shape(1, thr)
+        for _ in range(3):
+            ctx.cycle()
+        out.append(ctx.particles())
+        if thr == 32:
+            for bad in [(1, 96), (2, 32), (3, 64)]:
+                with pytest.raises(S.SMCError):
+                    ctx.set_launch_shape(*bad)
+        ctx.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+# ---------------------------------------------- log score and PIT (Section 4.1)
+def _prefix_lml(X, y, m0, s0, t):
+    V0 = np.diag(s0 ** 2)
+    return stats.multivariate_normal(X[:t] @ m0, np.eye(t) + X[:t] @ V0 @ X[:t].T).logpdf(y[:t])
+
+
+def _predictive_cdf(X, y, m0, s0):
+    Vinv, b = np.diag(1 / s0 ** 2), np.diag(1 / s0 ** 2) @ m0
+    out = np.zeros(len(y))
+    for s in range(len(y)):
+        V = np.linalg.inv(Vinv)
+        x = X[s]
+        out[s] = stats.norm.cdf((y[s] - x @ (V @ b)) / math.sqrt(1.0 + x @ V @ x))
+        Vinv = Vinv + np.outer(x, x)
+        b = b + x * y[s]
+    return out
+
+
+def test_linreg_log_score_and_pit_match_closed_forms(S):
+    X, y, m0, s0, lml, mn, Vn = _linreg()
+    b = 20
+    J, N = 16, 512
+    m = S.model_linreg(3, 1.0, m0, s0)
+    c = S.config_default(J=J, N=N, precision=S.FP64, seed=13, tempering=S.DATA, burnin=b, pit=1)
+    th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), J * N, seed=7)
+    ctx = S.init(m, c, y, th0, X=X)
+    ts = []
+    while True:
+        info = ctx.cycle()
+        ts.append(info["t"])
+        if info["done"]:
+            break
+    assert b in ts
+    ls, nse = ctx.log_score()
+    exact = lml - _prefix_lml(X, y, m0, s0, b)
+    assert abs(ls - exact) < 3.5 * nse + 0.02, (ls, exact, nse)
+    lm, lnse, _ = ctx.log_ml()
+    assert abs(lm - lml) < 3.5 * lnse + 0.02
+    pit = ctx.pit()
+    err = np.abs(pit - _predictive_cdf(X, y, m0, s0))
+    assert np.all(np.isfinite(pit)) and err.max() < 0.08 and err.mean() < 0.02, (err.max(), err.mean())
+    ctx.close()
+    # the same prior draws give the oracle's PIT up to rounding through the first cycle
+    spec = O.ModelSpec(model=O.LINREG, p=3, sigma=1.0, prior_mean=m0, prior_sd=s0)
+    r = O.smc_run(spec, y, th0, J, N, X=X, tempering=0, pit=True, burnin=b, seed=13)
+    t1 = min(ts[0], r["t"][0])
+    np.testing.assert_allclose(pit[:t1], r["pit"][:t1], rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_egarch_pit_first_cycle_matches_oracle(S, precision):
+    """EGARCH(1,2): through the first cycle both sides weight the same prior
+    draws, so the PIT values agree up to rounding (FP32: the indicator can flip
+    only where the simulated and observed shocks tie to FP32 precision)."""
+    tr = I.EgarchTruth(0.0, 0.01, (0.95,), (0.12,), (-0.05,))
+    y = I.simulate_egarch(tr, 200, seed=41)
+    m = S.model_egarch(1, 2, True)
+    mean, sd, lo = S.model_prior(m)
+    J, N = 8, 512
+    th0 = I.draw_prior(mean, sd, lo, J * N, seed=42)
+    prec = S.FP64 if precision == "fp64" else S.FP32
+    ctx = S.init(m, S.config_default(J=J, N=N, precision=prec, seed=9, tempering=S.DATA, pit=1), y, th0)
+    tg = ctx.cycle()["t"]
+    pit = ctx.pit()
+    ctx.close()
+    assert np.all(np.isfinite(pit[:tg])) and np.all(np.isnan(pit[tg:]))   # not yet reached
+    spec = O.ModelSpec(K=1, I=2, gamma=True)
+    r = O.smc_run(spec, y, th0, J, N, tempering=0, pit=True, seed=9, max_cycles=1)
+    t1 = min(tg, r["t"][0])
+    tol = 1e-9 if precision == "fp64" else 2e-3
+    np.testing.assert_allclose(pit[:t1], r["pit"][:t1], rtol=0, atol=tol)
+
+
+def test_log_score_and_pit_need_data_tempering(S):
+    X, y, m0, s0, lml, mn, Vn = _linreg()
+    m = S.model_linreg(3, 1.0, m0, s0)
+    th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), 2 * 64, seed=7)
+    for kw in (dict(burnin=10), dict(pit=1)):
+        with pytest.raises(S.SMCError):
+            S.init(m, S.config_default(J=2, N=64, precision=S.FP64, tempering=S.POWER, **kw), y, th0, X=X)
+    with pytest.raises(S.SMCError):
+        S.init(m, S.config_default(J=2, N=64, precision=S.FP64, tempering=S.DATA, burnin=len(y)), y, th0, X=X)
+    ctx = S.init(m, S.config_default(J=2, N=64, precision=S.FP64, tempering=S.DATA), y, th0, X=X)
+    with pytest.raises(S.SMCError):
+        ctx.pit()
+    with pytest.raises(S.SMCError):
+        ctx.log_score()
     ctx.close()
