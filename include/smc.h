@@ -224,11 +224,13 @@ smc_status smc_design_get(smc_ctx* ctx, double* x, int* R, double* L);
 smc_status smc_design_replay(smc_ctx* ctx, int ncycles, const double* x, const int* R, const double* L);
 
 /* Launch shape of the M-phase mutation kernel.  For FP32 EGARCH random-walk
- * runs a thread can carry two particles (their recursions interleave, hiding
- * each other's dependency latency when particles per scheduler are few).
+ * runs a thread can carry two particles, whose recursions run side by side in
+ * Blackwell's paired FP32 instructions (one issue slot for both; results
+ * bitwise those of one particle per thread).
  * smc_autotune times `iters` Metropolis iterations of each candidate shape
  * (random walk: 1 particle x 128, 64 or 32 threads per block; FP32 EGARCH
- * also 2 x 64 and 2 x 128; MALA: 1 x 128 only) on a snapshot of the particles,
+ * also 2 particles x 32, 64 or 128 threads, the pair's recursions in packed
+ * FP32x2 instructions; MALA: 1 x 128 only) on a snapshot of the particles,
  * restores them, and keeps the fastest; outputs (host, nullable): the shape and
  * its time per iteration.  Results do not depend on the shape.
  * Smaller blocks split P particles into more blocks, which evens the load over

@@ -944,6 +944,7 @@ smc_status smc_autotune(smc_ctx* ctx, int iters, int* ppt, int* threads, double*
         cand.push_back({1, 32});
     }
     if (fp32_egarch) {
+        cand.push_back({2, 32});
         cand.push_back({2, 64});
         cand.push_back({2, 128});
     }
@@ -1003,7 +1004,6 @@ smc_status smc_set_launch_shape(smc_ctx* ctx, int ppt, int threads)
     if (ppt == 2 && !(ctx->model.model == SMC_EGARCH && ctx->cfg.precision == SMC_FP32 &&
                       ctx->cfg.mutation == SMC_RW))
         return set_err(ctx, SMC_EINVAL, "two particles per thread needs the FP32 EGARCH random walk");
-    if (ppt == 2 && threads == 32) return set_err(ctx, SMC_EINVAL, "two particles per thread use 64 or 128 threads");
     ctx->ppt = ppt;
     ctx->mut_threads = threads;
     return SMC_OK;

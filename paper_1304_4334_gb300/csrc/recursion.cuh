@@ -556,16 +556,179 @@ __device__ __forceinline__ bool run_egarch_f32(EgarchF32<K, I>& mdl, ObsPipe<flo
     return true;
 }
 
-// Two particles per thread: the two recursions are independent, so the
-// compiler interleaves their instruction streams and each hides the other's
-// dependency latency.
+// ------------------------------------------- two particles in packed FP32x2
+// Blackwell's paired FP32 instructions (fma/add/mul/sub .f32x2) run the same
+// operation on two particles' recursions in one issue slot.  The pair is
+// packed from two set-up EgarchF32 models and unpacked back into them, and
+// every lane performs exactly the scalar recursion's operations in its order
+// (IEEE round-to-nearest per lane), so the results are bitwise those of two
+// EgarchF32 runs.  The mixture terms are carried negated where that saves a
+// negation: y_i = z_i^2 - c_i = -x_i exactly, max_i x_i = max_i(-y_i),
+// x_0 - x_1 = y_1 - y_0.
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b)
+{
+    unsigned long long x, y, r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+    float2 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+    return o;
+}
+
+template <int K, int I>
+struct EgarchF32Pair {
+    float2 nmu;                            // -mu_Y
+    float2 al[K], be[K], ga[K], nb[K];
+    float2 a[I], b[I], nc[I];              // 1/sigma_i; -mu_i s / sigma_i; -log2(p_i / sigma_i)
+    float2 v0[K];
+    float2 v[K], es;
+    float2 sh, sm, prod;                   // I = 1: sm holds the negated sum
+    float part[2];
+    double acc[2];
+
+    __device__ __forceinline__ void load(const EgarchF32<K, I>& A, const EgarchF32<K, I>& B)
+    {
+        nmu = make_float2(-A.mu, -B.mu);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            al[k] = make_float2(A.al[k], B.al[k]);
+            be[k] = make_float2(A.be[k], B.be[k]);
+            ga[k] = make_float2(A.ga[k], B.ga[k]);
+            nb[k] = make_float2(A.nb[k], B.nb[k]);
+            v0[k] = make_float2(A.v0[k], B.v0[k]);
+            v[k] = make_float2(A.v[k], B.v[k]);
+        }
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+            a[i] = make_float2(A.a[i], B.a[i]);
+            b[i] = make_float2(A.b[i], B.b[i]);
+            nc[i] = make_float2(-A.c[i], -B.c[i]);
+        }
+        es = make_float2(A.es, B.es);
+        sh = make_float2(A.sh, B.sh);
+        sm = I == 1 ? make_float2(-A.sm, -B.sm) : make_float2(A.sm, B.sm);
+        prod = make_float2(A.prod, B.prod);
+        part[0] = A.part;
+        part[1] = B.part;
+        acc[0] = A.acc;
+        acc[1] = B.acc;
+    }
+
+    __device__ __forceinline__ void store(EgarchF32<K, I>& A, EgarchF32<K, I>& B) const
+    {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            A.v[k] = v[k].x;
+            B.v[k] = v[k].y;
+        }
+        A.es = es.x;
+        B.es = es.y;
+        A.sh = sh.x;
+        B.sh = sh.y;
+        A.sm = I == 1 ? -sm.x : sm.x;
+        B.sm = I == 1 ? -sm.y : sm.y;
+        A.prod = prod.x;
+        B.prod = prod.y;
+        A.part = part[0];
+        B.part = part[1];
+        A.acc = acc[0];
+        B.acc = acc[1];
+    }
+
+    template <bool kFirst>
+    __device__ __forceinline__ void step(float y)
+    {
+        if constexpr (kFirst) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = v0[k];
+        } else {
+            float2 vp[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) vp[k] = f2_fma(al[k], v[k], nb[k]);
+            const float2 ae = make_float2(fabsf(es.x), fabsf(es.y));
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = f2_fma(be[k], ae, f2_fma(ga[k], es, vp[k]));
+        }
+        float2 e = v[0];
+#pragma unroll
+        for (int k = 1; k < K; ++k) e = f2_add(e, v[k]);
+        sh = f2_add(sh, e);
+        const float2 ex = make_float2(ex2_approx(-e.x), ex2_approx(-e.y));
+        es = f2_mul(f2_add(make_float2(y, y), nmu), ex);
+        if constexpr (I == 1) {
+            sm = f2_fma(es, es, sm);
+        } else if constexpr (I == 2) {
+            const float2 z0 = f2_fma(a[0], es, b[0]), z1 = f2_fma(a[1], es, b[1]);
+            const float2 y0 = f2_fma(z0, z0, nc[0]), y1 = f2_fma(z1, z1, nc[1]);
+            sm = f2_add(sm, make_float2(fmaxf(-y0.x, -y1.x), fmaxf(-y0.y, -y1.y)));
+            const float2 dd = f2_sub(y1, y0);
+            const float2 r = make_float2(ex2_approx(-fabsf(dd.x)), ex2_approx(-fabsf(dd.y)));
+            prod = f2_fma(prod, r, prod);
+        } else {
+            float2 yv[I];
+#pragma unroll
+            for (int i = 0; i < I; ++i) {
+                const float2 z = f2_fma(a[i], es, b[i]);
+                yv[i] = f2_fma(z, z, nc[i]);
+            }
+            float2 m = make_float2(-yv[0].x, -yv[0].y);
+#pragma unroll
+            for (int i = 1; i < I; ++i) m = make_float2(fmaxf(m.x, -yv[i].x), fmaxf(m.y, -yv[i].y));
+            float2 t = f2_add(yv[0], m);
+            float2 ssum = make_float2(ex2_approx(-t.x), ex2_approx(-t.y));
+#pragma unroll
+            for (int i = 1; i < I; ++i) {
+                t = f2_add(yv[i], m);
+                ssum = f2_add(ssum, make_float2(ex2_approx(-t.x), ex2_approx(-t.y)));
+            }
+            sm = f2_add(sm, m);
+            prod = f2_mul(prod, ssum);
+        }
+    }
+
+    // The scalar model's flush, lane by lane.
+    __device__ __forceinline__ void flush()
+    {
+        float u0, u1;
+        if constexpr (I == 1) {
+            u0 = -(sm.x + sh.x);
+            u1 = -(sm.y + sh.y);
+        } else {
+            u0 = sm.x - sh.x;
+            u1 = sm.y - sh.y;
+            u0 += lg2_approx(prod.x);
+            u1 += lg2_approx(prod.y);
+        }
+        part[0] += u0;
+        part[1] += u1;
+        sh = sm = make_float2(0.0f, 0.0f);
+        prod = make_float2(1.0f, 1.0f);
+    }
+
+    __device__ __forceinline__ void flush_fp64()
+    {
+        acc[0] += (double)part[0];
+        acc[1] += (double)part[1];
+        part[0] = part[1] = 0.0f;
+    }
+};
+
+// Two particles per thread through the packed recursion; A and B hold the
+// two models' end states and sums afterwards.
 template <int K, int I>
 __device__ __forceinline__ bool run_egarch_f32_x2(EgarchF32<K, I>& ma, EgarchF32<K, I>& mb,
                                                   ObsPipe<float, kChunkF32>& pipe, int T)
 {
+    EgarchF32Pair<K, I> pr;
+    pr.load(ma, mb);
     for (int c = 0; c < pipe.nchunks; ++c) {
         if (!pipe.wait(c)) {
             pipe.drain(c);
+            pr.store(ma, mb);
             return false;
         }
         const float* yb = pipe.buf + (c & 1) * kChunkF32;
@@ -575,64 +738,43 @@ __device__ __forceinline__ bool run_egarch_f32_x2(EgarchF32<K, I>& ma, EgarchF32
             const float4* y4 = reinterpret_cast<const float4*>(yb + 32 * u);
             if (c == 0 && u == 0) {
                 float4 q = y4[0];
-                ma.template step<true>(q.x);
-                mb.template step<true>(q.x);
-                ma.template step<false>(q.y);
-                mb.template step<false>(q.y);
-                ma.template step<false>(q.z);
-                mb.template step<false>(q.z);
-                ma.template step<false>(q.w);
-                mb.template step<false>(q.w);
+                pr.template step<true>(q.x);
+                pr.template step<false>(q.y);
+                pr.template step<false>(q.z);
+                pr.template step<false>(q.w);
 #pragma unroll
                 for (int j = 1; j < 8; ++j) {
                     q = y4[j];
-                    ma.template step<false>(q.x);
-                    mb.template step<false>(q.x);
-                    ma.template step<false>(q.y);
-                    mb.template step<false>(q.y);
-                    ma.template step<false>(q.z);
-                    mb.template step<false>(q.z);
-                    ma.template step<false>(q.w);
-                    mb.template step<false>(q.w);
+                    pr.template step<false>(q.x);
+                    pr.template step<false>(q.y);
+                    pr.template step<false>(q.z);
+                    pr.template step<false>(q.w);
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const float4 q = y4[j];
-                    ma.template step<false>(q.x);
-                    mb.template step<false>(q.x);
-                    ma.template step<false>(q.y);
-                    mb.template step<false>(q.y);
-                    ma.template step<false>(q.z);
-                    mb.template step<false>(q.z);
-                    ma.template step<false>(q.w);
-                    mb.template step<false>(q.w);
+                    pr.template step<false>(q.x);
+                    pr.template step<false>(q.y);
+                    pr.template step<false>(q.z);
+                    pr.template step<false>(q.w);
                 }
             }
-            ma.flush();
-            mb.flush();
-            if ((u & 7) == 7) {
-                ma.flush_fp64();
-                mb.flush_fp64();
-            }
+            pr.flush();
+            if ((u & 7) == 7) pr.flush_fp64();
         }
         const int rem = cnt & 31;
         if (rem) {
             for (int r = 0; r < rem; ++r) {
                 const int tl = 32 * nunits + r;
-                if (c == 0 && tl == 0) {
-                    ma.template step<true>(yb[tl]);
-                    mb.template step<true>(yb[tl]);
-                } else {
-                    ma.template step<false>(yb[tl]);
-                    mb.template step<false>(yb[tl]);
-                }
+                if (c == 0 && tl == 0) pr.template step<true>(yb[tl]);
+                else pr.template step<false>(yb[tl]);
             }
-            ma.flush();
-            mb.flush();
+            pr.flush();
         }
         pipe.release(c);
     }
+    pr.store(ma, mb);
     return true;
 }
 

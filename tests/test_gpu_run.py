@@ -261,7 +261,7 @@ def test_launch_shapes_give_identical_runs(S):
     J, N = 16, 300   # P = 4800: ragged against 64/128/256-particle tiles
     th0 = I.draw_prior(mean, sd, lo, J * N, seed=9)
     out = []
-    shapes = [(1, 128), (1, 64), (1, 32), (2, 64), (2, 128)]
+    shapes = [(1, 128), (1, 64), (1, 32), (2, 32), (2, 64), (2, 128)]
     for ppt, thr in shapes:
         ctx = S.init(m, S.config_default(J=J, N=N, precision=S.FP32, seed=5), y, th0)
         ctx.set_launch_shape(ppt, thr)
@@ -296,7 +296,7 @@ def test_small_blocks_fp64_and_invalid_shapes(S):
             ctx.cycle()
         out.append(ctx.particles())
         if thr == 32:
-            for bad in [(1, 96), (2, 32), (3, 64)]:
+            for bad in [(1, 96), (2, 32), (3, 64)]:   # (2, 32): FP64 has no packed pair
                 with pytest.raises(S.SMCError):
                     ctx.set_launch_shape(*bad)
         ctx.close()
