@@ -409,8 +409,10 @@ smc_status smc_group_moments(const double* g, int nf, int J, int N, double* out,
  * address (cudaGetSymbolAddress) with that device current; make that first
  * call before any stream capture.  All calls on a device share the array:
  * calls whose kernels overlap on the GPU (unordered streams) race on it.
- * Every entry read in a call is written earlier in the same call, so no
- * clearing is needed.  Arguments, outputs and errors as smc_cov_chol. */
+ * Every partial sum read in a call is written earlier in the same call and
+ * the reduction's counter (the array's last word) is back at zero when a call
+ * ends, so no clearing is needed.  Arguments, outputs and errors as
+ * smc_cov_chol. */
 smc_status smc_cov_chol_noalloc(const double* theta, int d, int P, int h_tenths, double* mean,
                                 double* cov, double* L, void* stream);
 

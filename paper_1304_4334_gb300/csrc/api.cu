@@ -214,6 +214,10 @@ static void fill_model_dev(const smc_model& m, ModelDev& d)
         d.prior_isd[i] = 1.0 / sd;
         d.prior_c[i] = -0.5 * kLog2Pi - std::log(sd);
         d.prior_lo[i] = m.prior_lo[i];
+        d.prior_mean_f[i] = (float)d.prior_mean[i];
+        d.prior_isd_f[i] = (float)d.prior_isd[i];
+        d.prior_c_f[i] = (float)d.prior_c[i];
+        d.prior_lo_f[i] = (float)d.prior_lo[i];
     }
 }
 
@@ -353,7 +357,7 @@ static void release(smc_ctx* c)
                     c->grad[0], c->grad[1], c->ckpt, c->design_L,
                     c->state[0], c->state[1], c->thp, c->logw, c->g, c->a, c->lw, c->gstat,
                     c->idx, c->cov_part, c->search_part, c->cd_part, c->mom_part, c->mom_out, c->ml_out,
-                    c->L, c->qmean, c->lq, c->a_score, c->pit, c->gather_ptrs, c->ctl};
+                    c->L, c->qmean, c->covtile, c->covshift_f, c->cov_tot, c->cov_counter, c->lq, c->a_score, c->pit, c->gather_ptrs, c->ctl};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->ctl_host) cudaFreeHost(c->ctl_host);
@@ -429,10 +433,17 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
         // Sigma = h^2 V; the independent sampler takes V itself (h pinned at
         // 10 tenths for the factor, still updated from the acceptance rate)
         // and the pooled mean.
+        // After the first iteration of an M phase the previous mutation
+        // launch has left the covariance tile sums of the current particles.
         const bool indep = c.mutation == SMC_INDEP;
-        CU(launch_cov(th, d, P, ctx->cov_part, ctx->cov_G, ctx->ctl, indep ? 10 : 0, c.acc_target,
-                      c.hmin_tenths, c.hmax_tenths, indep ? ctx->qmean : nullptr, nullptr, ctx->L,
-                      ctx->stream));
+        if (r > 0 && ctx->tiles_ready)
+            CU(launch_cov_tiles(ctx->covtile, ctx->ntiles, ctx->tile_kd, d, P, ctx->cov_tot, ctx->cov_counter,
+                                ctx->covshift_f, ctx->qmean, ctx->ctl, indep ? 10 : 0, c.acc_target,
+                                c.hmin_tenths, c.hmax_tenths, ctx->L, ctx->stream));
+        else
+            CU(launch_cov(th, d, P, ctx->cov_part, ctx->cov_G, ctx->cov_counter, ctx->ctl, indep ? 10 : 0,
+                          c.acc_target, c.hmin_tenths, c.hmax_tenths, ctx->qmean, nullptr, ctx->L,
+                          ctx->stream, ctx->covshift_f));
         if (indep) CU(launch_indep_logq(th, d, P, ctx->L, ctx->qmean, ctx->lq, ctx->stream));
     }
     if (ctx->record) {
@@ -493,6 +504,11 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
     a.L = ctx->L;
     a.qmean = c.mutation == SMC_INDEP ? ctx->qmean : nullptr;
     a.lq = ctx->lq;
+    const bool tiles = ctx->covtile && !ctx->replay;
+    a.covtile = tiles ? ctx->covtile : nullptr;
+    a.covshift = ctx->covshift_f;
+    a.ntiles = ctx->ntiles;
+    ctx->tiles_ready = tiles;
     a.phi = phi;
     a.seed = c.seed;
     a.cycle = (uint64_t)ctx->cycle;
@@ -777,7 +793,7 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
     CU(dalloc(&ctx->gstat, (size_t)J * 3));
     CU(dalloc(&ctx->idx, Ps));
     ctx->cov_G = cov_grid(P);
-    CU(dalloc(&ctx->cov_part, (size_t)(ctx->cov_G + 1) * (d + d * (d + 1) / 2)));
+    CU(dalloc(&ctx->cov_part, (size_t)(ctx->cov_G + 1) * (d + d * (d + 1) / 2)));   // + totals row
     CU(dalloc(&ctx->search_part, search_part_len(P)));
     CU(dalloc(&ctx->cd_part, (size_t)((P + kMutThreads - 1) / kMutThreads) * kCdataChunk * 3));
     const int nf_max = d + 3;
@@ -786,6 +802,18 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
     CU(dalloc(&ctx->ml_out, 3));
     CU(dalloc(&ctx->L, (size_t)d * d));
     CU(dalloc(&ctx->qmean, (size_t)d));
+    {
+        const int nacc = d + d * (d + 1) / 2;
+        // the mutation kernels' compile-time parameter bound (Table 1 count)
+        ctx->tile_kd = m->model == SMC_LINREG ? 8 : (m->I == 1 ? 2 + 3 * m->K : 2 + 3 * m->K + 3 * m->I);
+        const int kd = ctx->tile_kd;
+        ctx->ntiles = (P + 31) / 32;
+        if (c->mutation != SMC_MALA) CU(dalloc(&ctx->covtile, (size_t)ctx->ntiles * (kd + kd * (kd + 1) / 2)));
+        CU(dalloc(&ctx->covshift_f, (size_t)d));
+        CU(dalloc(&ctx->cov_tot, (size_t)nacc));
+        CU(dalloc(&ctx->cov_counter, 1));
+        CU(cudaMemset(ctx->cov_counter, 0, sizeof(unsigned int)));
+    }
     if (c->mutation == SMC_INDEP) CU(dalloc(&ctx->lq, Ps));
     CU(dalloc(&ctx->ctl, 1));
     CU(cudaMallocHost((void**)&ctx->ctl_host, sizeof(Ctl)));

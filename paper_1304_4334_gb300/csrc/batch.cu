@@ -167,6 +167,9 @@ static void fill_descriptors(smc_batch* b, const std::vector<int>& R)
         a.L = c->L;
         a.qmean = nullptr;
         a.lq = nullptr;
+        a.covtile = c->covtile;
+        a.covshift = c->covshift_f;
+        a.ntiles = c->ntiles;
         a.phi = c->phi;
         a.seed = c->cfg.seed;
         a.cycle = (uint64_t)c->cycle;
@@ -189,6 +192,11 @@ static void fill_descriptors(smc_batch* b, const std::vector<int>& R)
         j.hmin = c->cfg.hmin_tenths;
         j.hmax = c->cfg.hmax_tenths;
         j.R = R[i];
+        j.tiles = c->covtile;
+        j.ntiles = c->ntiles;
+        j.tile_kd = c->tile_kd;
+        j.shift_f = c->covshift_f;
+        j.mean = c->qmean;
     }
 }
 

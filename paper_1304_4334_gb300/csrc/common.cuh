@@ -97,6 +97,25 @@ __device__ __forceinline__ double log_uniform_mh(uint64_t seed, uint64_t p, uint
     return log(uniform53(r.v0));
 }
 
+// Metropolis-Hastings decision log u < log_alpha for the uniform of
+// log_uniform_mh, without the FP64 logarithm in nearly all cases: the log of
+// the 24-bit uniform u24 (the centre of the 2^-24 interval holding the 53-bit
+// uniform, so |u24 - u53| <= 2^-25) is within 3e-5 of log u53 when
+// u24 >= 2^-10, and the FP32 logarithm and rounding of log_alpha add at most
+// ~1e-6 while |log_alpha| < 20 (beyond that the margin is large).  A decision
+// more than 1e-3 from the threshold is therefore the FP64 decision; the rest,
+// and u24 < 2^-10, take the FP64 logarithm.  A NaN log_alpha rejects.
+__device__ __forceinline__ bool mh_accept(uint64_t seed, uint64_t p, uint64_t iter, uint64_t cycle,
+                                          double log_alpha)
+{
+    const U64x4 r = philox4x64_10(p, iter, cycle, (uint64_t)kTagUniform << 32, seed, 0);
+    const float u24 = ((float)(uint32_t)(r.v0 >> 40) + 0.5f) * 0x1.0p-24f;
+    const float lu = __logf(u24);
+    const float la = (float)log_alpha;
+    if (u24 >= 0x1.0p-10f && fabsf(lu - la) > 1e-3f) return lu < la;
+    return log(uniform53(r.v0)) < log_alpha;
+}
+
 // ------------------------------------------------------------ SFU instructions
 // Hardware base-2 exponential / logarithm (PTX ex2.approx / lg2.approx, flush
 // to zero).  Used only on the FP32 path, whose tolerance against the FP64

@@ -47,7 +47,15 @@ struct smc_ctx {
     double* mom_out = nullptr;       // [nf][4]
     double* ml_out = nullptr;        // [3]
     double* L = nullptr;             // [d][d]
-    double* qmean = nullptr;         // [d] independent-sampler proposal mean
+    double* qmean = nullptr;         // [d] pooled mean of the particles at the last covariance
+                                     // (independent-sampler proposal mean; shift of the tiles)
+    float* covtile = nullptr;        // [kD + kD(kD+1)/2][ntiles] mutation-kernel covariance tile sums
+    float* covshift_f = nullptr;     // [d] the tiles' shift (pooled mean rounded to FP32)
+    int tile_kd = 0;                 // the mutation policy's parameter bound kD
+    double* cov_tot = nullptr;       // [nacc] combined tile sums
+    unsigned int* cov_counter = nullptr;  // last-block counter of the covariance reduction (zero between launches)
+    int ntiles = 0;
+    bool tiles_ready = false;        // covtile holds the current particles' sums
     double* lq = nullptr;            // [P] independent sampler: log q of the current particles
     double** gather_ptrs = nullptr;  // [2][nrows] device row-pointer tables
     int gather_rows = 0;

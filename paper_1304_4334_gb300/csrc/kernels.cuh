@@ -32,6 +32,13 @@ struct MutateArgs {
     int ns;
     const double* L;        // [d][d] lower Cholesky factor of h^2 V, row-major
     const double* qmean;    // [d] independent-sampler mean (nullptr: random walk)
+    // Covariance of the next iteration (nullable): per 32-particle tile, FP32
+    // sums of theta_i - covshift_i and of their products over the tile's
+    // particles after this iteration's decision, entry-major
+    // [kD + kD(kD+1)/2][ntiles] with kD the policy's parameter bound.
+    float* covtile;
+    const float* covshift;  // [d] the tiles' shift (the pooled mean rounded to FP32)
+    int ntiles;
     const double* lq;       // [P] independent sampler: log q(theta) of the current particles
     double phi;
     uint64_t seed, cycle, iter;
@@ -115,6 +122,7 @@ struct PolicyEgarchF32 {
     static constexpr int kChunk = kChunkF32;
     using Model = EgarchF32<K, I>;
     static constexpr int kNs = K + 1;
+    static constexpr int kMaxFree = I == 1 ? 2 + 3 * K : 2 + 3 * K + 3 * I;   // Table 1
     __device__ static void setup(Model& mdl, const ModelDev& m, const Real* full)
     {
         mdl.setup(full, m.gamma, m.eps0_zero);
@@ -140,6 +148,7 @@ struct PolicyEgarchF64 {
     static constexpr int kChunk = kChunkF64;
     using Model = EgarchF64<K, I>;
     static constexpr int kNs = K + 1;
+    static constexpr int kMaxFree = I == 1 ? 2 + 3 * K : 2 + 3 * K + 3 * I;
     __device__ static void setup(Model& mdl, const ModelDev& m, const Real* full)
     {
         mdl.setup(full, m.gamma, m.eps0_zero);
@@ -163,6 +172,7 @@ struct PolicyLinreg {
     static constexpr int kChunk = kChunkF64;
     using Model = LinregF64;
     static constexpr int kNs = 0;
+    static constexpr int kMaxFree = 8;
     __device__ static void setup(Model& mdl, const ModelDev& m, const Real* full)
     {
         mdl.setup(full, m.p, m.sigma);
@@ -203,6 +213,73 @@ struct MutateSmem {
     unsigned int acc_s;
 };
 
+// Row of entry q of the packed lower triangle (q = i(i+1)/2 + k, k <= i).
+__host__ __device__ constexpr int tri_row(int q)
+{
+    int i = 0;
+    while ((i + 1) * (i + 2) / 2 <= q) ++i;
+    return i;
+}
+
+// Covariance tile sums of one warp's 32 consecutive particles (p is this
+// lane's particle; lanes past P contribute zeros): S1_i (entry i) and S2_ik
+// (entry kD + i(i+1)/2 + k, k <= i) of x_i = theta_i - shift_i in FP32, for
+// the compile-time bound kD >= d (entries past d are zero).  The warp forms
+// the products 16 entries at a time and reduce-scatters them in four halving
+// levels and one exchange, after which lanes 2e and 2e + 1 hold entry e of the
+// group: one shuffle per entry instead of five, with independent shuffles at
+// each level.
+// The tile is the same 32 particles in every launch shape, so the covariance
+// does not depend on the shape.  Reads the particle's theta after the
+// decision; covtile is [kD + kD(kD+1)/2][ntiles].
+template <int kD>
+__device__ __forceinline__ void cov_tile_sums(const MutateArgs& a, int p, bool active)
+{
+    constexpr int kAcc = kD + kD * (kD + 1) / 2;
+    constexpr int kGroups = (kAcc + 15) / 16;
+    const int tile = p >> 5;
+    if (tile >= a.ntiles) return;   // a whole warp past P (warp-uniform)
+    const int lane = threadIdx.x & 31;
+    const size_t P = (size_t)a.P;
+    const int d = a.m.d;
+    float x[kD];
+#pragma unroll
+    for (int i = 0; i < kD; ++i) x[i] = (active && i < d) ? (float)a.theta[i * P + p] - a.covshift[i] : 0.0f;
+    const size_t nt = (size_t)a.ntiles;
+#pragma unroll
+    for (int c = 0; c < kGroups; ++c) {
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int g = 16 * c + j;
+            if (g < kD) {
+                v[j] = x[g < kD ? g : 0];
+            } else if (g < kAcc) {
+                const int q = g - kD;
+                const int i = tri_row(q), k = q - tri_row(q) * (tri_row(q) + 1) / 2;
+                v[j] = x[i < kD ? i : 0] * x[k < kD ? k : 0];
+            } else {
+                v[j] = 0.0f;
+            }
+        }
+        // four halving levels leave lane l with entry (l >> 1) summed over
+        // 16 lanes; the last exchange adds the other half of the warp
+#pragma unroll
+        for (int o = 16, n = 16; o >= 2; o >>= 1, n >>= 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int j = 0; j < n / 2; ++j) {
+                const float keep = up ? v[j + n / 2] : v[j];
+                const float send = up ? v[j] : v[j + n / 2];
+                v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+        const int g = 16 * c + (lane >> 1);
+        if ((lane & 1) == 0 && g < kAcc) a.covtile[(size_t)g * nt + tile] = v[0];
+    }
+}
+
 // One block's tile of particles p0 + threadIdx.x: proposal, likelihood
 // recursion over the staged observations, Metropolis-Hastings decision.
 // Every thread of the block must call it (block barriers inside).  kIndep
@@ -231,6 +308,7 @@ __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, 
     // sampler (Section 3.3), written to the scratch rows.
     double thn[kMaxD];
     double zz = 0.0;
+    Real thr[kMaxD];   // the proposal in the working precision
     {
         Real z[kMaxD];
         proposal_normals<Real>(a.seed, (uint64_t)pp, iter, a.cycle, d, z);
@@ -243,14 +321,21 @@ __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, 
             } else {
                 thn[i] = a.theta[i * P + pp] + (double)s;
             }
+            thr[i] = (Real)thn[i];
             if (active) a.thp[i * P + p] = thn[i];
         }
     }
-    const double lp_new = log_prior(a.m, thn);
+    double lp_new;
     typename Pol::Model mdl;
     {
         Real full[kMaxD];
-        full_theta<Real>(a.m, thn, full);
+        if constexpr (sizeof(Real) == 4) {
+            lp_new = log_prior_f(a.m, thn, thr);
+            full_theta_f(a.m, thr, full);
+        } else {
+            lp_new = log_prior(a.m, thn);
+            full_theta<Real>(a.m, thn, full);
+        }
         Pol::setup(mdl, a.m, full);
     }
     const bool ok = Pol::run(mdl, pipe, a.T, a.W);
@@ -263,8 +348,7 @@ __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, 
         double log_alpha = tempered_target(lp_new, ll_new, a.phi) -
                            tempered_target(a.lp[p], a.ll[p], a.phi);
         if constexpr (kIndep) log_alpha += a.lq[p] + 0.5 * zz;
-        const double log_u = log_uniform_mh(a.seed, (uint64_t)p, iter, a.cycle);
-        acc = log_u < log_alpha;
+        acc = mh_accept(a.seed, (uint64_t)p, iter, a.cycle, log_alpha);
         if (acc) {
             for (int i = 0; i < d; ++i) a.theta[i * P + p] = a.thp[i * P + p];
             a.ll[p] = ll_new;
@@ -277,6 +361,7 @@ __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, 
         }
     }
     const unsigned int nacc = __popc(__ballot_sync(0xffffffffu, acc));
+    if (a.covtile) cov_tile_sums<Pol::kMaxFree>(a, p, active);
     if ((threadIdx.x & 31) == 0 && nacc) atomicAdd(&sm.acc_s, nacc);
     __syncthreads();
     if (threadIdx.x == 0 && sm.acc_s) atomicAdd(a.acc_count, (unsigned long long)sm.acc_s);
@@ -316,17 +401,19 @@ __device__ __forceinline__ void mutate_tile_x2(const MutateArgs& a, uint64_t ite
         act[h] = p < a.P;
         pq[h] = act[h] ? p : a.P - 1;
         double thn[kMaxD];
+        float thr[kMaxD];
         float z[kMaxD];
         proposal_normals<float>(a.seed, (uint64_t)pq[h], iter, a.cycle, d, z);
         for (int i = 0; i < d; ++i) {
             float s = 0;
             for (int k = 0; k <= i; ++k) s += sm.Ls[i * d + k] * z[k];
             thn[i] = a.theta[i * P + pq[h]] + (double)s;
+            thr[i] = (float)thn[i];
             if (act[h]) a.thp[i * P + p] = thn[i];
         }
-        lpn[h] = log_prior(a.m, thn);
+        lpn[h] = log_prior_f(a.m, thn, thr);
         float full[kMaxD];
-        full_theta<float>(a.m, thn, full);
+        full_theta_f(a.m, thr, full);
         Pol::setup(mdl[h], a.m, full);
     }
     const bool ok = run_egarch_f32_x2<K, I>(mdl[0], mdl[1], pipe, a.T);
@@ -341,7 +428,7 @@ __device__ __forceinline__ void mutate_tile_x2(const MutateArgs& a, uint64_t ite
         if (act[h]) {
             const double log_alpha = tempered_target(lpn[h], ll_new, a.phi) -
                                      tempered_target(a.lp[p], a.ll[p], a.phi);
-            acc = log_uniform_mh(a.seed, (uint64_t)p, iter, a.cycle) < log_alpha;
+            acc = mh_accept(a.seed, (uint64_t)p, iter, a.cycle, log_alpha);
             if (acc) {
                 for (int i = 0; i < d; ++i) a.theta[i * P + p] = a.thp[i * P + p];
                 a.ll[p] = ll_new;
@@ -354,6 +441,7 @@ __device__ __forceinline__ void mutate_tile_x2(const MutateArgs& a, uint64_t ite
             }
         }
         nacc += __popc(__ballot_sync(0xffffffffu, acc));
+        if (a.covtile) cov_tile_sums<Pol::kMaxFree>(a, p0 + h * (int)blockDim.x + (int)threadIdx.x, act[h]);
     }
     if ((threadIdx.x & 31) == 0 && nacc) atomicAdd(&sm.acc_s, nacc);
     __syncthreads();

@@ -219,8 +219,7 @@ __global__ void __launch_bounds__(kMalaThreads) k_mutate_mala(MalaArgs a)
             log_alpha = tempered_target(lp_new, ll_new, a.phi) - tempered_target(a.lp[p], a.ll[p], a.phi) -
                         0.5 * uu + 0.5 * (double)zz;
         }
-        const double log_u = log_uniform_mh(a.seed, (uint64_t)p, a.iter, a.cycle);
-        acc = log_u < log_alpha;
+        acc = mh_accept(a.seed, (uint64_t)p, a.iter, a.cycle, log_alpha);
         if (acc) {
             for (int i = 0; i < d; ++i) {
                 a.theta[i * P + p] = prop[i];

@@ -9,11 +9,12 @@
 // cudaMallocAsync.  The caller still passes theta and the outputs.
 //
 // The scratch is one file-scope __device__ array, so every process that loads
-// the library holds it on every device it uses until exit
-// (kNoAllocScratchBytes).  All calls on a device share it and it keeps the last
-// call's contents: each call writes every entry it later reads, so nothing
-// needs clearing, but two calls whose kernels overlap on the GPU (different
-// streams without ordering between them) race on it and must not be issued.
+// the library holds it on every device it uses until exit (about 1.1 MB).
+// All calls on a device share it and it keeps the last call's contents: each
+// call writes every partial sum it later reads, and the reduction's counter in
+// the last element returns to zero at the end of each call, so nothing needs
+// clearing; but two calls whose kernels overlap on the GPU (different streams
+// without ordering between them) race on it and must not be issued.
 #include "../../include/smc.h"
 #include "phase.cuh"
 
@@ -27,7 +28,9 @@ constexpr int kNoAllocCovBlocks = 256;
 constexpr int kNoAllocCovRow = kMaxD + kMaxD * (kMaxD + 1) / 2;
 constexpr size_t kNoAllocScratchDoubles = (size_t)(kNoAllocCovBlocks + 1) * kNoAllocCovRow;
 
-static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+// The element after the partial sums holds the reduction's counter (zero
+// while no call runs: device memory starts zeroed and each call resets it).
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles + 1];
 
 namespace {
 
@@ -68,7 +71,8 @@ extern "C" smc_status smc_cov_chol_noalloc(const double* theta, int d, int P, in
     if (scratch_on_current_device(&scratch) != cudaSuccess) return SMC_ECUDA;
     int G = cov_grid(P);
     if (G > kNoAllocCovBlocks) G = kNoAllocCovBlocks;
-    const cudaError_t e = launch_cov(theta, d, P, scratch, G, nullptr, h_tenths, 0.0, 1, 10, mean,
+    unsigned int* counter = reinterpret_cast<unsigned int*>(scratch + kNoAllocScratchDoubles);
+    const cudaError_t e = launch_cov(theta, d, P, scratch, G, counter, nullptr, h_tenths, 0.0, 1, 10, mean,
                                      cov, L, (cudaStream_t)stream);
     return e == cudaSuccess ? SMC_OK : SMC_ECUDA;
 }

@@ -121,38 +121,28 @@ __global__ void k_adapt_h(Ctl* ctl, int P, double target, int hmin, int hmax)
     if (threadIdx.x == 0 && blockIdx.x == 0) apply_h_update(ctl, P, target, hmin, hmax);
 }
 
-// Sum of the G block partials of each accumulator entry: one block per entry,
-// fixed combination order.  Result in part[G * nacc + e].
-__device__ void cov_combine_body(double* part, int G, int nacc, int e)
-{
-    __shared__ double red[32];
-    double s = 0.0;
-    for (int g = threadIdx.x; g < G; g += blockDim.x) s += part[(size_t)g * nacc + e];
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) part[(size_t)G * nacc + e] = s;
-}
 
-__global__ void __launch_bounds__(128) k_cov_combine(double* part, int G, int nacc)
-{
-    cov_combine_body(part, G, nacc, blockIdx.x);
-}
 
-// Combines the partial sums, updates h from the previous iteration's
-// acceptance (when a control block is given; a positive fixed_h still scales
-// Sigma in place of the adapted h) and factors Sigma = h^2 V by a
-// right-looking Cholesky in shared memory; a non-positive pivot zeroes its
-// column, as in the oracle.
-__device__ void cov_final_body(const double* __restrict__ part, int G, int d, int P,
-                               const double* __restrict__ theta, Ctl* ctl, int fixed_h, double target,
-                               int hmin, int hmax, double* mean_out, double* cov_out, double* L_out)
+// Final step of the covariance (one block): updates h from the previous
+// iteration's acceptance (when a control block is given; a positive fixed_h
+// still scales Sigma in place of the adapted h), forms V from the totals of
+// the shifted sums and factors Sigma = h^2 V by a right-looking Cholesky in
+// shared memory, done by the first warp (lane i owns row i, d <= 32); a
+// non-positive pivot zeroes its column, as in the oracle.
+// The shift of the sums is shift_f[i] (FP32, the mutation tiles) when given,
+// else shift_in[i * shift_stride]; the pooled mean goes to mean_out (FP64)
+// and, rounded, to mean_f_out (the next tiles' shift; may be shift_f).
+__device__ void cov_final_body(const double* __restrict__ tot, int d, int P,
+                               const double* __restrict__ shift_in, size_t shift_stride,
+                               const float* shift_f, Ctl* ctl, int fixed_h, double target, int hmin,
+                               int hmax, double* mean_out, float* mean_f_out, double* cov_out,
+                               double* L_out)
 {
     __shared__ double S1[kMaxD];
     __shared__ double A[kMaxD][kMaxD + 1];
     __shared__ double shift[kMaxD];
-    __shared__ double hh;
+    __shared__ double hh, invP, invP1;
     const int npair = d * (d + 1) / 2;
-    const int nacc = d + npair;
-    const size_t Ps = (size_t)P;
     if (threadIdx.x == 0) {
         int h = fixed_h;
         if (ctl) {
@@ -160,45 +150,70 @@ __device__ void cov_final_body(const double* __restrict__ part, int G, int d, in
             if (fixed_h <= 0) h = ctl->h_tenths;   // fixed_h > 0 overrides the adapted step size
         }
         hh = (h / 10.0) * (h / 10.0);
+        invP = 1.0 / (double)P;
+        invP1 = 1.0 / (double)(P - 1);
     }
-    for (int i = threadIdx.x; i < d; i += blockDim.x) shift[i] = theta[i * Ps];
-    const double* tot = part + (size_t)G * nacc;
-    for (int e = threadIdx.x; e < d; e += blockDim.x) S1[e] = tot[e];
+    for (int i = threadIdx.x; i < d; i += blockDim.x)
+        shift[i] = shift_f ? (double)shift_f[i] : shift_in[i * shift_stride];
+    for (int e = threadIdx.x; e < d; e += blockDim.x) S1[e] = __ldcg(tot + e);
     __syncthreads();
     for (int e = threadIdx.x; e < npair; e += blockDim.x) {
         int i, k;
         unpack_pair(e, i, k);
-        const double s = tot[d + e];
-        const double c = (s - S1[i] * S1[k] / (double)P) / (double)(P - 1);
+        const double c = (__ldcg(tot + d + e) - S1[i] * S1[k] * invP) * invP1;
         A[i][k] = c;
         A[k][i] = c;
     }
     __syncthreads();
-    if (mean_out)
-        for (int i = threadIdx.x; i < d; i += blockDim.x) mean_out[i] = shift[i] + S1[i] / (double)P;
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {   // the shifts are in shared memory already
+        const double mu = shift[i] + S1[i] * invP;
+        if (mean_out) mean_out[i] = mu;
+        if (mean_f_out) mean_f_out[i] = (float)mu;
+    }
     if (cov_out)
         for (int e = threadIdx.x; e < d * d; e += blockDim.x) cov_out[e] = A[e / d][e % d];
-    for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
-        const int i = e / d, k = e % d;
-        if (k <= i) A[i][k] *= hh;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // FP64 instructions have a long dependent latency on this part, so the
+        // pivot's square root and reciprocal come from an FP32 reciprocal
+        // square root refined by two Newton steps in FP64 (each doubles the
+        // correct bits: 24 -> 48 -> full precision), and the trailing update
+        // spreads its elements over the lanes.
+        const int lane = threadIdx.x;
+        const int nel = d * (d + 1) / 2;
+        for (int e = lane; e < nel; e += 32) {
+            int i, k;
+            unpack_pair(e, i, k);
+            A[i][k] *= hh;
+        }
+        __syncwarp();
+        for (int j = 0; j < d; ++j) {
+            const double piv = A[j][j];
+            double inv = 0.0, ljj = 0.0;
+            if (piv > 0.0) {
+                double y = (double)rsqrtf((float)piv);
+                if (!(y > 0.0 && y < INFINITY)) y = rsqrt(piv);   // pivot outside the FP32 range
+                y = fma(0.5 * y, fma(-piv * y, y, 1.0), y);
+                y = fma(0.5 * y, fma(-piv * y, y, 1.0), y);
+                inv = y;
+                ljj = piv * y;
+            }
+            __syncwarp();
+            if (lane == j) A[j][j] = ljj;
+            if (lane > j && lane < d) A[lane][j] *= inv;
+            __syncwarp();
+            const int m = d - j - 1;
+            for (int e = lane; e < m * (m + 1) / 2; e += 32) {
+                int ii, kk;
+                unpack_pair(e, ii, kk);
+                ii += j + 1;
+                kk += j + 1;
+                A[ii][kk] = fma(-A[ii][j], A[kk][j], A[ii][kk]);
+            }
+            __syncwarp();
+        }
     }
     __syncthreads();
-    for (int j = 0; j < d; ++j) {
-        if (threadIdx.x == 0) A[j][j] = A[j][j] > 0.0 ? sqrt(A[j][j]) : 0.0;
-        __syncthreads();
-        const double ljj = A[j][j];
-        for (int i = j + 1 + threadIdx.x; i < d; i += blockDim.x) A[i][j] = ljj > 0.0 ? A[i][j] / ljj : 0.0;
-        __syncthreads();
-        const int m = d - j - 1;
-        for (int e = threadIdx.x; e < m * (m + 1) / 2; e += blockDim.x) {
-            int ii, kk;
-            unpack_pair(e, ii, kk);
-            ii += j + 1;
-            kk += j + 1;
-            A[ii][kk] = fma(-A[ii][j], A[kk][j], A[ii][kk]);
-        }
-        __syncthreads();
-    }
     if (L_out)
         for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
             const int i = e / d, k = e % d;
@@ -206,61 +221,136 @@ __device__ void cov_final_body(const double* __restrict__ part, int G, int d, in
         }
 }
 
-__global__ void __launch_bounds__(kCovThreads) k_cov_final(const double* __restrict__ part, int G, int d,
-                                                          int P, const double* __restrict__ theta,
-                                                          Ctl* ctl, int fixed_h, double target,
-                                                          int hmin, int hmax, double* mean_out,
-                                                          double* cov_out, double* L_out)
+// Totals of the partial sums (one block per entry, fixed order), then the
+// final step in the last block to finish (the counter returns to zero for the
+// next launch).  Partials: kTiles, FP32 tile sums [nacc][nparts]; otherwise
+// FP64 block sums [nparts][nacc].
+struct CovFinalArgs {
+    int d, P;
+    const double* shift_in;
+    long long shift_stride;
+    const float* shift_f;
+    Ctl* ctl;
+    int fixed_h;
+    double target;
+    int hmin, hmax;
+    double* mean_out;
+    float* mean_f_out;
+    double *cov_out, *L_out;
+    int tile_kd;   // tile layout bound (tiles only)
+};
+
+// Total of entry e over the partials, kCovThreads threads in a fixed order
+// (the single-run and batched paths share it, so their sums agree bitwise).
+// For tiles, entry e of the d-layout is row e (e < d) or e - d + kD of the
+// tiles' kD-layout.
+template <bool kTiles>
+__device__ __forceinline__ double cov_entry_total(const void* __restrict__ parts, int nparts, int nacc, int e,
+                                                  int d, int kD, double* red)
 {
-    cov_final_body(part, G, d, P, theta, ctl, fixed_h, target, hmin, hmax, mean_out, cov_out, L_out);
+    double s = 0.0;
+    if constexpr (kTiles) {
+        const int r = e < d ? e : e - d + kD;
+        const float* row = static_cast<const float*>(parts) + (size_t)r * nparts;
+        for (int t = threadIdx.x; t < nparts; t += blockDim.x) s += (double)row[t];
+    } else {
+        const double* pp = static_cast<const double*>(parts);
+        for (int g = threadIdx.x; g < nparts; g += blockDim.x) s += pp[(size_t)g * nacc + e];
+    }
+    return block_sum(s, red);
 }
 
+template <bool kTiles>
+__global__ void __launch_bounds__(kCovThreads) k_cov_reduce(const void* __restrict__ parts, int nparts,
+                                                            int nacc, double* tot, unsigned int* counter,
+                                                            CovFinalArgs f)
+{
+    __shared__ double red[32];
+    __shared__ int last;
+    const int e = blockIdx.x;
+    const double s = cov_entry_total<kTiles>(parts, nparts, nacc, e, f.d, f.tile_kd, red);
+    if (threadIdx.x == 0) {
+        tot[e] = s;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) *counter = 0u;
+    cov_final_body(tot, f.d, f.P, f.shift_in, (size_t)f.shift_stride, f.shift_f, f.ctl, f.fixed_h, f.target,
+                   f.hmin, f.hmax, f.mean_out, f.mean_f_out, f.cov_out, f.L_out);
+}
+
+
 // ----- batched covariance: one launch per stage for many particle sets -----
+// Iteration 0 of a cycle takes block partials of theta; later iterations take
+// the tile sums the mutation kernel left (when the job has them), exactly as
+// the single-run path does.
 __global__ void __launch_bounds__(kCovThreads) k_cov_partial_batch(const CovJob* __restrict__ jobs,
                                                                   const int* iter)
 {
     const CovJob& j = jobs[blockIdx.y];
-    if ((int)blockIdx.x >= j.G || *iter >= j.R) return;
+    if ((int)blockIdx.x >= j.G || *iter >= j.R || (*iter > 0 && j.tiles)) return;
     cov_partial_body(j.theta, j.d, j.P, j.part, blockIdx.x, j.G);
 }
 
-__global__ void __launch_bounds__(128) k_cov_combine_batch(const CovJob* __restrict__ jobs, const int* iter)
+__global__ void __launch_bounds__(kCovThreads) k_cov_combine_batch(const CovJob* __restrict__ jobs, const int* iter)
 {
+    __shared__ double red[32];
     const CovJob& j = jobs[blockIdx.y];
     const int nacc = j.d + j.d * (j.d + 1) / 2;
-    if ((int)blockIdx.x >= nacc || *iter >= j.R) return;
-    cov_combine_body(j.part, j.G, nacc, blockIdx.x);
+    const int e = blockIdx.x;
+    if (e >= nacc || *iter >= j.R) return;
+    const double s = (*iter > 0 && j.tiles) ? cov_entry_total<true>(j.tiles, j.ntiles, nacc, e, j.d, j.tile_kd, red)
+                                            : cov_entry_total<false>(j.part, j.G, nacc, e, j.d, 0, red);
+    if (threadIdx.x == 0) j.part[(size_t)j.G * nacc + e] = s;
 }
 
 __global__ void __launch_bounds__(kCovThreads) k_cov_final_batch(const CovJob* __restrict__ jobs, const int* iter)
 {
     const CovJob& j = jobs[blockIdx.x];
     if (*iter >= j.R) return;
-    cov_final_body(j.part, j.G, j.d, j.P, j.theta, j.ctl, 0, j.target, j.hmin, j.hmax, nullptr, nullptr, j.L);
+    const int nacc = j.d + j.d * (j.d + 1) / 2;
+    const bool tiles = *iter > 0 && j.tiles;
+    cov_final_body(j.part + (size_t)j.G * nacc, j.d, j.P, j.theta, (size_t)j.P, tiles ? j.shift_f : nullptr,
+                   j.ctl, 0, j.target, j.hmin, j.hmax, j.mean, j.shift_f, nullptr, j.L);
 }
 
 cudaError_t launch_cov_batch(const CovJob* jobs, int n, int Gmax, int dmax, const int* iter, cudaStream_t s)
 {
     k_cov_partial_batch<<<dim3(Gmax, n), kCovThreads, 0, s>>>(jobs, iter);
     count_launch();
-    k_cov_combine_batch<<<dim3(dmax + dmax * (dmax + 1) / 2, n), 128, 0, s>>>(jobs, iter);
+    k_cov_combine_batch<<<dim3(dmax + dmax * (dmax + 1) / 2, n), kCovThreads, 0, s>>>(jobs, iter);
     count_launch();
     k_cov_final_batch<<<n, kCovThreads, 0, s>>>(jobs, iter);
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_cov(const double* theta, int d, int P, double* part, int G, Ctl* ctl,
-                       int fixed_h_tenths, double acc_target, int hmin, int hmax, double* mean,
-                       double* cov, double* L, cudaStream_t s)
+cudaError_t launch_cov(const double* theta, int d, int P, double* part, int G, unsigned int* counter,
+                       Ctl* ctl, int fixed_h_tenths, double acc_target, int hmin, int hmax, double* mean,
+                       double* cov, double* L, cudaStream_t s, float* mean_f)
 {
     k_cov_partial<<<G, kCovThreads, 0, s>>>(theta, d, P, part);
     count_launch();
     const int nacc = d + d * (d + 1) / 2;
-    k_cov_combine<<<nacc, 128, 0, s>>>(part, G, nacc);
+    const CovFinalArgs f{d, P, theta, (long long)P, nullptr, ctl, fixed_h_tenths, acc_target, hmin, hmax,
+                         mean, mean_f, cov, L, 0};
+    k_cov_reduce<false><<<nacc, kCovThreads, 0, s>>>(part, G, nacc, part + (size_t)G * nacc, counter, f);
     count_launch();
-    k_cov_final<<<1, kCovThreads, 0, s>>>(part, G, d, P, theta, ctl, fixed_h_tenths, acc_target,
-                                          hmin, hmax, mean, cov, L);
+    return cudaGetLastError();
+}
+
+// ----- covariance from the mutation kernel's 32-particle tiles -----
+cudaError_t launch_cov_tiles(const float* tiles, int ntiles, int tile_kd, int d, int P, double* tot,
+                             unsigned int* counter, float* shift_f, double* mean, Ctl* ctl, int fixed_h_tenths,
+                             double acc_target, int hmin, int hmax, double* L, cudaStream_t s)
+{
+    const int nacc = d + d * (d + 1) / 2;
+    const CovFinalArgs f{d, P, nullptr, 1, shift_f, ctl, fixed_h_tenths, acc_target, hmin, hmax, mean,
+                         shift_f, nullptr, L, tile_kd};
+    k_cov_reduce<true><<<nacc, kCovThreads, 0, s>>>(tiles, ntiles, nacc, tot, counter, f);
     count_launch();
     return cudaGetLastError();
 }
@@ -358,20 +448,27 @@ __global__ void k_search_init(const double* part, int G, Ctl* ctl)
 
 __device__ __forceinline__ double candidate(double lo, double hi, int c)
 {
-    return c == kCand - 1 ? hi : lo + (hi - lo) * (double)(c + 1) / (double)kCand;
+    // (c + 1) / kCand as a product with the exact power-of-two reciprocal
+    return c == kCand - 1 ? hi : lo + (hi - lo) * ((double)(c + 1) * (1.0 / kCand));
 }
 
+// One pass: each block sums, per candidate (one per lane), w and w^2 over its
+// particles into part; the last block to finish (ctl->search_blocks counts
+// them and returns to zero) totals the blocks in FP64 and narrows the bracket
+// to the first candidate whose pooled RSS is below D1.
 __global__ void __launch_bounds__(kSearchThreads) k_power_pass(const double* __restrict__ ll, int P,
-                                                              const Ctl* ctl, double* part)
+                                                              Ctl* ctl, double* part, double d1, int passes)
 {
     if (ctl->done) return;
     __shared__ double s1w[kSearchThreads / 32][kCand], s2w[kSearchThreads / 32][kCand];
+    __shared__ int last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwb = blockDim.x >> 5;
     const double llmax = ctl->llmax;
     const float dc = (float)(candidate(ctl->lo, ctl->hi, lane) * kLog2e);
     double s1 = 0.0, s2 = 0.0;
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+    const int nw = gridDim.x * nwb;
+    const int gw = blockIdx.x * nwb + warp;
     for (int base = gw * 32; base < P; base += nw * 32) {
         const int n = base + lane;
         const float x = n < P ? (float)(ll[n] - llmax) : -INFINITY;
@@ -391,40 +488,43 @@ __global__ void __launch_bounds__(kSearchThreads) k_power_pass(const double* __r
     __syncthreads();
     if (warp == 0) {
         double t1 = 0.0, t2 = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        for (int w = 0; w < nwb; ++w) {
             t1 += s1w[w][lane];
             t2 += s2w[w][lane];
         }
         part[((size_t)blockIdx.x * kCand + lane) * 2 + 0] = t1;
         part[((size_t)blockIdx.x * kCand + lane) * 2 + 1] = t2;
+        __threadfence();
+        unsigned int prev = 0;
+        if (lane == 0) prev = atomicAdd(&ctl->search_blocks, 1u);
+        prev = __shfl_sync(0xffffffffu, prev, 0);
+        if (lane == 0) last = prev == gridDim.x - 1;
     }
-}
-
-__global__ void __launch_bounds__(1024) k_power_select(const double* part, int G, int P, double d1,
-                                                      int passes, Ctl* ctl)
-{
-    if (ctl->done) return;
-    __shared__ double r1[32][kCand + 1], r2[32][kCand + 1];
-    const int c = threadIdx.x & 31, w = threadIdx.x >> 5;
-    double t1 = 0.0, t2 = 0.0;
-    for (int g = w; g < G; g += 32) {
-        t1 += part[((size_t)g * kCand + c) * 2 + 0];
-        t2 += part[((size_t)g * kCand + c) * 2 + 1];
-    }
-    r1[w][c] = t1;
-    r2[w][c] = t2;
     __syncthreads();
-    if (w != 0) return;
-    t1 = 0.0;
-    t2 = 0.0;
-    for (int k = 0; k < 32; ++k) {
-        t1 += r1[k][c];
-        t2 += r2[k][c];
+    if (!last) return;
+    __threadfence();
+    // ---- select (last block): totals per candidate, warps over block rows ----
+    {
+        double t1 = 0.0, t2 = 0.0;
+        for (int g = warp; g < (int)gridDim.x; g += nwb) {
+            t1 += __ldcg(part + ((size_t)g * kCand + lane) * 2 + 0);
+            t2 += __ldcg(part + ((size_t)g * kCand + lane) * 2 + 1);
+        }
+        __syncthreads();
+        s1w[warp][lane] = t1;
+        s2w[warp][lane] = t2;
     }
-    const int lane = c;
+    __syncthreads();
+    if (warp != 0) return;
+    double t1 = 0.0, t2 = 0.0;
+    for (int w = 0; w < nwb; ++w) {
+        t1 += s1w[w][lane];
+        t2 += s2w[w][lane];
+    }
     const double rss = t1 * t1 / ((double)P * t2);
     const unsigned below = __ballot_sync(0xffffffffu, rss < d1);
     if (lane == 0) {
+        ctl->search_blocks = 0u;
         const double lo = ctl->lo, hi = ctl->hi;
         if (below == 0u) {
             // RSS stays >= D1 up to hi: in the first pass this takes the whole
@@ -474,9 +574,7 @@ cudaError_t launch_power_search(const double* ll, int P, double d1, int passes, 
     k_search_init<<<1, 32, 0, s>>>(mx, G, ctl);
     count_launch();
     for (int p = 0; p < passes; ++p) {
-        k_power_pass<<<G, kSearchThreads, 0, s>>>(ll, P, ctl, part);
-        count_launch();
-        k_power_select<<<1, 1024, 0, s>>>(part, G, P, d1, passes, ctl);
+        k_power_pass<<<G, kSearchThreads, 0, s>>>(ll, P, ctl, part, d1, passes);
         count_launch();
     }
     return cudaGetLastError();

@@ -18,6 +18,7 @@ struct Ctl {
     // C phase, power tempering: k-ary search state.
     double llmax, lo, hi, dphi, rss, phi;
     int pass, done, last;
+    unsigned int search_blocks;     // blocks of the current pass that have finished (reset by the last)
     // C phase, data tempering: observations to absorb from the current chunk,
     // whether the chunk contains the stopping observation, and whether the
     // stop was forced (date of interest or T with RSS >= D1).
@@ -32,12 +33,21 @@ struct Ctl {
 // ---- launchers (phase.cu) ----
 int device_sm_count();
 
-// Covariance: partial sums per block, then a single block that combines them,
-// applies the pending step-size update and factors h^2 V.
+// Covariance: partial sums per block (part: [G + 1][nacc] doubles, the last
+// row receiving the totals), then one block per total whose last finisher
+// applies the pending step-size update and factors h^2 V.  counter: a device
+// word that is zero before the call and zero again after it.
 int cov_grid(int P);
-cudaError_t launch_cov(const double* theta, int d, int P, double* part, int G, Ctl* ctl,
-                       int fixed_h_tenths, double acc_target, int hmin, int hmax, double* mean,
-                       double* cov, double* L, cudaStream_t s);
+cudaError_t launch_cov(const double* theta, int d, int P, double* part, int G, unsigned int* counter,
+                       Ctl* ctl, int fixed_h_tenths, double acc_target, int hmin, int hmax, double* mean,
+                       double* cov, double* L, cudaStream_t s, float* mean_f = nullptr);
+// From the mutation kernel's 32-particle tile sums (entry-major
+// [kD + kD(kD+1)/2][ntiles], values shifted by shift_f): combine in FP64, then
+// the same final step; the pooled mean goes to mean (FP64) and, rounded, back
+// into shift_f (the next tiles' shift).
+cudaError_t launch_cov_tiles(const float* tiles, int ntiles, int tile_kd, int d, int P, double* tot,
+                             unsigned int* counter, float* shift_f, double* mean, Ctl* ctl, int fixed_h_tenths,
+                             double acc_target, int hmin, int hmax, double* L, cudaStream_t s);
 // Batched form: one covariance job per particle set, skipped once the
 // device iteration counter reaches the job's iteration count R.
 struct CovJob {
@@ -50,6 +60,10 @@ struct CovJob {
     double target;
     int hmin, hmax;
     int R;
+    const float* tiles;   // mutation tile sums [kD + kD(kD+1)/2][ntiles] (nullable)
+    int ntiles, tile_kd;
+    float* shift_f;       // [d] the tiles' shift: the pooled mean rounded, rewritten by each final step
+    double* mean;         // [d] pooled mean
 };
 cudaError_t launch_cov_batch(const CovJob* jobs, int n, int Gmax, int dmax, const int* iter, cudaStream_t s);
 

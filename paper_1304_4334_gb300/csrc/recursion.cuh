@@ -47,6 +47,8 @@ struct ModelDev {
     double prior_isd[kMaxD];   // 1 / prior s.d.
     double prior_c[kMaxD];     // -1/2 log 2pi - log prior s.d.
     double prior_lo[kMaxD];
+    // the same prior constants rounded to FP32 (FP32 log prior)
+    float prior_mean_f[kMaxD], prior_isd_f[kMaxD], prior_c_f[kMaxD], prior_lo_f[kMaxD];
 };
 
 // Full parameter vector from a particle's free parameters.
@@ -59,6 +61,34 @@ __device__ __forceinline__ void full_theta(const ModelDev& m, const double* th, 
     }
     for (int i = 0; i < m.d_full; ++i) full[i] = (Real)m.theta_fixed[i];
     for (int k = 0; k < m.d; ++k) full[m.free_idx[k]] = (Real)th[k];
+}
+
+// Full parameter vector from FP32 free parameters.
+__device__ __forceinline__ void full_theta_f(const ModelDev& m, const float* th, float* full)
+{
+    if (!m.has_free) {
+        for (int i = 0; i < m.d_full; ++i) full[i] = th[i];
+        return;
+    }
+    for (int i = 0; i < m.d_full; ++i) full[i] = (float)m.theta_fixed[i];
+    for (int k = 0; k < m.d; ++k) full[m.free_idx[k]] = th[k];
+}
+
+// The log prior in FP32 arithmetic on thf = (float)th (the FP32 path, whose
+// likelihood carries FP32 error far above it).  The support test is exact:
+// rounding is monotone, so thf > (float)lo implies th >= lo, and otherwise th
+// itself is compared in FP64.
+__device__ __forceinline__ double log_prior_f(const ModelDev& m, const double* th, const float* thf)
+{
+    float lp = 0.0f;
+    for (int k = 0; k < m.d; ++k) {
+        const float x = thf[k];
+        if (!(x > m.prior_lo_f[k]) && !(th[k] >= m.prior_lo[k])) return -INFINITY;
+        if (!isfinite(x)) return -INFINITY;
+        const float z = (x - m.prior_mean_f[k]) * m.prior_isd_f[k];
+        lp += m.prior_c_f[k] - 0.5f * z * z;
+    }
+    return (double)lp;
 }
 
 // Log prior density kernel (Gaussian per free parameter, truncated below).

@@ -37,6 +37,10 @@ void model_dev(const smc_model& m, ModelDev& d)
         d.prior_isd[i] = 1.0 / sd;
         d.prior_c[i] = -0.5 * kLog2Pi - std::log(sd);
         d.prior_lo[i] = m.prior_lo[i];
+        d.prior_mean_f[i] = (float)d.prior_mean[i];
+        d.prior_isd_f[i] = (float)d.prior_isd[i];
+        d.prior_c_f[i] = (float)d.prior_c[i];
+        d.prior_lo_f[i] = (float)d.prior_lo[i];
     }
 }
 
@@ -125,6 +129,9 @@ static smc_status mutate_impl(const smc_model* m, int precision, const void* obs
     a.L = L;
     a.qmean = qmean;
     a.lq = lq;
+    a.covtile = nullptr;
+    a.covshift = nullptr;
+    a.ntiles = 0;
     a.phi = phi;
     a.seed = seed;
     a.cycle = cycle;
@@ -243,8 +250,11 @@ smc_status smc_cov_chol(const double* theta, int d, int P, int h_tenths, double*
     cudaStream_t s = (cudaStream_t)stream;
     const int G = cov_grid(P);
     double* part = nullptr;
-    CK(cudaMallocAsync((void**)&part, (size_t)(G + 1) * (d + d * (d + 1) / 2) * sizeof(double), s));
-    cudaError_t e = launch_cov(theta, d, P, part, G, nullptr, h_tenths, 0.0, 1, 10, mean, cov, L, s);
+    const size_t n = (size_t)(G + 1) * (d + d * (d + 1) / 2);
+    CK(cudaMallocAsync((void**)&part, (n + 1) * sizeof(double), s));
+    unsigned int* counter = reinterpret_cast<unsigned int*>(part + n);
+    CK(cudaMemsetAsync(counter, 0, sizeof(unsigned int), s));
+    cudaError_t e = launch_cov(theta, d, P, part, G, counter, nullptr, h_tenths, 0.0, 1, 10, mean, cov, L, s);
     cudaFreeAsync(part, s);
     return from_cuda(e);
 }
