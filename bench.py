@@ -38,9 +38,7 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT_GB300 = 152
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per k_mutate launch, by
 # (workload, particles per thread, threads per block)
-MUTATE_TRAFFIC = {("egarch22_T5000", 1, 128): 8_751_872 + 55_296,
-                  ("egarch22_T5000", 1, 64): 8_746_496 + 80_896,
-                  ("egarch22_T5000", 1, 32): 8_752_128 + 73_984}
+MUTATE_TRAFFIC = {("egarch22_T5000", 2, 64): 8_684_288 + 33_280}
 SM_MAX_MHZ_FALLBACK = 2070.0
 L2_FLUSH_BYTES = 256 << 20
 
@@ -72,14 +70,19 @@ def alu_ops_per_eval(K, I, gamma):
     return fp32, mufu
 
 
-def alu_peak_evals(K, I, gamma, sms, mhz):
-    """Evaluations/s bound: issue (4 x 32 lanes/clk/SM, every instruction) and
-    SFU (16 lanes/clk/SM) limits at the given SM clock."""
+def alu_peak_evals(K, I, gamma, sms, mhz, paired=False):
+    """Evaluations/s bound at the given SM clock from the FP32 pipe (128
+    lanes/clk/SM), the SFU (32 lanes/clk/SM for ex2/lg2 on this part: the
+    profiled kernels' XU-pipe share against their known SFU rate) and
+    instruction issue (4 x 32 lanes/clk/SM, each instruction once).  With
+    paired FP32 instructions (two particles per thread) an FP32 instruction
+    carries two lanes' work, so issue counts fp32/2 + mufu per evaluation while
+    the FP32 pipe still bounds fp32."""
     fp32, mufu = alu_ops_per_eval(K, I, gamma)
-    issue = 128.0 / (fp32 + mufu)
-    sfu = 16.0 / mufu
-    bound = min(issue, sfu)
-    return sms * mhz * 1e6 * bound, ("issue" if issue <= sfu else "mufu")
+    limits = {"issue": 128.0 / ((fp32 / 2.0 if paired else fp32) + mufu),
+              "fp32": 128.0 / fp32, "mufu": 32.0 / mufu}
+    pipe = min(limits, key=limits.get)
+    return sms * mhz * 1e6 * limits[pipe], pipe
 
 
 def sm_max_mhz():
@@ -371,11 +374,12 @@ def main():
 
     # ---- roofline of the dominant kernel (fused RW mutate) ----
     # DRAM bytes (read + write) of one mutate launch from an ncu capture of the
-    # same kernel, workload and launch shape (profiles/k_mutate_egarch22_T5000.md);
+    # same kernel, workload and launch shape (profiles/k_mutate_x2_egarch22_T5000.md);
     # None where no capture of the current kernel exists.
     traffic = MUTATE_TRAFFIC.get((args.workload, shape[0], shape[1])) if not mala else None
     mhz, src = sm_max_mhz()
-    peak, pipe = alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, mhz)
+    paired = shape[0] == 2
+    peak, pipe = alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, mhz, paired)
     avg_launch_s = (mut_ms / mut_n) / 1e3 if mut_n else float("nan")
     achieved = w.P * w.T / avg_launch_s if mut_n else float("nan")
     fp32_ops, mufu_ops = alu_ops_per_eval(w.K, w.I, w.gamma)
@@ -385,12 +389,14 @@ def main():
             "frac": achieved / peak, "traffic": traffic, "pipe": pipe, "peak_source": f"{src} SM clock {mhz:.0f} MHz x {SM_COUNT_GB300} SMs",
             "ops_per_eval": {"fp32": fp32_ops, "mufu": mufu_ops},
             "kernel": (f"k_mutate_mala<GradEgarch<float,{w.K},{w.I}>>" if mala
+                       else f"k_mutate_x2<{w.K},{w.I}>" if paired
                        else f"k_mutate<PolicyEgarchF32<{w.K},{w.I}>>"), "avg_launch_ms": avg_launch_s * 1e3,
             "launches": mut_n, "share_of_step": (mut_ms / 1e3) / t_total if t_total else None,
             "launch_shape": {"particles_per_thread": shape[0], "threads_per_block": shape[1],
                              "autotune_ms_per_iteration": shape[2]}}
     if clk.get("sm_mhz"):
-        roof["frac_at_median_clock"] = achieved / alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, clk["sm_mhz"])[0]
+        roof["frac_at_median_clock"] = achieved / alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, clk["sm_mhz"],
+                                                                 paired)[0]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
