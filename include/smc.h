@@ -255,6 +255,16 @@ smc_status smc_log_score(smc_ctx* ctx, double* log_score, double* nse);
  * are NaN.  Synchronises. */
 smc_status smc_pit(smc_ctx* ctx, double* out, int T);
 
+/* Failure-detection self-test: one block runs the library's bounded mbarrier
+ * wait (the one guarding every staged-observation copy) with a limit of
+ * limit_ns (0 < limit_ns <= 2 s) on a barrier that is completed only when
+ * `complete` is nonzero.  Returns SMC_ETIMEOUT when the wait ran out (the
+ * kernel then returns normally and the context stays usable), SMC_OK when it
+ * completed, SMC_EINVAL for a bad limit.  Synchronises the stream.  The paper
+ * has no counterpart; it exists so that the timeout path can be exercised
+ * without faulting or hanging the device. */
+smc_status smc_wait_selftest(uint64_t limit_ns, int complete, void* stream);
+
 /* Number of kernel launches this library has issued in this process. */
 uint64_t smc_launch_count(void);
 

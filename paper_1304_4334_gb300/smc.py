@@ -85,6 +85,7 @@ def _declare(L):
     L.smc_run.argtypes = [vp, C.c_int, P(smc_cycle_info), P(C.c_int)]
     L.smc_log_ml.argtypes = [vp, dp, dp, dp]
     L.smc_log_score.argtypes = [vp, dp, dp]
+    L.smc_wait_selftest.argtypes = [C.c_uint64, C.c_int, vp]
     L.smc_pit.argtypes = [vp, dp, C.c_int]
     L.smc_moments.argtypes = [vp, dp, P(C.c_int)]
     L.smc_get_particles.argtypes = [vp, dp, dp, dp, dp]
@@ -490,6 +491,11 @@ def mutate_rw(model, precision, obs, theta, ll, lp, state, L, phi, seed, cycle, 
                                _ptr(lp), _ptr(state), P, _ptr(L), float(phi), seed, cycle, it,
                                C.byref(acc), _stream(stream)))
     return acc.value
+
+
+def wait_selftest(limit_ns, complete, stream=None):
+    """Status of the bounded-wait self-test (ETIMEOUT when the wait ran out)."""
+    return lib().smc_wait_selftest(int(limit_ns), int(bool(complete)), _stream(stream))
 
 
 def mutate_indep(model, precision, obs, theta, ll, lp, state, mean, L, phi, seed, cycle, it, stream=None):

@@ -422,3 +422,24 @@ def test_group_moments_and_ml_match_oracle(S):
     x, s = S.ml_from_groups(dev(a))
     xo, so = O.log_ml(a)
     assert x == pytest.approx(xo, rel=1e-14) and s == pytest.approx(so, rel=1e-10)
+
+
+def test_bounded_wait_times_out_and_the_context_survives(S):
+    """Failure detection without a fault: the library's bounded mbarrier wait
+    on a barrier nothing completes returns SMC_ETIMEOUT after its limit, the
+    same wait on a completed barrier returns OK, and device work still runs
+    afterwards."""
+    import time
+    torch = torch_cuda()
+    t0 = time.perf_counter()
+    assert S.wait_selftest(20_000_000, False) == S.ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert S.wait_selftest(20_000_000, True) == S.OK
+    K, I_, T, P = 1, 1, 64, 40
+    truth = egarch_truth(K, I_)
+    y = I.simulate_egarch(truth, T, seed=3)
+    spec = O.ModelSpec(K=K, I=I_, gamma=True)
+    th = particles(spec.d, truth, K, I_, True, P, 4)
+    ll = torch.empty(P, dtype=torch.float64, device="cuda")
+    S.loglik(S.model_egarch(K, I_, True), S.FP64, dev(y), soa(th), ll)
+    np.testing.assert_allclose(host(ll), O.loglik(spec, y, th), rtol=1e-9)

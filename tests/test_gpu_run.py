@@ -393,3 +393,27 @@ def test_log_score_and_pit_need_data_tempering(S):
     with pytest.raises(S.SMCError):
         ctx.log_score()
     ctx.close()
+
+
+def test_nse_coverage_over_seeds_on_gpu(S):
+    """Proposition 1: over 200 independent seeds the GPU runs' posterior-mean
+    and log-ML errors, standardized by their NSE, cover the closed forms at
+    about the t(J-1) rate (two-sided 95%, binomial tolerance)."""
+    X, y, m0, s0, lml, mn, Vn = _linreg(T=40, seed=8)
+    J, N = 8, 256
+    m = S.model_linreg(3, 1.0, m0, s0)
+    tq = stats.t(J - 1).ppf(0.975)
+    hits_m = hits_ml = 0
+    n = 200
+    for s in range(n):
+        th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), J * N, seed=3000 + s)
+        ctx = S.init(m, S.config_default(J=J, N=N, precision=S.FP64, seed=700 + s, rbar=10), y, th0, X=X)
+        ctx.run()
+        lm, nse, _ = ctx.log_ml()
+        mom = ctx.moments()
+        ctx.close()
+        hits_m += abs(mom[0, 0] - mn[0]) < tq * mom[0, 2]
+        hits_ml += abs(lm - lml) < tq * nse
+    # binomial(200, 0.95): mean 190, sd 3.1
+    assert hits_m >= 175, hits_m
+    assert hits_ml >= 160, hits_ml   # the log-ML normal approximation is the weaker one (ML_se)
