@@ -262,11 +262,12 @@ __device__ double adj_forward_fast(const float* th, int has_gamma, int eps0_zero
     for (int sg = 0; sg < nseg; ++sg) {
         const int t0 = sg * kSeg, n = min(kSeg, T - t0);
         if (sg > 0) {
-            double st[K + 1];
-            f.state_out(st);
+            // the state in natural units, converted in FP32 (it is stored in
+            // FP32): v_k = 2 ln2 v'_k (v'_1 less log2 sigma_Y - log2 s), eps = es / s
             float* c = ckpt + (size_t)(sg - 1) * (K + 1) * P + p;
 #pragma unroll
-            for (int k = 0; k <= K; ++k) c[k * P] = (float)st[k];
+            for (int k = 0; k < K; ++k) c[k * P] = (k == 0 ? f.v[0] - f.lsy2p : f.v[k]) * (float)(2.0 * kLn2);
+            c[K * P] = f.es * (float)(1.0 / kSfac);
         }
         if (n == kSeg && t0 > 0) {
 #pragma unroll 8
@@ -301,6 +302,72 @@ __device__ void adj_reverse(EgarchNat<Real, K, I> m, const Real* __restrict__ y,
 #pragma unroll
     for (int k = 0; k < K; ++k) vb[k] = 0;
     const Real c0 = (Real)kSqrt2OverPi;
+    // per-particle constants of the step below
+    Real a2[I], sgi[I], bp[K], bm[K];
+#pragma unroll
+    for (int i = 0; i < I; ++i) {
+        a2[i] = m.a[i] * m.a[i];
+        sgi[i] = Real(1) / m.a[i];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        bp[k] = m.be[k] + m.ga[k];   // beta sgn(eps) + gamma for eps > 0
+        bm[k] = m.ga[k] - m.be[k];   // and for eps < 0
+    }
+    // One reverse step at observation t: state (eps_t, exp(-s_t)), previous
+    // state (v_k,t-1, eps_t-1); has_prev: t >= 1 (0-based), i.e. v_k,t came
+    // from the recursion rather than from v_k0.
+    auto back = [&](Real eps, Real inv, const Real* vp, Real ep, bool has_prev) {
+        Real dle;
+        if constexpr (I == 1) {
+            dle = -eps;
+        } else {
+            Real x[I], dz[I], mx = -INFINITY;
+#pragma unroll
+            for (int i = 0; i < I; ++i) {
+                dz[i] = eps - m.mi[i];
+                const Real z = dz[i] * m.a[i];
+                x[i] = m.lpa[i] - Real(0.5) * z * z;
+                mx = fmax(mx, x[i]);
+            }
+            Real sum = 0;
+#pragma unroll
+            for (int i = 0; i < I; ++i) {
+                x[i] = nexp<Real>(x[i] - mx);
+                sum += x[i];
+            }
+            Real isum;
+            if constexpr (sizeof(Real) == 4) isum = __fdividef(1.0f, sum);   // sum in [1, I]
+            else isum = Real(1) / sum;
+            dle = 0;
+#pragma unroll
+            for (int i = 0; i < I; ++i) {
+                const Real ri = x[i] * isum;
+                const Real t = ri * dz[i] * a2[i];
+                dle -= t;
+                gs[2 + 3 * K + i] += ri;
+                gs[2 + 3 * K + I + i] += t;
+                gs[2 + 3 * K + 2 * I + i] += ri * (sgi[i] - dz[i] * dz[i] * m.a[i]);
+            }
+        }
+        Real eb = dle;
+#pragma unroll
+        for (int k = 0; k < K; ++k) eb += vb[k] * (eps > Real(0) ? bp[k] : (eps < Real(0) ? bm[k] : m.ga[k]));
+        const Real sb = Real(-1) - eb * eps;
+        gs[0] -= eb * inv;
+        gs[1] += sb;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            vb[k] = Real(0.5) * sb + m.al[k] * vb[k];
+            if (has_prev) {
+                gs[2 + k] += vb[k] * vp[k];
+                gs[2 + K + k] += vb[k] * (fabs(ep) - c0);
+                gs[2 + 2 * K + k] += vb[k] * ep;
+            } else if (m.eps0_zero) {
+                gs[2 + K + k] += vb[k] * (-c0);
+            }
+        }
+    };
     const int nseg = (T + kSeg - 1) / kSeg;
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int t0 = sg * kSeg, n = min(kSeg, T - t0);
@@ -340,72 +407,20 @@ __device__ void adj_reverse(EgarchNat<Real, K, I> m, const Real* __restrict__ y,
                 put(r, inv);
             }
         }
-        // reverse through the segment
+        // reverse through the segment: observations t0 + n - 1 .. t0 + 1 take
+        // their previous state from the buffer, observation t0 from the
+        // checkpoint; only the first observation of the series (t = 0) has no
+        // previous shock
+        const Real* q = buf + (size_t)(n - 1) * W * stride;
 #pragma unroll 1
-        for (int r = n - 1; r >= 0; --r) {
-            const int t = t0 + r;
-            const Real eps = buf[(r * W + K) * stride];
-            const Real inv = buf[(r * W + K + 1) * stride];
-            Real dle;
-            if constexpr (I == 1) {
-                dle = -eps;
-            } else {
-                Real x[I], mx = -INFINITY;
+        for (int r = n - 1; r >= 1; --r, q -= W * stride) {
+            const Real* qp = q - W * stride;
+            Real vp[K];
 #pragma unroll
-                for (int i = 0; i < I; ++i) {
-                    const Real z = (eps - m.mi[i]) * m.a[i];
-                    x[i] = m.lpa[i] - Real(0.5) * z * z;
-                    mx = fmax(mx, x[i]);
-                }
-                Real sum = 0;
-#pragma unroll
-                for (int i = 0; i < I; ++i) {
-                    x[i] = nexp<Real>(x[i] - mx);
-                    sum += x[i];
-                }
-                const Real isum = Real(1) / sum;
-                dle = 0;
-#pragma unroll
-                for (int i = 0; i < I; ++i) {
-                    const Real ri = x[i] * isum;
-                    const Real dz = eps - m.mi[i];
-                    const Real a2 = m.a[i] * m.a[i];
-                    dle -= ri * dz * a2;
-                    gs[2 + 3 * K + i] += ri;
-                    gs[2 + 3 * K + I + i] += ri * dz * a2;
-                    gs[2 + 3 * K + 2 * I + i] += ri * (Real(1) / m.a[i] - dz * dz * m.a[i]);
-                }
-            }
-            const Real sg_eps = eps > Real(0) ? Real(1) : (eps < Real(0) ? Real(-1) : Real(0));
-            Real eb = dle;
-#pragma unroll
-            for (int k = 0; k < K; ++k) eb += vb[k] * (m.be[k] * sg_eps + m.ga[k]);
-            const Real sb = Real(-1) - eb * eps;
-            gs[0] -= eb * inv;
-            gs[1] += sb;
-            // previous state (v_k,t-1, eps_t-1)
-            Real vp[K], ep;
-            if (r > 0) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) vp[k] = buf[((r - 1) * W + k) * stride];
-                ep = buf[((r - 1) * W + K) * stride];
-            } else {
-#pragma unroll
-                for (int k = 0; k < K; ++k) vp[k] = vprev[k];
-                ep = eprev;
-            }
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                vb[k] = Real(0.5) * sb + m.al[k] * vb[k];
-                if (t > 0) {
-                    gs[2 + k] += vb[k] * vp[k];
-                    gs[2 + K + k] += vb[k] * (fabs(ep) - c0);
-                    gs[2 + 2 * K + k] += vb[k] * ep;
-                } else if (m.eps0_zero) {
-                    gs[2 + K + k] += vb[k] * (-c0);
-                }
-            }
+            for (int k = 0; k < K; ++k) vp[k] = qp[k * stride];
+            back(q[K * stride], q[(K + 1) * stride], vp, qp[K * stride], true);
         }
+        back(buf[K * stride], buf[(K + 1) * stride], vprev, eprev, t0 > 0);
         if ((sg & 7) == 0 || sg == 0) {
 #pragma unroll
             for (int i = 0; i < NP; ++i) {

@@ -8,6 +8,10 @@
 namespace smc {
 
 constexpr int kMalaThreads = 128;
+// Launch width of the gradient kernels: each thread holds a shared-memory slab
+// for one segment's recomputed states (32 x (K + 2) values), so narrower blocks
+// pack more resident blocks per SM and leave a smaller last wave.
+constexpr int kMalaLaunch = 64;
 
 struct GradArgs {
     ModelDev m;
@@ -241,26 +245,26 @@ __global__ void __launch_bounds__(kMalaThreads) k_mutate_mala(MalaArgs a)
 template <class GP>
 cudaError_t launch_grad_t(const GradArgs& a, cudaStream_t s)
 {
-    const size_t sm = GP::smem_bytes(kMalaThreads);
+    const size_t sm = GP::smem_bytes(kMalaLaunch);
     static bool attr = false;
     if (!attr && sm > 0) {   // static + dynamic shared memory may pass the 48 KB default
         cudaFuncSetAttribute(k_loglik_grad<GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         attr = true;
     }
-    k_loglik_grad<GP><<<(a.P + kMalaThreads - 1) / kMalaThreads, kMalaThreads, sm, s>>>(a);
+    k_loglik_grad<GP><<<(a.P + kMalaLaunch - 1) / kMalaLaunch, kMalaLaunch, sm, s>>>(a);
     return cudaGetLastError();
 }
 
 template <class GP>
 cudaError_t launch_mala_t(const MalaArgs& a, cudaStream_t s)
 {
-    const size_t sm = GP::smem_bytes(kMalaThreads);
+    const size_t sm = GP::smem_bytes(kMalaLaunch);
     static bool attr = false;
     if (!attr && sm > 0) {   // static + dynamic shared memory may pass the 48 KB default
         cudaFuncSetAttribute(k_mutate_mala<GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         attr = true;
     }
-    k_mutate_mala<GP><<<(a.P + kMalaThreads - 1) / kMalaThreads, kMalaThreads, sm, s>>>(a);
+    k_mutate_mala<GP><<<(a.P + kMalaLaunch - 1) / kMalaLaunch, kMalaLaunch, sm, s>>>(a);
     return cudaGetLastError();
 }
 
