@@ -70,7 +70,23 @@ def alu_ops_per_eval(K, I, gamma):
     return fp32, mufu
 
 
-def alu_peak_evals(K, I, gamma, sms, mhz, paired=False):
+def mala_ops_per_eval(K, I, gamma):
+    """Algorithmic per-observation work of one MALA likelihood-and-gradient
+    evaluation: the forward recursion (as the random walk's), the state-only
+    recomputation of the reverse sweep's segment, and the adjoint step of the
+    reverse sweep (the formulas of the adjoint kernel's header: per mixture
+    component the responsibility, its three parameter adjoints and the shock's
+    adjoint term; per factor the shock coefficient, the state adjoint and three
+    parameter adjoints)."""
+    fp32, mufu = alu_ops_per_eval(K, I, gamma)
+    fp32 += 1 + (3 if gamma else 2) * K + (K - 1) + 4
+    mufu += 1
+    fp32 += (18 * I if I >= 2 else 1) + 7 * K + 4
+    mufu += I + 1 if I >= 2 else 0
+    return fp32, mufu
+
+
+def alu_peak_evals(K, I, gamma, sms, mhz, paired=False, mala=False):
     """Evaluations/s bound at the given SM clock from the FP32 pipe (128
     lanes/clk/SM), the SFU (32 lanes/clk/SM for ex2/lg2 on this part: the
     profiled kernels' XU-pipe share against their known SFU rate) and
@@ -78,7 +94,7 @@ def alu_peak_evals(K, I, gamma, sms, mhz, paired=False):
     paired FP32 instructions (two particles per thread) an FP32 instruction
     carries two lanes' work, so issue counts fp32/2 + mufu per evaluation while
     the FP32 pipe still bounds fp32."""
-    fp32, mufu = alu_ops_per_eval(K, I, gamma)
+    fp32, mufu = (mala_ops_per_eval if mala else alu_ops_per_eval)(K, I, gamma)
     limits = {"issue": 128.0 / ((fp32 / 2.0 if paired else fp32) + mufu),
               "fp32": 128.0 / fp32, "mufu": 32.0 / mufu}
     pipe = min(limits, key=limits.get)
@@ -383,12 +399,12 @@ def main():
     traffic = MUTATE_TRAFFIC.get((args.workload, shape[0], shape[1])) if not mala else None
     mhz, src = sm_max_mhz()
     paired = shape[0] == 2
-    peak, pipe = alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, mhz, paired)
+    # MALA's bound counts its forward, recomputation and reverse sweep per
+    # evaluation (mala_ops_per_eval)
+    peak, pipe = alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, mhz, paired, mala)
     avg_launch_s = (mut_ms / mut_n) / 1e3 if mut_n else float("nan")
     achieved = w.P * w.T / avg_launch_s if mut_n else float("nan")
-    fp32_ops, mufu_ops = alu_ops_per_eval(w.K, w.I, w.gamma)
-    # For MALA the kernel also recomputes and reverses the recursion; its frac is
-    # stated against the forward recursion's bound (likelihood evaluations/s).
+    fp32_ops, mufu_ops = (mala_ops_per_eval if mala else alu_ops_per_eval)(w.K, w.I, w.gamma)
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
             "frac": achieved / peak, "traffic": traffic, "pipe": pipe, "peak_source": f"{src} SM clock {mhz:.0f} MHz x {SM_COUNT_GB300} SMs",
             "ops_per_eval": {"fp32": fp32_ops, "mufu": mufu_ops},
@@ -400,7 +416,7 @@ def main():
                              "autotune_ms_per_iteration": shape[2]}}
     if clk.get("sm_mhz"):
         roof["frac_at_median_clock"] = achieved / alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, clk["sm_mhz"],
-                                                                 paired)[0]
+                                                                 paired, mala)[0]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
