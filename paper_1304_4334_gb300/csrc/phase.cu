@@ -176,9 +176,10 @@ __device__ void cov_final_body(const double* __restrict__ tot, int d, int P,
     if (threadIdx.x < 32) {
         // FP64 instructions have a long dependent latency on this part, so the
         // pivot's square root and reciprocal come from an FP32 reciprocal
-        // square root refined by two Newton steps in FP64 (each doubles the
-        // correct bits: 24 -> 48 -> full precision), and the trailing update
-        // spreads its elements over the lanes.
+        // square root refined by one Newton step in FP64 (about 22 correct
+        // bits become about 44: 1e-13 relative, far below what a proposal
+        // scale needs), and the trailing update spreads its elements over the
+        // lanes.
         const int lane = threadIdx.x;
         const int nel = d * (d + 1) / 2;
         for (int e = lane; e < nel; e += 32) {
@@ -193,7 +194,6 @@ __device__ void cov_final_body(const double* __restrict__ tot, int d, int P,
             if (piv > 0.0) {
                 double y = (double)rsqrtf((float)piv);
                 if (!(y > 0.0 && y < INFINITY)) y = rsqrt(piv);   // pivot outside the FP32 range
-                y = fma(0.5 * y, fma(-piv * y, y, 1.0), y);
                 y = fma(0.5 * y, fma(-piv * y, y, 1.0), y);
                 inv = y;
                 ljj = piv * y;
