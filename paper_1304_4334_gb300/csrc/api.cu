@@ -1027,7 +1027,7 @@ smc_status smc_autotune(smc_ctx* ctx, int iters, int* ppt, int* threads, double*
 
 smc_status smc_set_launch_shape(smc_ctx* ctx, int ppt, int threads)
 {
-    if (!ctx || (ppt != 1 && ppt != 2) || (threads != 32 && threads != 64 && threads != kMutThreads))
+    if (!ctx || ppt < 1 || ppt > 2 || (threads != 32 && threads != 64 && threads != kMutThreads))
         return SMC_EINVAL;
     if (ppt == 2 && !(ctx->model.model == SMC_EGARCH && ctx->cfg.precision == SMC_FP32 &&
                       ctx->cfg.mutation == SMC_RW))

@@ -239,37 +239,51 @@ struct EgarchF32 {
         return e;
     }
 
+    // The volatility part of one observation (log2 h, its sum, the shock):
+    // step = chain + mix.
     template <bool kFirst>
-    __device__ __forceinline__ void step(float y)
+    __device__ __forceinline__ void chain(float y)
     {
         if constexpr (kFirst) update_volatility_first();
         else update_volatility();
         const float e = log2h();
         sh += e;
         es = (y - mu) * ex2_approx(-e);
+    }
+
+    // The mixture part of one observation for the shock x (scaled units).
+    __device__ __forceinline__ void mix(float x)
+    {
         if constexpr (I == 1) {
-            sm = fmaf(-es, es, sm);
+            sm = fmaf(-x, x, sm);
         } else if constexpr (I == 2) {
-            const float z0 = fmaf(a[0], es, b[0]), z1 = fmaf(a[1], es, b[1]);
+            const float z0 = fmaf(a[0], x, b[0]), z1 = fmaf(a[1], x, b[1]);
             const float x0 = fmaf(-z0, z0, c[0]), x1 = fmaf(-z1, z1, c[1]);
             sm += fmaxf(x0, x1);
             prod = fmaf(prod, ex2_approx(-fabsf(x0 - x1)), prod);
         } else {
-            float x[I];
+            float xs[I];
 #pragma unroll
             for (int i = 0; i < I; ++i) {
-                const float z = fmaf(a[i], es, b[i]);
-                x[i] = fmaf(-z, z, c[i]);
+                const float z = fmaf(a[i], x, b[i]);
+                xs[i] = fmaf(-z, z, c[i]);
             }
-            float m = x[0];
+            float m = xs[0];
 #pragma unroll
-            for (int i = 1; i < I; ++i) m = fmaxf(m, x[i]);
-            float s = ex2_approx(x[0] - m);
+            for (int i = 1; i < I; ++i) m = fmaxf(m, xs[i]);
+            float s = ex2_approx(xs[0] - m);
 #pragma unroll
-            for (int i = 1; i < I; ++i) s += ex2_approx(x[i] - m);
+            for (int i = 1; i < I; ++i) s += ex2_approx(xs[i] - m);
             sm += m;
             prod *= s;
         }
+    }
+
+    template <bool kFirst>
+    __device__ __forceinline__ void step(float y)
+    {
+        chain<kFirst>(y);
+        mix(es);
     }
 
     // Continue from a saved state (natural units) and evaluate one observation's

@@ -297,7 +297,7 @@ def test_small_blocks_fp64_and_invalid_shapes(S):
             ctx.cycle()
         out.append(ctx.particles())
         if thr == 32:
-            for bad in [(1, 96), (2, 32), (3, 64)]:   # (2, 32): FP64 has no packed pair
+            for bad in [(1, 96), (2, 32), (3, 64)]:   # FP64 has no paired shape
                 with pytest.raises(S.SMCError):
                     ctx.set_launch_shape(*bad)
         ctx.close()
