@@ -255,6 +255,24 @@ smc_status smc_log_score(smc_ctx* ctx, double* log_score, double* nse);
  * are NaN.  Synchronises. */
 smc_status smc_pit(smc_ctx* ctx, double* out, int T);
 
+/* Checkpoint and resume between cycles.  smc_save writes everything a run
+ * carries across a cycle boundary to `path`: the model, the settings, the
+ * observations, the current particles (theta, log likelihood, log prior,
+ * recursion state, MALA gradient), the per-group log-ML and log-score
+ * accumulators, the PIT values, the device control block (step size, power,
+ * log wtilde, acceptance bookkeeping), the cycle count and the hybrid design
+ * being recorded or replayed.  Call it between smc_cycle calls (it
+ * synchronises the stream).  smc_load creates a context from such a file on
+ * `stream` (the caller frees it with smc_free); later smc_cycle calls continue
+ * the saved run exactly, the random numbers being counter-based.  SMC_EINVAL
+ * for an unreadable or inconsistent file (written by another build of the
+ * library, for instance); SMC_ECUDA / SMC_ENOMEM for device failures.
+ * smc_describe copies a context's model, settings and observation count
+ * (each output nullable). */
+smc_status smc_save(smc_ctx* ctx, const char* path);
+smc_status smc_load(const char* path, void* stream, smc_ctx** out);
+smc_status smc_describe(const smc_ctx* ctx, smc_model* m, smc_config* c, int* T);
+
 /* Failure-detection self-test: one block runs the library's bounded mbarrier
  * wait (the one guarding every staged-observation copy) with a limit of
  * limit_ns (0 < limit_ns <= 2 s) on a barrier that is completed only when

@@ -86,6 +86,9 @@ def _declare(L):
     L.smc_log_ml.argtypes = [vp, dp, dp, dp]
     L.smc_log_score.argtypes = [vp, dp, dp]
     L.smc_wait_selftest.argtypes = [C.c_uint64, C.c_int, vp]
+    L.smc_save.argtypes = [vp, C.c_char_p]
+    L.smc_load.argtypes = [C.c_char_p, vp, P(vp)]
+    L.smc_describe.argtypes = [vp, P(smc_model), P(smc_config), P(C.c_int)]
     L.smc_pit.argtypes = [vp, dp, C.c_int]
     L.smc_moments.argtypes = [vp, dp, P(C.c_int)]
     L.smc_get_particles.argtypes = [vp, dp, dp, dp, dp]
@@ -358,6 +361,27 @@ class Ctx:
         _check(lib().smc_mutate_time(self.h, C.byref(ms), C.byref(n), int(reset)), self.h)
         return ms.value, n.value
 
+    def save(self, path):
+        """Checkpoint the run between cycles (smc_save)."""
+        _check(lib().smc_save(self.h, str(path).encode()), self.h)
+
+    @classmethod
+    def load(cls, path, stream=None):
+        """A context resumed from a checkpoint file (smc_load)."""
+        h = C.c_void_p()
+        st = lib().smc_load(str(path).encode(), _stream(stream), C.byref(h))
+        if st != OK:
+            raise SMCError(st, "smc_load failed")
+        self = cls.__new__(cls)
+        self.h = h
+        m, c, T = smc_model(), smc_config(), C.c_int()
+        _check(lib().smc_describe(h, C.byref(m), C.byref(c), C.byref(T)), h)
+        self.model, self.cfg = m, c
+        self.d = m.n_free if m.n_free > 0 else m.d_full
+        self.P = c.J * c.N
+        self.T = T.value
+        return self
+
     def close(self):
         if getattr(self, "h", None):
             lib().smc_free(self.h)
@@ -463,6 +487,10 @@ class Batch:
 
 def init(model, cfg, y, theta0, X=None, stream=None, theta0_on_device=False):
     return Ctx(model, cfg, y, theta0, X=X, stream=stream, theta0_on_device=theta0_on_device)
+
+
+def load(path, stream=None):
+    return Ctx.load(path, stream=stream)
 
 
 # ------------------------------------------------ stateless (torch device buffers)
