@@ -255,6 +255,17 @@ smc_status smc_log_score(smc_ctx* ctx, double* log_score, double* nse);
  * are NaN.  Synchronises. */
 smc_status smc_pit(smc_ctx* ctx, double* out, int T);
 
+/* Prior simulation (Table 1) on the device: theta (device [d][P]) gets P
+ * draws of the model's free parameters, theta_i = prior_mean_i + prior_sd_i z
+ * with z standard normal, components with a finite prior_lo redrawn until they
+ * are inside (truncation by rejection; after 64 rejected attempts the bound
+ * itself).  Component i of particle n at attempt a is normal i % 4 of the
+ * Philox4x64-10 block at counter (n, a, 0, 5 << 32 | i / 4), key (seed, 0),
+ * by Box-Muller on the 53-bit uniform pairs (0, 1) and (2, 3) (cosine for the
+ * even, sine for the odd normal).  The result is a valid theta0 for smc_init
+ * with theta0_on_device = 1.  Asynchronous on `stream`. */
+smc_status smc_draw_prior(const smc_model* m, uint64_t seed, int P, double* theta, void* stream);
+
 /* Checkpoint and resume between cycles.  smc_save writes everything a run
  * carries across a cycle boundary to `path`: the model, the settings, the
  * observations, the current particles (theta, log likelihood, log prior,

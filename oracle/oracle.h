@@ -39,6 +39,7 @@ double or_philox_log_uniform(uint64_t seed, uint64_t p, uint64_t iter, uint64_t 
 #define OR_TAG_M_UNIFORM 2u   /* Metropolis-Hastings uniform (M phase)        */
 #define OR_TAG_S_RESID   3u   /* residual / multinomial draws (S phase)       */
 #define OR_TAG_C_PIT     4u   /* PIT auxiliary draw Y_s (C phase, Section 4.1) */
+#define OR_TAG_PRIOR     5u   /* prior draws (Table 1)                         */
 
 /* ---- model description ---------------------------------------------------- */
 enum { OR_EGARCH = 0, OR_LINREG = 1 };
@@ -128,6 +129,11 @@ int or_resample(const double *w, int J, int N, int resid, uint64_t seed,
  * (the last two are the paper's experimental alternatives). */
 int or_resample_scheme(const double *w, int J, int N, int scheme, uint64_t seed,
                        uint64_t cycle, int32_t *idx);
+
+/* ---- prior draws (Table 1; truncation by rejection) ------------------------ */
+/* theta[P][d] (free parameters): component i of particle n at attempt a is
+ * normal i % 4 of the Philox block (n, a, 0, OR_TAG_PRIOR << 32 | i / 4).     */
+void or_draw_prior(const or_model *m, uint64_t seed, int P, double *theta);
 
 /* ---- probability integral transform (Section 4.1) -------------------------- */
 /* Simulated standardized shock of Y_s ~ p(Y_s | y_{1:s-1}, theta) for particle

@@ -127,6 +127,7 @@ def _declare(L):
     L.or_mutate_indep.argtypes = [C.POINTER(Model), dp, dp, C.c_int, dp, dp, dp, dp, C.c_int, dp, dp,
                                   C.c_double, C.c_uint64, C.c_uint64, C.c_uint64, ip, C.c_int]
     L.or_mutate_indep.restype = C.c_long
+    L.or_draw_prior.argtypes = [C.POINTER(Model), C.c_uint64, C.c_int, dp]
     L.or_pit_shock.argtypes = [C.POINTER(Model), dp, C.c_uint64, C.c_uint64, C.c_int]
     L.or_pit_shock.restype = C.c_double
     L.or_power_search.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_int, dp]
@@ -396,6 +397,13 @@ def mutate_mala(spec, y, theta, ll, lp, grad, state, Lmat, phi, seed, cycle, it,
                                len(y), _d(theta), _d(ll), _d(lp), _d(grad), _d(state), P,
                                _d(_f64(Lmat)), phi, seed, cycle, it, acc.ctypes.data_as(ip), nthreads)
     return theta, ll, lp, grad, state, acc, n
+
+
+def draw_prior(spec, seed, P):
+    """Prior draws theta[P][d] from Table 1 by Philox (truncation by rejection)."""
+    th = np.zeros((P, spec.d))
+    _load().or_draw_prior(C.byref(spec.c), seed, P, _d(th))
+    return th
 
 
 def pit_shock(spec, theta, seed, particle, s):

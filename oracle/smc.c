@@ -70,6 +70,35 @@ double or_philox_log_uniform(uint64_t seed, uint64_t p, uint64_t iter, uint64_t 
     return log(u53(out[0]));
 }
 
+/* ------------------------------ prior draws ------------------------------- */
+/* Table 1 priors: theta_i = m_i + s_i z_i, z_i standard normal; a component
+ * with a finite lower bound (theta_8i >= -3) is redrawn until it is inside
+ * (truncation by rejection).  The draw of component i at attempt a is normal
+ * i % 4 of the Philox block at counter (particle, a, 0, tag 5 << 32 | i / 4):
+ * Box-Muller on the uniform pairs (0,1) -> normals 0 (cos), 1 (sin) and
+ * (2,3) -> normals 2, 3.  After 64 rejected attempts the bound itself is used. */
+void or_draw_prior(const or_model *m, uint64_t seed, int P, double *theta)
+{
+    const uint64_t key[2] = {seed, 0};
+    const int d = m->d;
+    for (int n = 0; n < P; ++n)
+        for (int i = 0; i < d; ++i) {
+            double x = m->prior_lo[i];
+            for (int a = 0; a < 64; ++a) {
+                uint64_t ctr[4] = {(uint64_t)n, (uint64_t)a, 0, ((uint64_t)OR_TAG_PRIOR << 32) | (uint64_t)(i / 4)};
+                uint64_t out[4];
+                or_philox4x64(ctr, key, out);
+                const int pair = (i % 4) / 2;
+                double rho = sqrt(-2.0 * log(u53(out[2 * pair])));
+                double ang = 2.0 * M_PI * u53(out[2 * pair + 1]);
+                double z = (i % 2 == 0) ? rho * cos(ang) : rho * sin(ang);
+                double v = m->prior_mean[i] + m->prior_sd[i] * z;
+                if (v >= m->prior_lo[i]) { x = v; break; }
+            }
+            theta[(size_t)n * d + i] = x;
+        }
+}
+
 /* ------------------------ probability integral transform ------------------ */
 /* Section 4.1: Y_s ~ p(Y_s | y_{1:s-1}, theta) is location + scale * e with e the
  * standardized shock (EGARCH: location mu_Y, scale h_s; LINREG: x_s'beta and

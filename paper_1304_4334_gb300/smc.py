@@ -87,6 +87,7 @@ def _declare(L):
     L.smc_log_score.argtypes = [vp, dp, dp]
     L.smc_wait_selftest.argtypes = [C.c_uint64, C.c_int, vp]
     L.smc_save.argtypes = [vp, C.c_char_p]
+    L.smc_draw_prior.argtypes = [P(smc_model), C.c_uint64, C.c_int, vp, vp]
     L.smc_load.argtypes = [C.c_char_p, vp, P(vp)]
     L.smc_describe.argtypes = [vp, P(smc_model), P(smc_config), P(C.c_int)]
     L.smc_pit.argtypes = [vp, dp, C.c_int]
@@ -491,6 +492,14 @@ def init(model, cfg, y, theta0, X=None, stream=None, theta0_on_device=False):
 
 def load(path, stream=None):
     return Ctx.load(path, stream=stream)
+
+
+def draw_prior(model, seed, P, stream=None):
+    """Table 1 prior draws on the device: a float64 cuda tensor [d, P]."""
+    import torch
+    th = torch.empty((model.d, P), dtype=torch.float64, device="cuda")
+    _check(lib().smc_draw_prior(C.byref(model), seed, P, _ptr(th), _stream(stream)))
+    return th
 
 
 # ------------------------------------------------ stateless (torch device buffers)

@@ -443,3 +443,17 @@ def test_bounded_wait_times_out_and_the_context_survives(S):
     ll = torch.empty(P, dtype=torch.float64, device="cuda")
     S.loglik(S.model_egarch(K, I_, True), S.FP64, dev(y), soa(th), ll)
     np.testing.assert_allclose(host(ll), O.loglik(spec, y, th), rtol=1e-9)
+
+
+def test_prior_draws_match_the_oracle(S):
+    """Device prior draws (Table 1, Philox counters, truncation by rejection)
+    equal the oracle's to rounding, for EGARCH(2,2) and the regression."""
+    torch = torch_cuda()
+    for K, I_ in [(2, 2), (3, 4), (1, 1)]:
+        spec = O.ModelSpec(K=K, I=I_, gamma=True)
+        m = S.model_egarch(K, I_, True)
+        th = host(S.draw_prior(m, 11, 5003)).T
+        th_o = O.draw_prior(spec, 11, 5003)
+        np.testing.assert_allclose(th, th_o, rtol=1e-12, atol=1e-13)
+        mean, sd, lo = O.table1_prior(K, I_)
+        assert np.all(th >= lo)

@@ -471,3 +471,17 @@ def test_checkpoint_resume_continues_the_run_exactly(S, tmp_path, case):
         assert np.array_equal(a.pit(), b.pit())
     a.close()
     b.close()
+
+
+def test_run_from_device_prior_draws_matches_closed_form(S):
+    """A run started from device prior draws (smc_draw_prior, theta0 on the
+    device) reaches the regression's exact log ML."""
+    X, y, m0, s0, lml, mn, Vn = _linreg()
+    J, N = 16, 512
+    m = S.model_linreg(3, 1.0, m0, s0)
+    th0 = S.draw_prior(m, 17, J * N)
+    ctx = S.init(m, S.config_default(J=J, N=N, precision=S.FP64, seed=18), y, th0, X=X, theta0_on_device=True)
+    ctx.run()
+    lm, nse, _ = ctx.log_ml()
+    assert abs(lm - lml) < 3.5 * nse + 0.02, (lm, lml, nse)
+    ctx.close()

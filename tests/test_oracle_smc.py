@@ -504,3 +504,26 @@ def test_pit_shock_draws_the_mixture():
     spec1 = O.ModelSpec(K=1, I=1, gamma=False)
     e1 = np.array([O.pit_shock(spec1, np.zeros(spec1.d), 9, n, 3) for n in range(20000)])
     assert stats.kstest(e1, "norm").pvalue > 1e-3
+
+
+# ------------------------------------------------- prior draws (Table 1)
+def test_prior_draws_follow_table1():
+    """Philox prior draws: untruncated components are N(m, s^2) (KS), the
+    truncated theta_8 components follow the truncated normal above -3 (KS),
+    and a seed reproduces its draws while another seed changes them."""
+    spec = O.ModelSpec(K=2, I=2, gamma=True)
+    mean, sd, lo = O.table1_prior(2, 2)
+    th = O.draw_prior(spec, 7, 20000)
+    assert th.shape == (20000, spec.d)
+    for i in range(spec.d):
+        if np.isfinite(lo[i]):
+            a = (lo[i] - mean[i]) / sd[i]
+            assert th[:, i].min() >= lo[i]
+            assert stats.kstest(th[:, i], stats.truncnorm(a, np.inf, loc=mean[i], scale=sd[i]).cdf).pvalue > 1e-3
+        else:
+            assert stats.kstest((th[:, i] - mean[i]) / sd[i], "norm").pvalue > 1e-3
+    assert np.array_equal(th, O.draw_prior(spec, 7, 20000))
+    assert not np.array_equal(th[:10], O.draw_prior(spec, 8, 10))
+    # components are independent draws: no correlation between neighbours
+    c = np.corrcoef(th[:, 0], th[:, 1])[0, 1]
+    assert abs(c) < 0.03
