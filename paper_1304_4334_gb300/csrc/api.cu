@@ -795,6 +795,7 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
     ctx->cov_G = cov_grid(P);
     CU(dalloc(&ctx->cov_part, (size_t)(ctx->cov_G + 1) * (d + d * (d + 1) / 2)));   // + totals row
     CU(dalloc(&ctx->search_part, search_part_len(P)));
+    CU(cudaMemset(ctx->search_part, 0, search_bar_bytes()));
     CU(dalloc(&ctx->cd_part, (size_t)((P + kMutThreads - 1) / kMutThreads) * kCdataChunk * 3));
     const int nf_max = d + 3;
     CU(dalloc(&ctx->mom_part, (size_t)nf_max * J * 2));

@@ -126,12 +126,19 @@ __global__ void k_adapt_h(Ctl* ctl, int P, double target, int hmin, int hmax)
 // Final step of the covariance (one block): updates h from the previous
 // iteration's acceptance (when a control block is given; a positive fixed_h
 // still scales Sigma in place of the adapted h), forms V from the totals of
-// the shifted sums and factors Sigma = h^2 V by a right-looking Cholesky in
-// shared memory, done by the first warp (lane i owns row i, d <= 32); a
-// non-positive pivot zeroes its column, as in the oracle.
+// the shifted sums and factors Sigma = h^2 V as h chol(V) by a right-looking
+// Cholesky in shared memory, done by the first warp; a non-positive pivot
+// zeroes its column, as in the oracle.
 // The shift of the sums is shift_f[i] (FP32, the mutation tiles) when given,
 // else shift_in[i * shift_stride]; the pooled mean goes to mean_out (FP64)
 // and, rounded, to mean_f_out (the next tiles' shift; may be shift_f).
+// Every FP64 instruction of this part occupies its pipe for about 64 cycles
+// whatever the number of active lanes, so the serial chain is kept short:
+// the divisions and the step-size update run on separate warps while the
+// totals load, element indices come from a table, and each pivot costs three
+// FP64 instructions (below).
+constexpr int kMaxPair = kMaxD * (kMaxD + 1) / 2;
+
 __device__ void cov_final_body(const double* __restrict__ tot, int d, int P,
                                const double* __restrict__ shift_in, size_t shift_stride,
                                const float* shift_f, Ctl* ctl, int fixed_h, double target, int hmin,
@@ -141,25 +148,33 @@ __device__ void cov_final_body(const double* __restrict__ tot, int d, int P,
     __shared__ double S1[kMaxD];
     __shared__ double A[kMaxD][kMaxD + 1];
     __shared__ double shift[kMaxD];
-    __shared__ double hh, invP, invP1;
+    __shared__ unsigned char pi_[kMaxPair], pk_[kMaxPair];
+    __shared__ double hs, invP, invP1;
     const int npair = d * (d + 1) / 2;
     if (threadIdx.x == 0) {
+        invP = 1.0 / (double)P;
+    } else if (threadIdx.x == 32) {
+        invP1 = 1.0 / (double)(P - 1);
+    } else if (threadIdx.x == 64) {
         int h = fixed_h;
         if (ctl) {
             apply_h_update(ctl, P, target, hmin, hmax);
             if (fixed_h <= 0) h = ctl->h_tenths;   // fixed_h > 0 overrides the adapted step size
         }
-        hh = (h / 10.0) * (h / 10.0);
-        invP = 1.0 / (double)P;
-        invP1 = 1.0 / (double)(P - 1);
+        hs = h / 10.0;
+    }
+    for (int e = threadIdx.x; e < npair; e += blockDim.x) {
+        int i, k;
+        unpack_pair(e, i, k);
+        pi_[e] = (unsigned char)i;
+        pk_[e] = (unsigned char)k;
     }
     for (int i = threadIdx.x; i < d; i += blockDim.x)
         shift[i] = shift_f ? (double)shift_f[i] : shift_in[i * shift_stride];
     for (int e = threadIdx.x; e < d; e += blockDim.x) S1[e] = __ldcg(tot + e);
     __syncthreads();
     for (int e = threadIdx.x; e < npair; e += blockDim.x) {
-        int i, k;
-        unpack_pair(e, i, k);
+        const int i = pi_[e], k = pk_[e];
         const double c = (__ldcg(tot + d + e) - S1[i] * S1[k] * invP) * invP1;
         A[i][k] = c;
         A[k][i] = c;
@@ -174,40 +189,34 @@ __device__ void cov_final_body(const double* __restrict__ tot, int d, int P,
         for (int e = threadIdx.x; e < d * d; e += blockDim.x) cov_out[e] = A[e / d][e % d];
     __syncthreads();
     if (threadIdx.x < 32) {
-        // FP64 instructions have a long dependent latency on this part, so the
-        // pivot's square root and reciprocal come from an FP32 reciprocal
-        // square root refined by one Newton step in FP64 (about 22 correct
-        // bits become about 44: 1e-13 relative, far below what a proposal
-        // scale needs), and the trailing update spreads its elements over the
-        // lanes.
+        // Pivot: y = piv^-1/2 from the FP32 reciprocal square root refined by
+        // one Newton step in FP64, y = y0 + (y0/2)(1 - piv y0^2): about 22
+        // correct bits become about 44 (1e-13 relative, far below what a
+        // proposal scale needs).  The column scaling and sqrt(piv) = piv y
+        // share one multiply across the lanes.
         const int lane = threadIdx.x;
-        const int nel = d * (d + 1) / 2;
-        for (int e = lane; e < nel; e += 32) {
-            int i, k;
-            unpack_pair(e, i, k);
-            A[i][k] *= hh;
-        }
-        __syncwarp();
         for (int j = 0; j < d; ++j) {
             const double piv = A[j][j];
-            double inv = 0.0, ljj = 0.0;
-            if (piv > 0.0) {
-                double y = (double)rsqrtf((float)piv);
-                if (!(y > 0.0 && y < INFINITY)) y = rsqrt(piv);   // pivot outside the FP32 range
-                y = fma(0.5 * y, fma(-piv * y, y, 1.0), y);
-                inv = y;
-                ljj = piv * y;
+            const long long pb = __double_as_longlong(piv);
+            double y = 0.0;
+            if (pb > 0 && pb < 0x7ff0000000000000LL) {   // positive and finite
+                const float y0f = rsqrtf((float)piv);
+                if (y0f > 0.0f && y0f < INFINITY) {
+                    const double y0 = (double)y0f;
+                    y = fma((double)(0.5f * y0f), fma(-piv * y0, y0, 1.0), y0);
+                } else {
+                    y = rsqrt(piv);   // pivot outside the FP32 range
+                }
             }
+            const bool col = lane >= j && lane < d;
+            const double v = col ? A[lane][j] * y : 0.0;
             __syncwarp();
-            if (lane == j) A[j][j] = ljj;
-            if (lane > j && lane < d) A[lane][j] *= inv;
+            if (col) A[lane][j] = v;
             __syncwarp();
             const int m = d - j - 1;
-            for (int e = lane; e < m * (m + 1) / 2; e += 32) {
-                int ii, kk;
-                unpack_pair(e, ii, kk);
-                ii += j + 1;
-                kk += j + 1;
+            const int ne = m * (m + 1) / 2;
+            for (int e = lane; e < ne; e += 32) {
+                const int ii = pi_[e] + j + 1, kk = pk_[e] + j + 1;
                 A[ii][kk] = fma(-A[ii][j], A[kk][j], A[ii][kk]);
             }
             __syncwarp();
@@ -217,7 +226,7 @@ __device__ void cov_final_body(const double* __restrict__ tot, int d, int P,
     if (L_out)
         for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
             const int i = e / d, k = e % d;
-            L_out[e] = k <= i ? A[i][k] : 0.0;
+            L_out[e] = k <= i ? A[i][k] * hs : 0.0;
         }
 }
 
@@ -250,9 +259,53 @@ __device__ __forceinline__ double cov_entry_total(const void* __restrict__ parts
 {
     double s = 0.0;
     if constexpr (kTiles) {
+        // Runs of 16 tile sums are added in FP32 with the rounding error of
+        // every addition carried along (Knuth's TwoSum), so each run enters
+        // FP64 as an almost exact pair: a sixteenth of the FP64 additions
+        // (each FP64 instruction holds its pipe for about 64 cycles here), with
+        // no loss against summing every tile in FP64.  A thread issues all
+        // loads of a run before it adds (16-byte loads when rows allow).
         const int r = e < d ? e : e - d + kD;
         const float* row = static_cast<const float*>(parts) + (size_t)r * nparts;
-        for (int t = threadIdx.x; t < nparts; t += blockDim.x) s += (double)row[t];
+        float hi = 0.0f, lo = 0.0f;
+        auto add = [&](float v) {
+            const float a = hi + v;
+            const float bv = a - hi;
+            lo += (hi - (a - bv)) + (v - bv);
+            hi = a;
+        };
+        auto flush = [&]() {
+            s += (double)hi + (double)lo;
+            hi = lo = 0.0f;
+        };
+        const int nb = blockDim.x;
+        if ((nparts & 3) == 0) {
+            const float4* row4 = reinterpret_cast<const float4*>(row);
+            const int n4 = nparts >> 2;
+            for (int t0 = threadIdx.x; t0 < n4; t0 += 4 * nb) {
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    v[u] = t0 + u * nb < n4 ? row4[t0 + u * nb] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    add(v[u].x);
+                    add(v[u].y);
+                    add(v[u].z);
+                    add(v[u].w);
+                }
+                flush();
+            }
+        } else {
+            for (int t0 = threadIdx.x; t0 < nparts; t0 += 16 * nb) {
+                float v[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) v[u] = t0 + u * nb < nparts ? row[t0 + u * nb] : 0.0f;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) add(v[u]);
+                flush();
+            }
+        }
     } else {
         const double* pp = static_cast<const double*>(parts);
         for (int g = threadIdx.x; g < nparts; g += blockDim.x) s += pp[(size_t)g * nacc + e];
@@ -399,51 +452,108 @@ cudaError_t launch_adapt_h(Ctl* ctl, int P, double acc_target, int hmin, int hma
 // RSS(dphi) = (sum_n w_n)^2 / (P sum_n w_n^2) with w_n = exp(dphi (l_n - max l))
 // (Section 3.3, pooled over all particles).  One pass evaluates 32 candidate
 // increments spread evenly over (lo, hi]: lane c of every warp owns candidate
-// c and the warp walks its particles with shuffles.  Candidate weights are
-// FP32 hardware exponentials, summed in FP32 over one warp tile and in FP64
-// across tiles; the chosen power is then used in FP64 for the weights.
-constexpr int kSearchThreads = 256;
+// c and the warp walks its 32-particle tiles with shuffles.  Candidate weights
+// are FP32 hardware exponentials summed in FP32 over one tile; tile sums
+// (<= 32) enter 64-bit fixed point (2^-36 units), so block and grid totals are
+// exact integer sums whose value does not depend on the order of addition.
+// The whole search (max l, then every pass) is one cooperative launch with at
+// most one block per SM; blocks meet at bounded grid barriers, and each block
+// takes the same decision from the same totals.
+constexpr int kSearchThreads = 512;
+constexpr int kSearchWarps = kSearchThreads / 32;
 constexpr int kCand = 32;
+constexpr int kRegTiles = 4;                      // tiles a warp keeps in registers
+constexpr float kFixScale = 68719476736.0f;       // 2^36
+constexpr double kFixInv2 = 1.0 / 68719476736.0;  // 2^-36
 
 int search_grid(int P)
 {
-    const int by = (P + kSearchThreads - 1) / kSearchThreads;
-    const int cap = 2 * device_sm_count();
-    return by < cap ? by : cap;
+    const int tiles = (P + 31) / 32;
+    const int by = (tiles + kSearchWarps - 1) / kSearchWarps;
+    const int cap = device_sm_count();
+    return by < 1 ? 1 : (by < cap ? by : cap);
+}
+
+// Scratch (doubles): 8 barrier words, 3 rotating slots of 64 fixed-point
+// totals, one max key per block, then the shifted FP32 log likelihoods of the
+// tiles a warp does not keep in registers.
+struct SearchScratch {
+    unsigned int* bar;            // [0] arrivals, [1] generation, [2] abort
+    unsigned long long* acc;      // [3][2 kCand]
+    long long* bkey;              // [G]
+    float* xf;                    // [P]
+};
+
+__host__ __device__ inline SearchScratch search_scratch(double* part, int G)
+{
+    SearchScratch s;
+    s.bar = reinterpret_cast<unsigned int*>(part);
+    s.acc = reinterpret_cast<unsigned long long*>(part + 8);
+    s.bkey = reinterpret_cast<long long*>(part + 8 + 3 * 2 * kCand);
+    s.xf = reinterpret_cast<float*>(part + 8 + 3 * 2 * kCand + G);
+    return s;
 }
 
 size_t search_part_len(int P)
 {
-    return (size_t)search_grid(P) * kCand * 2 + 2 * (size_t)search_grid(P);
+    return 8 + 3 * 2 * kCand + (size_t)search_grid(P) + ((size_t)P + 1) / 2;
 }
 
-__global__ void __launch_bounds__(kSearchThreads) k_llmax_partial(const double* __restrict__ ll, int P,
-                                                                 double* part)
+size_t search_bar_bytes() { return 8 * sizeof(double); }
+
+// Order-preserving map of a double onto a signed 64-bit key, in integer
+// arithmetic (a NaN log likelihood counts as -inf, as in the S phase).
+constexpr long long kNegInfBits = (long long)0xfff0000000000000ull;
+__device__ __forceinline__ long long order_key(double x)
 {
-    __shared__ double red[32];
-    double m = -INFINITY;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < P; n += gridDim.x * blockDim.x) {
-        const double x = ll[n];
-        if (x > m) m = x;
+    long long b = __double_as_longlong(x);
+    if ((b & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL) b = kNegInfBits;
+    return b >= 0 ? b : b ^ 0x7fffffffffffffffLL;
+}
+constexpr long long kNegInfKey = kNegInfBits ^ 0x7fffffffffffffffLL;
+
+__device__ __forceinline__ double key_value(long long k)
+{
+    return __longlong_as_double(k >= 0 ? k : k ^ 0x7fffffffffffffffLL);
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Barrier over the blocks of a cooperative launch.  Arrivals count up to the
+// grid size; the last arrival resets the count and advances the generation.
+// The wait is bounded: on time-out (or when another block gave up) the abort
+// word is set and every block returns false.
+__device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        __threadfence();
+        const unsigned int gen = ld_acquire_u32(bar + 1);
+        if (atomicAdd(bar, 1u) + 1u == nblocks) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (ld_acquire_u32(bar + 1) == gen) {
+                if (ld_acquire_u32(bar + 2) != 0u || global_ns() - t0 > kWaitLimitNs) {
+                    atomicExch(bar + 2, 1u);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
     }
-    m = block_max(m, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = m;
-}
-
-__global__ void k_search_init(const double* part, int G, Ctl* ctl)
-{
-    double m = -INFINITY;
-    for (int g = threadIdx.x; g < G; g += 32) m = fmax(m, part[g]);
-    m = warp_max(m);
-    if (threadIdx.x != 0) return;
-    ctl->llmax = m;
-    ctl->lo = 0.0;
-    ctl->hi = 1.0 - ctl->phi;
-    ctl->pass = 0;
-    ctl->done = (m == -INFINITY) || !(ctl->hi > 0.0);
-    ctl->last = ctl->done;
-    ctl->dphi = ctl->hi;
-    if (m == -INFINITY) raise_error(&ctl->err, kErrDegenerate);
+    __syncthreads();
+    return ok != 0;
 }
 
 __device__ __forceinline__ double candidate(double lo, double hi, int c)
@@ -452,97 +562,169 @@ __device__ __forceinline__ double candidate(double lo, double hi, int c)
     return c == kCand - 1 ? hi : lo + (hi - lo) * ((double)(c + 1) * (1.0 / kCand));
 }
 
-// One pass: each block sums, per candidate (one per lane), w and w^2 over its
-// particles into part; the last block to finish (ctl->search_blocks counts
-// them and returns to zero) totals the blocks in FP64 and narrows the bracket
-// to the first candidate whose pooled RSS is below D1.
-__global__ void __launch_bounds__(kSearchThreads) k_power_pass(const double* __restrict__ ll, int P,
-                                                              Ctl* ctl, double* part, double d1, int passes)
+__device__ __forceinline__ long long warp_max_key(long long k)
 {
-    if (ctl->done) return;
-    __shared__ double s1w[kSearchThreads / 32][kCand], s2w[kSearchThreads / 32][kCand];
-    __shared__ int last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwb = blockDim.x >> 5;
-    const double llmax = ctl->llmax;
-    const float dc = (float)(candidate(ctl->lo, ctl->hi, lane) * kLog2e);
-    double s1 = 0.0, s2 = 0.0;
-    const int nw = gridDim.x * nwb;
-    const int gw = blockIdx.x * nwb + warp;
-    for (int base = gw * 32; base < P; base += nw * 32) {
-        const int n = base + lane;
-        const float x = n < P ? (float)(ll[n] - llmax) : -INFINITY;
-        float a1 = 0.0f, a2 = 0.0f;
-#pragma unroll 8
-        for (int j = 0; j < 32; ++j) {
-            const float xj = __shfl_sync(0xffffffffu, x, j);
-            const float w = xj == -INFINITY ? 0.0f : ex2_approx(dc * xj);
-            a1 += w;
-            a2 = fmaf(w, w, a2);
-        }
-        s1 += (double)a1;
-        s2 += (double)a2;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long v = __shfl_xor_sync(0xffffffffu, k, o);
+        k = v > k ? v : k;
     }
-    s1w[warp][lane] = s1;
-    s2w[warp][lane] = s2;
+    return k;
+}
+
+__global__ void __launch_bounds__(kSearchThreads, 1) k_power_search(const double* __restrict__ ll, int P,
+                                                                   Ctl* ctl, double* part, double d1,
+                                                                   int passes)
+{
+    __shared__ long long skey[kSearchWarps];
+    __shared__ unsigned long long sacc[2 * kCand];
+    __shared__ double s_lo, s_hi, s_dphi;
+    __shared__ int s_done, s_last, s_pass;
+    const int G = gridDim.x;
+    const SearchScratch sc = search_scratch(part, G);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ntiles = (P + 31) / 32;
+    const int nw = G * kSearchWarps;
+    const int gw = blockIdx.x * kSearchWarps + warp;
+    if (threadIdx.x < 2 * kCand) sacc[threadIdx.x] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x < 2 * kCand) sc.acc[threadIdx.x] = 0ull;   // slot of pass 0
+
+    // ---- max l over all particles (integer keys: exact, order-free) ----
+    long long kr[kRegTiles];
+    long long km = kNegInfKey;
+#pragma unroll
+    for (int k = 0; k < kRegTiles; ++k) {
+        const int t = gw + k * nw;
+        const int n = t * 32 + lane;
+        kr[k] = (t < ntiles && n < P) ? order_key(ll[n]) : kNegInfKey;
+        km = kr[k] > km ? kr[k] : km;
+    }
+    for (int t = gw + kRegTiles * nw; t < ntiles; t += nw) {
+        const int n = t * 32 + lane;
+        const long long kk = n < P ? order_key(ll[n]) : kNegInfKey;
+        km = kk > km ? kk : km;
+    }
+    km = warp_max_key(km);
+    if (lane == 0) skey[warp] = km;
     __syncthreads();
     if (warp == 0) {
-        double t1 = 0.0, t2 = 0.0;
-        for (int w = 0; w < nwb; ++w) {
-            t1 += s1w[w][lane];
-            t2 += s2w[w][lane];
-        }
-        part[((size_t)blockIdx.x * kCand + lane) * 2 + 0] = t1;
-        part[((size_t)blockIdx.x * kCand + lane) * 2 + 1] = t2;
-        __threadfence();
-        unsigned int prev = 0;
-        if (lane == 0) prev = atomicAdd(&ctl->search_blocks, 1u);
-        prev = __shfl_sync(0xffffffffu, prev, 0);
-        if (lane == 0) last = prev == gridDim.x - 1;
+        long long k = lane < kSearchWarps ? skey[lane] : kNegInfKey;
+        k = warp_max_key(k);
+        if (lane == 0) sc.bkey[blockIdx.x] = k;
     }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // ---- select (last block): totals per candidate, warps over block rows ----
-    {
-        double t1 = 0.0, t2 = 0.0;
-        for (int g = warp; g < (int)gridDim.x; g += nwb) {
-            t1 += __ldcg(part + ((size_t)g * kCand + lane) * 2 + 0);
-            t2 += __ldcg(part + ((size_t)g * kCand + lane) * 2 + 1);
+    if (!grid_barrier(sc.bar, G)) {
+        if (threadIdx.x == 0) raise_error(&ctl->err, kErrTimeout);
+        return;
+    }
+    long long kg = kNegInfKey;
+    for (int b = lane; b < G; b += 32) {
+        const long long k = __ldcg(sc.bkey + b);
+        kg = k > kg ? k : kg;
+    }
+    kg = warp_max_key(kg);
+    const double llmax = key_value(kg);
+
+    // ---- shifted FP32 log likelihoods: registers, then scratch ----
+    float xr[kRegTiles];
+#pragma unroll
+    for (int k = 0; k < kRegTiles; ++k) {
+        xr[k] = -INFINITY;
+        if (gw + k * nw < ntiles && kr[k] != kNegInfKey) xr[k] = (float)(key_value(kr[k]) - llmax);
+    }
+    for (int t = gw + kRegTiles * nw; t < ntiles; t += nw) {
+        const int n = t * 32 + lane;
+        if (n < P) {
+            const long long kk = order_key(ll[n]);
+            sc.xf[n] = kk == kNegInfKey ? -INFINITY : (float)(key_value(kk) - llmax);
+        }
+    }
+
+    double lo = 0.0, hi = 1.0 - ctl->phi, dphi = hi;
+    int done = (kg == kNegInfKey) || !(hi > 0.0);
+    int last = done, pass = 0;
+    for (int p = 0; p < passes && !done; ++p) {
+        const int slot = p % 3;
+        const float dc = (float)(candidate(lo, hi, lane) * kLog2e);
+        unsigned long long q1 = 0ull, q2 = 0ull;
+        auto tile = [&](float x) {
+            float a1 = 0.0f, a2 = 0.0f;
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) {
+                const float xj = __shfl_sync(0xffffffffu, x, j);
+                const float w = xj == -INFINITY ? 0.0f : ex2_approx(dc * xj);
+                a1 += w;
+                a2 = fmaf(w, w, a2);
+            }
+            q1 += __float2ull_rn(a1 * kFixScale);
+            q2 += __float2ull_rn(a2 * kFixScale);
+        };
+#pragma unroll
+        for (int k = 0; k < kRegTiles; ++k)
+            if (gw + k * nw < ntiles) tile(xr[k]);
+        for (int t = gw + kRegTiles * nw; t < ntiles; t += nw) {
+            const int n = t * 32 + lane;
+            tile(n < P ? sc.xf[n] : -INFINITY);
+        }
+        atomicAdd(&sacc[lane], q1);
+        atomicAdd(&sacc[kCand + lane], q2);
+        __syncthreads();
+        if (threadIdx.x < 2 * kCand) {
+            atomicAdd(&sc.acc[slot * 2 * kCand + threadIdx.x], sacc[threadIdx.x]);
+            sacc[threadIdx.x] = 0ull;
+        } else if (blockIdx.x == 0 && threadIdx.x < 4 * kCand) {
+            // the slot of the next pass was last read before the previous barrier
+            sc.acc[((p + 1) % 3) * 2 * kCand + threadIdx.x - 2 * kCand] = 0ull;
+        }
+        if (!grid_barrier(sc.bar, G)) {
+            if (threadIdx.x == 0) raise_error(&ctl->err, kErrTimeout);
+            return;
+        }
+        if (warp == 0) {
+            const double Q1 = (double)__ldcg(sc.acc + slot * 2 * kCand + lane);
+            const double Q2 = (double)__ldcg(sc.acc + slot * 2 * kCand + kCand + lane);
+            // RSS < D1 with RSS = (Q1 2^-36)^2 / (P Q2 2^-36)
+            const unsigned below = __ballot_sync(0xffffffffu, Q1 * Q1 * kFixInv2 < d1 * (double)P * Q2);
+            if (lane == 0) {
+                if (below == 0u) {
+                    // RSS stays >= D1 up to hi: in the first pass this takes the
+                    // whole remaining power (the last cycle); later it cannot
+                    // occur because hi was itself a candidate with RSS < D1.
+                    s_dphi = hi;
+                    s_done = 1;
+                    s_last = pass == 0;
+                    s_lo = lo;
+                    s_hi = hi;
+                    s_pass = pass;
+                } else {
+                    const int cc = __ffs(below) - 1;
+                    const double nhi = candidate(lo, hi, cc);
+                    s_lo = cc == 0 ? lo : candidate(lo, hi, cc - 1);
+                    s_hi = nhi;
+                    s_dphi = nhi;
+                    s_pass = pass + 1;
+                    s_done = s_pass >= passes;
+                    s_last = 0;
+                }
+            }
         }
         __syncthreads();
-        s1w[warp][lane] = t1;
-        s2w[warp][lane] = t2;
+        lo = s_lo;
+        hi = s_hi;
+        dphi = s_dphi;
+        done = s_done;
+        last = s_last;
+        pass = s_pass;
+        __syncthreads();
     }
-    __syncthreads();
-    if (warp != 0) return;
-    double t1 = 0.0, t2 = 0.0;
-    for (int w = 0; w < nwb; ++w) {
-        t1 += s1w[w][lane];
-        t2 += s2w[w][lane];
-    }
-    const double rss = t1 * t1 / ((double)P * t2);
-    const unsigned below = __ballot_sync(0xffffffffu, rss < d1);
-    if (lane == 0) {
-        ctl->search_blocks = 0u;
-        const double lo = ctl->lo, hi = ctl->hi;
-        if (below == 0u) {
-            // RSS stays >= D1 up to hi: in the first pass this takes the whole
-            // remaining power (the last cycle); later it cannot occur because hi
-            // was itself a candidate with RSS < D1.
-            ctl->dphi = hi;
-            ctl->done = 1;
-            ctl->last = ctl->pass == 0;
-        } else {
-            const int cc = __ffs(below) - 1;
-            const double nhi = candidate(lo, hi, cc);
-            const double nlo = cc == 0 ? lo : candidate(lo, hi, cc - 1);
-            ctl->lo = nlo;
-            ctl->hi = nhi;
-            ctl->dphi = nhi;
-            ctl->pass += 1;
-            if (ctl->pass >= passes) ctl->done = 1;
-        }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->llmax = llmax;
+        ctl->lo = lo;
+        ctl->hi = hi;
+        ctl->dphi = dphi;
+        ctl->pass = pass;
+        ctl->done = 1;
+        ctl->last = last;
+        if (kg == kNegInfKey) raise_error(&ctl->err, kErrDegenerate);
     }
 }
 
@@ -567,17 +749,12 @@ cudaError_t launch_set_power(Ctl* ctl, double phi_target, cudaStream_t s)
 cudaError_t launch_power_search(const double* ll, int P, double d1, int passes, double* part,
                                 Ctl* ctl, cudaStream_t s)
 {
-    const int G = search_grid(P);
-    double* mx = part + (size_t)G * kCand * 2;
-    k_llmax_partial<<<G, kSearchThreads, 0, s>>>(ll, P, mx);
+    int G = search_grid(P);
+    void* args[] = {(void*)&ll, (void*)&P, (void*)&ctl, (void*)&part, (void*)&d1, (void*)&passes};
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_power_search, dim3(G), dim3(kSearchThreads),
+                                                      args, 0, s);
     count_launch();
-    k_search_init<<<1, 32, 0, s>>>(mx, G, ctl);
-    count_launch();
-    for (int p = 0; p < passes; ++p) {
-        k_power_pass<<<G, kSearchThreads, 0, s>>>(ll, P, ctl, part, d1, passes);
-        count_launch();
-    }
-    return cudaGetLastError();
+    return e;
 }
 
 // ================================================================= S phase

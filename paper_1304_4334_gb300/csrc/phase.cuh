@@ -18,7 +18,6 @@ struct Ctl {
     // C phase, power tempering: k-ary search state.
     double llmax, lo, hi, dphi, rss, phi;
     int pass, done, last;
-    unsigned int search_blocks;     // blocks of the current pass that have finished (reset by the last)
     // C phase, data tempering: observations to absorb from the current chunk,
     // whether the chunk contains the stopping observation, and whether the
     // stop was forced (date of interest or T with RSS >= D1).
@@ -70,9 +69,12 @@ cudaError_t launch_cov_batch(const CovJob* jobs, int n, int Gmax, int dmax, cons
 // Applies a pending acceptance count to h (end of an M phase).
 cudaError_t launch_adapt_h(Ctl* ctl, int P, double acc_target, int hmin, int hmax, cudaStream_t s);
 
-// Power-tempering search; part sized search_part_len(P) doubles.
+// Power-tempering search; part sized search_part_len(P) doubles, whose first
+// search_bar_bytes() bytes (grid-barrier words) are zero before the first
+// call and are left zero by every call that completes.
 int search_grid(int P);
 size_t search_part_len(int P);
+size_t search_bar_bytes();
 cudaError_t launch_power_search(const double* ll, int P, double d1, int passes, double* part,
                                 Ctl* ctl, cudaStream_t s);
 

@@ -272,6 +272,7 @@ smc_status smc_power_search(const double* ll, int P, double phi, double d1, int 
     double* a = nullptr;
     int32_t* idx = nullptr;
     CK(cudaMallocAsync((void**)&part, search_part_len(P) * sizeof(double), s));
+    CK(cudaMemsetAsync(part, 0, search_bar_bytes(), s));
     CK(cudaMallocAsync((void**)&ctl, sizeof(Ctl), s));
     CK(cudaMallocAsync((void**)&gstat, 3 * sizeof(double), s));
     CK(cudaMallocAsync((void**)&lw, sizeof(double), s));
