@@ -331,7 +331,10 @@ def main():
         one_run(k)
     torch.cuda.synchronize()
 
-    ctx.profile(True)
+    # events around the first mutation launch of every M phase only: an event
+    # recorded between two kernels linked by programmatic dependent launch
+    # serialises them, so timing every launch would slow the step it measures
+    ctx.profile(2)
     ctx.mutate_time(reset=True)
     clocks = ClockSampler(local)
     if world > 1:
@@ -411,7 +414,9 @@ def main():
             "kernel": (f"k_mutate_mala<GradEgarch<float,{w.K},{w.I}>>" if mala
                        else f"k_mutate_x2<{w.K},{w.I}>" if paired
                        else f"k_mutate<PolicyEgarchF32<{w.K},{w.I}>>"), "avg_launch_ms": avg_launch_s * 1e3,
-            "launches": mut_n, "share_of_step": (mut_ms / 1e3) / t_total if t_total else None,
+            "launches": int(sum(msteps)), "timed_launches": mut_n,
+            "timed": "first mutation launch of every M phase (CUDA events)",
+            "share_of_step": avg_launch_s * sum(msteps) / t_total if t_total and mut_n else None,
             "launch_shape": {"particles_per_thread": shape[0], "threads_per_block": shape[1],
                              "autotune_ms_per_iteration": shape[2]}}
     if clk.get("sm_mhz"):

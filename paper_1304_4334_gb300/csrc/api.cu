@@ -476,13 +476,14 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
         a.pending = &ctx->ctl->pending;
         a.err = &ctx->ctl->err;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (ctx->profile) {
+        const bool timed = ctx->profile == 1 || (ctx->profile == 2 && r == 0);
+        if (timed) {
             e0 = take_event(ctx);
             e1 = take_event(ctx);
             CU(cudaEventRecord(e0, ctx->stream));
         }
         CU(launch_mala(a, c.precision, ctx->stream));
-        if (ctx->profile) {
+        if (timed) {
             CU(cudaEventRecord(e1, ctx->stream));
             ctx->ev_pending.push_back({e0, e1});
             ctx->mutate_launches += 1;
@@ -517,14 +518,18 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
     a.pending = &ctx->ctl->pending;
     a.err = &ctx->ctl->err;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (ctx->profile) {
+    const bool timed = ctx->profile == 1 || (ctx->profile == 2 && r == 0);
+    // a timed launch sits between two events, which serialise it anyway: it
+    // is launched plainly so that the events bracket the kernel alone
+    a.dependent = timed ? 0 : 1;
+    if (timed) {
         e0 = take_event(ctx);
         e1 = take_event(ctx);
         CU(cudaEventRecord(e0, ctx->stream));
     }
     if (ctx->ppt == 2) CU(launch_mutate_x2(a, ctx->mut_threads, ctx->stream));
     else CU(launch_mutate(a, c.precision, ctx->mut_threads, ctx->stream));
-    if (ctx->profile) {
+    if (timed) {
         CU(cudaEventRecord(e1, ctx->stream));
         ctx->ev_pending.push_back({e0, e1});
         ctx->mutate_launches += 1;
@@ -1111,7 +1116,8 @@ smc_status smc_design_replay(smc_ctx* ctx, int ncycles, const double* x, const i
 smc_status smc_profile(smc_ctx* ctx, int enable)
 {
     if (!ctx) return SMC_EINVAL;
-    ctx->profile = enable ? 1 : 0;
+    if (enable < 0 || enable > 2) return set_err(ctx, SMC_EINVAL, "profile mode must be 0, 1 or 2");
+    ctx->profile = enable;
     return SMC_OK;
 }
 

@@ -292,6 +292,32 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
         : "memory");
 }
 
+// Programmatic dependent launch (PTX griddepcontrol): a kernel launched with
+// pdl_launch may start while its predecessor in the stream is still running.
+// pdl_wait() returns once the predecessor has completed and its writes are
+// visible (at once when there is no such predecessor), so a kernel calls it
+// before touching anything a preceding kernel writes; pdl_trigger() lets the
+// next kernel launch once every block of this one has passed it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Error word bits reported through the context.
 enum : int { kErrTimeout = 1, kErrNonFinite = 2, kErrDegenerate = 4, kErrBounds = 8 };
 

@@ -23,13 +23,16 @@ cudaError_t launch_mutate_k(const MutateArgs& a, int threads, cudaStream_t s)
         }
         return cudaGetLastError();
     }
+    void (*k)(MutateArgs) = nullptr;
     switch (a.m.I) {
-    case 1: k_mutate<Pol<K, 1>><<<g, threads, 0, s>>>(a); break;
-    case 2: k_mutate<Pol<K, 2>><<<g, threads, 0, s>>>(a); break;
-    case 3: k_mutate<Pol<K, 3>><<<g, threads, 0, s>>>(a); break;
-    case 4: k_mutate<Pol<K, 4>><<<g, threads, 0, s>>>(a); break;
+    case 1: k = k_mutate<Pol<K, 1>>; break;
+    case 2: k = k_mutate<Pol<K, 2>>; break;
+    case 3: k = k_mutate<Pol<K, 3>>; break;
+    case 4: k = k_mutate<Pol<K, 4>>; break;
     default: return cudaErrorInvalidValue;
     }
+    if (a.dependent) return pdl_launch(k, g, threads, 0, s, a);
+    k<<<g, threads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -38,13 +41,16 @@ template <int K>
 cudaError_t launch_mutate_x2_k(const MutateArgs& a, int threads, cudaStream_t s)
 {
     const int g = (a.P + 2 * threads - 1) / (2 * threads);
+    void (*k)(MutateArgs) = nullptr;
     switch (a.m.I) {
-    case 1: k_mutate_x2<K, 1><<<g, threads, 0, s>>>(a); break;
-    case 2: k_mutate_x2<K, 2><<<g, threads, 0, s>>>(a); break;
-    case 3: k_mutate_x2<K, 3><<<g, threads, 0, s>>>(a); break;
-    case 4: k_mutate_x2<K, 4><<<g, threads, 0, s>>>(a); break;
+    case 1: k = k_mutate_x2<K, 1>; break;
+    case 2: k = k_mutate_x2<K, 2>; break;
+    case 3: k = k_mutate_x2<K, 3>; break;
+    case 4: k = k_mutate_x2<K, 4>; break;
     default: return cudaErrorInvalidValue;
     }
+    if (a.dependent) return pdl_launch(k, g, threads, 0, s, a);
+    k<<<g, threads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

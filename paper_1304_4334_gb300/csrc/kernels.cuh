@@ -45,6 +45,9 @@ struct MutateArgs {
     unsigned long long* acc_count;   // += accepted proposals
     int* pending;                    // set to 1 (nullable): an acceptance count awaits its h update
     int* err;
+    // Host-side launch choice: nonzero launches the kernel as a programmatic
+    // dependent of the preceding kernel (its blocks become resident early).
+    int dependent = 0;
 };
 
 struct LoglikArgs {
@@ -291,6 +294,9 @@ __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, 
     using Real = typename Pol::Real;
     using Obs = typename Pol::Obs;
     const int d = a.m.d;
+    // Under a dependent launch the block is resident before its predecessor
+    // ends; it waits here, before reading anything that kernel writes.
+    pdl_wait();
     for (int i = threadIdx.x; i < d * d; i += blockDim.x) sm.Ls[i] = (Real)a.L[i];
     if (threadIdx.x == 0) sm.acc_s = 0;
 
@@ -339,6 +345,7 @@ __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, 
         Pol::setup(mdl, a.m, full);
     }
     const bool ok = Pol::run(mdl, pipe, a.T, a.W);
+    pdl_trigger();   // the next kernel may launch once every block is here
     double ll_new = ok ? mdl.finish(a.T) : -INFINITY;
     if (isnan(ll_new)) ll_new = -INFINITY;
     if (!ok && threadIdx.x == 0) raise_error(a.err, kErrTimeout);
@@ -385,6 +392,7 @@ __device__ __forceinline__ void mutate_tile_x2(const MutateArgs& a, uint64_t ite
 {
     using Pol = PolicyEgarchF32<K, I>;
     const int d = a.m.d;
+    pdl_wait();   // as in mutate_tile
     for (int i = threadIdx.x; i < d * d; i += blockDim.x) sm.Ls[i] = a.L[i];
     if (threadIdx.x == 0) sm.acc_s = 0;
     ObsPipe<float, kChunkF32> pipe{sm.obuf, sm.bars, (const float*)a.obs, (int64_t)a.T,
@@ -417,6 +425,7 @@ __device__ __forceinline__ void mutate_tile_x2(const MutateArgs& a, uint64_t ite
         Pol::setup(mdl[h], a.m, full);
     }
     const bool ok = run_egarch_f32_x2<K, I>(mdl[0], mdl[1], pipe, a.T);
+    pdl_trigger();
     if (!ok && threadIdx.x == 0) raise_error(a.err, kErrTimeout);
     unsigned int nacc = 0;
 #pragma unroll

@@ -320,6 +320,8 @@ __global__ void __launch_bounds__(kCovThreads) k_cov_reduce(const void* __restri
 {
     __shared__ double red[32];
     __shared__ int last;
+    pdl_trigger();   // the mutation kernel may launch while this runs
+    pdl_wait();
     const int e = blockIdx.x;
     const double s = cov_entry_total<kTiles>(parts, nparts, nacc, e, f.d, f.tile_kd, red);
     if (threadIdx.x == 0) {
@@ -403,9 +405,10 @@ cudaError_t launch_cov_tiles(const float* tiles, int ntiles, int tile_kd, int d,
     const int nacc = d + d * (d + 1) / 2;
     const CovFinalArgs f{d, P, nullptr, 1, shift_f, ctl, fixed_h_tenths, acc_target, hmin, hmax, mean,
                          shift_f, nullptr, L, tile_kd};
-    k_cov_reduce<true><<<nacc, kCovThreads, 0, s>>>(tiles, ntiles, nacc, tot, counter, f);
+    const cudaError_t e = pdl_launch(k_cov_reduce<true>, dim3(nacc), dim3(kCovThreads), 0, s,
+                                     (const void*)tiles, ntiles, nacc, tot, counter, f);
     count_launch();
-    return cudaGetLastError();
+    return e;
 }
 
 // Independent sampler (Section 3.3): log q of every current particle under
@@ -849,11 +852,15 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
     const int per = (N + blockDim.x - 1) / blockDim.x;
     const int n0 = min(N, tid * per), n1 = min(N, n0 + per);
     __syncthreads();
+    // (w / max w is w itself when the weights came from log weights, whose
+    // maximum is exp(0) = 1; 2^32 w~ is exact, and truncation is the floor of
+    // a non-negative number.)
     uint64_t qloc = 0;
+    const bool unit_max = wmax == 1.0;
     for (int n = n0; n < n1; ++n) {
         const double w = ws[n];
-        const double wn = w > 0.0 ? w / wmax : 0.0;
-        const uint64_t q = (uint64_t)floor(ldexp(wn, 32));
+        const double wn = w > 0.0 ? (unit_max ? w : w / wmax) : 0.0;
+        const uint64_t q = (uint64_t)(wn * 4294967296.0);
         qs[n] = q;
         qloc += q;
     }

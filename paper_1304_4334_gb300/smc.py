@@ -354,6 +354,7 @@ class Ctx:
                                        _dptr(L)), self.h)
 
     def profile(self, enable=True):
+        """True or 1: time every mutation launch; 2: the first of each M phase."""
         _check(lib().smc_profile(self.h, int(enable)), self.h)
 
     def mutate_time(self, reset=False):
