@@ -123,20 +123,75 @@ __global__ void k_adapt_h(Ctl* ctl, int P, double target, int hmin, int hmax)
 
 
 
+// ---- double-float arithmetic for the factorisation (value = hi + lo) ----
+// Error-free transformations on the FP32 pipe (Knuth's TwoSum, Dekker's
+// product through fmaf) carry about 44 significant bits at FP32 latency; on
+// this part an FP64 instruction holds its pipe for ~64 cycles.  Products that
+// feed an addition use __fmul_rn, which the compiler never fuses into an FMA
+// (a fused rounding would break the exact error terms).
+struct Df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ Df df_quick(float a, float b)   // |a| >= |b|
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ Df df_mul(Df x, Df y)
+{
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+    return df_quick(p, e);
+}
+
+// a - x y
+__device__ __forceinline__ Df df_fms(Df a, Df x, Df y)
+{
+    const Df p = df_mul(x, y);
+    const float s = a.hi - p.hi;
+    const float bv = s - a.hi;
+    float e = (a.hi - (s - bv)) + (-p.hi - bv);
+    e += a.lo - p.lo;
+    return df_quick(s, e);
+}
+
+// p^-1/2 for p > 0: the FP32 reciprocal square root y0 (about 22 correct
+// bits) refined by one Newton step y0 + (y0/2)(1 - p y0^2), the residual
+// formed from exact products (about 43 bits, 1e-13 relative).
+__device__ __forceinline__ Df df_rsqrt(Df p)
+{
+    const float y0 = rsqrtf(p.hi);
+    const float q = __fmul_rn(y0, y0);
+    const float qe = fmaf(y0, y0, -q);        // y0^2 = q + qe
+    const float t = __fmul_rn(p.hi, q);
+    const float te = fmaf(p.hi, q, -t);       // p.hi q = t + te
+    const float r = ((1.0f - t) - te) - fmaf(p.hi, qe, __fmul_rn(p.lo, q));
+    return df_quick(y0, __fmul_rn(__fmul_rn(0.5f, y0), r));
+}
+
+__device__ __forceinline__ double pow2(int m)   // 2^m, |m| <= 1022
+{
+    return __longlong_as_double((long long)(1023 + m) << 52);
+}
+
 // Final step of the covariance (one block): updates h from the previous
 // iteration's acceptance (when a control block is given; a positive fixed_h
 // still scales Sigma in place of the adapted h), forms V from the totals of
-// the shifted sums and factors Sigma = h^2 V as h chol(V) by a right-looking
-// Cholesky in shared memory, done by the first warp; a non-positive pivot
-// zeroes its column, as in the oracle.
+// the shifted sums and factors Sigma = h^2 V as h chol(V), a non-positive
+// pivot zeroing its column, as in the oracle.  The factorisation runs on
+// S = D V D, D = diag(2^-m_i) with 2^(2 m_i) near V_ii (exact scaling, unit-
+// sized entries), in double-float arithmetic by the first warp with element
+// indices from a table; chol(V) = D^-1 chol(S).  A pivot of S below 1e-30
+// (relative to its unit-sized diagonal: far below the rounding of V's sums)
+// counts as zero.
 // The shift of the sums is shift_f[i] (FP32, the mutation tiles) when given,
 // else shift_in[i * shift_stride]; the pooled mean goes to mean_out (FP64)
-// and, rounded, to mean_f_out (the next tiles' shift; may be shift_f).
-// Every FP64 instruction of this part occupies its pipe for about 64 cycles
-// whatever the number of active lanes, so the serial chain is kept short:
-// the divisions and the step-size update run on separate warps while the
-// totals load, element indices come from a table, and each pivot costs three
-// FP64 instructions (below).
+// and, rounded, to mean_f_out (the next tiles' shift; may be shift_f).  The
+// divisions and the step-size update run on separate warps while the totals
+// load.
 constexpr int kMaxPair = kMaxD * (kMaxD + 1) / 2;
 
 __device__ void cov_final_body(const double* __restrict__ tot, int d, int P,
@@ -147,7 +202,9 @@ __device__ void cov_final_body(const double* __restrict__ tot, int d, int P,
 {
     __shared__ double S1[kMaxD];
     __shared__ double A[kMaxD][kMaxD + 1];
+    __shared__ Df F[kMaxD][kMaxD + 1];
     __shared__ double shift[kMaxD];
+    __shared__ int msc[kMaxD];
     __shared__ unsigned char pi_[kMaxPair], pk_[kMaxPair];
     __shared__ double hs, invP, invP1;
     const int npair = d * (d + 1) / 2;
@@ -184,40 +241,38 @@ __device__ void cov_final_body(const double* __restrict__ tot, int d, int P,
         const double mu = shift[i] + S1[i] * invP;
         if (mean_out) mean_out[i] = mu;
         if (mean_f_out) mean_f_out[i] = (float)mu;
+        // m_i = floor(e_i / 2) for V_ii = 2^e_i * 1.f (positive normal), else 0
+        const long long b = __double_as_longlong(A[i][i]);
+        msc[i] = (b > 0x000fffffffffffffLL && b < 0x7ff0000000000000LL) ? (((int)(b >> 52) - 1023) >> 1) : 0;
     }
     if (cov_out)
         for (int e = threadIdx.x; e < d * d; e += blockDim.x) cov_out[e] = A[e / d][e % d];
     __syncthreads();
+    for (int e = threadIdx.x; e < npair; e += blockDim.x) {
+        const int i = pi_[e], k = pk_[e];
+        const double sik = A[i][k] * pow2(-(msc[i] + msc[k]));
+        const float hi = __double2float_rn(sik);
+        F[i][k] = {hi, __double2float_rn(sik - (double)hi)};
+    }
+    __syncthreads();
     if (threadIdx.x < 32) {
-        // Pivot: y = piv^-1/2 from the FP32 reciprocal square root refined by
-        // one Newton step in FP64, y = y0 + (y0/2)(1 - piv y0^2): about 22
-        // correct bits become about 44 (1e-13 relative, far below what a
-        // proposal scale needs).  The column scaling and sqrt(piv) = piv y
-        // share one multiply across the lanes.
         const int lane = threadIdx.x;
         for (int j = 0; j < d; ++j) {
-            const double piv = A[j][j];
-            const long long pb = __double_as_longlong(piv);
-            double y = 0.0;
-            if (pb > 0 && pb < 0x7ff0000000000000LL) {   // positive and finite
-                const float y0f = rsqrtf((float)piv);
-                if (y0f > 0.0f && y0f < INFINITY) {
-                    const double y0 = (double)y0f;
-                    y = fma((double)(0.5f * y0f), fma(-piv * y0, y0, 1.0), y0);
-                } else {
-                    y = rsqrt(piv);   // pivot outside the FP32 range
-                }
-            }
+            const Df piv = F[j][j];
+            Df y = {0.0f, 0.0f};
+            if (piv.hi > 1e-30f) y = df_rsqrt(piv);
+            // lane j forms sqrt(piv) = piv y, lanes below it l_ij = s_ij y
             const bool col = lane >= j && lane < d;
-            const double v = col ? A[lane][j] * y : 0.0;
+            Df v = {0.0f, 0.0f};
+            if (col) v = df_mul(F[lane][j], y);
             __syncwarp();
-            if (col) A[lane][j] = v;
+            if (col) F[lane][j] = v;
             __syncwarp();
             const int m = d - j - 1;
             const int ne = m * (m + 1) / 2;
             for (int e = lane; e < ne; e += 32) {
                 const int ii = pi_[e] + j + 1, kk = pk_[e] + j + 1;
-                A[ii][kk] = fma(-A[ii][j], A[kk][j], A[ii][kk]);
+                F[ii][kk] = df_fms(F[ii][kk], F[ii][j], F[kk][j]);
             }
             __syncwarp();
         }
@@ -226,7 +281,7 @@ __device__ void cov_final_body(const double* __restrict__ tot, int d, int P,
     if (L_out)
         for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
             const int i = e / d, k = e % d;
-            L_out[e] = k <= i ? A[i][k] * hs : 0.0;
+            L_out[e] = k <= i ? ((double)F[i][k].hi + (double)F[i][k].lo) * (hs * pow2(msc[i])) : 0.0;
         }
 }
 
