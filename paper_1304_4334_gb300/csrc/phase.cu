@@ -522,7 +522,6 @@ constexpr int kSearchWarps = kSearchThreads / 32;
 constexpr int kCand = 32;
 constexpr int kRegTiles = 4;                      // tiles a warp keeps in registers
 constexpr float kFixScale = 68719476736.0f;       // 2^36
-constexpr double kFixInv2 = 1.0 / 68719476736.0;  // 2^-36
 
 int search_grid(int P)
 {
@@ -582,22 +581,24 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p)
     return v;
 }
 
-// Barrier over the blocks of a cooperative launch.  Arrivals count up to the
-// grid size; the last arrival resets the count and advances the generation.
-// The wait is bounded: on time-out (or when another block gave up) the abort
-// word is set and every block returns false.
+// Barrier over the blocks of a cooperative launch.  Arrivals (a release
+// add, ordering the block's earlier writes) count up to the grid size; the
+// last arrival resets the count and advances the generation (release), which
+// the others poll with acquire loads.  The wait is bounded: on time-out (or
+// when another block gave up) the abort word is set and every block returns
+// false.
 __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks)
 {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
-        __threadfence();
         const unsigned int gen = ld_acquire_u32(bar + 1);
-        if (atomicAdd(bar, 1u) + 1u == nblocks) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        unsigned int arrived;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
+        if (arrived + 1u == nblocks) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
         } else {
             const uint64_t t0 = global_ns();
             while (ld_acquire_u32(bar + 1) == gen) {
@@ -608,7 +609,6 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks)
                 }
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return ok != 0;
@@ -636,14 +636,15 @@ __global__ void __launch_bounds__(kSearchThreads, 1) k_power_search(const double
 {
     __shared__ long long skey[kSearchWarps];
     __shared__ unsigned long long sacc[2 * kCand];
-    __shared__ double s_lo, s_hi, s_dphi;
-    __shared__ int s_done, s_last, s_pass;
+    __shared__ double scand[kCand];
+    __shared__ float sdc[kCand];
     const int G = gridDim.x;
     const SearchScratch sc = search_scratch(part, G);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ntiles = (P + 31) / 32;
     const int nw = G * kSearchWarps;
     const int gw = blockIdx.x * kSearchWarps + warp;
+    const double phi = ctl->phi;
     if (threadIdx.x < 2 * kCand) sacc[threadIdx.x] = 0ull;
     if (blockIdx.x == 0 && threadIdx.x < 2 * kCand) sc.acc[threadIdx.x] = 0ull;   // slot of pass 0
 
@@ -674,12 +675,12 @@ __global__ void __launch_bounds__(kSearchThreads, 1) k_power_search(const double
         if (threadIdx.x == 0) raise_error(&ctl->err, kErrTimeout);
         return;
     }
-    long long kg = kNegInfKey;
-    for (int b = lane; b < G; b += 32) {
-        const long long k = __ldcg(sc.bkey + b);
-        kg = k > kg ? k : kg;
-    }
+    // every block reads the G block maxima, one per thread (G <= SMs)
+    long long kg = (int)threadIdx.x < G ? __ldcg(sc.bkey + threadIdx.x) : kNegInfKey;
     kg = warp_max_key(kg);
+    if (lane == 0) skey[warp] = kg;
+    __syncthreads();
+    kg = warp_max_key(lane < kSearchWarps ? skey[lane] : kNegInfKey);
     const double llmax = key_value(kg);
 
     // ---- shifted FP32 log likelihoods: registers, then scratch ----
@@ -697,21 +698,41 @@ __global__ void __launch_bounds__(kSearchThreads, 1) k_power_search(const double
         }
     }
 
-    double lo = 0.0, hi = 1.0 - ctl->phi, dphi = hi;
+    double lo = 0.0, hi = 1.0 - phi, dphi = hi;
     int done = (kg == kNegInfKey) || !(hi > 0.0);
     int last = done, pass = 0;
+    // RSS < D1 compared as (Q1 2^-32)^2 < D1 P 2^4 (Q2 2^-32) in FP32: the
+    // fixed-point totals carry 2^-36 units, and FP32 resolves RSS to 1e-7,
+    // far inside the error of the FP32 weights themselves.
+    const float cmp = (float)(d1 * (double)P * 16.0);
     for (int p = 0; p < passes && !done; ++p) {
         const int slot = p % 3;
-        const float dc = (float)(candidate(lo, hi, lane) * kLog2e);
+        // candidates (FP64) and their FP32 exponent scale, once per block
+        if (warp == 0) {
+            const double cv = candidate(lo, hi, lane);
+            scand[lane] = cv;
+            sdc[lane] = (float)(cv * kLog2e);
+        }
+        __syncthreads();
+        const float dc = sdc[lane];
         unsigned long long q1 = 0ull, q2 = 0ull;
         auto tile = [&](float x) {
+            // eight shuffles and exponentials issued before their eight
+            // additions (the sums still run j = 0, 1, .., 31)
             float a1 = 0.0f, a2 = 0.0f;
-#pragma unroll 8
-            for (int j = 0; j < 32; ++j) {
-                const float xj = __shfl_sync(0xffffffffu, x, j);
-                const float w = xj == -INFINITY ? 0.0f : ex2_approx(dc * xj);
-                a1 += w;
-                a2 = fmaf(w, w, a2);
+#pragma unroll
+            for (int j0 = 0; j0 < 32; j0 += 8) {
+                float w[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float xj = __shfl_sync(0xffffffffu, x, j0 + u);
+                    w[u] = xj == -INFINITY ? 0.0f : ex2_approx(dc * xj);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    a1 += w[u];
+                    a2 = fmaf(w[u], w[u], a2);
+                }
             }
             q1 += __float2ull_rn(a1 * kFixScale);
             q2 += __float2ull_rn(a2 * kFixScale);
@@ -737,42 +758,28 @@ __global__ void __launch_bounds__(kSearchThreads, 1) k_power_search(const double
             if (threadIdx.x == 0) raise_error(&ctl->err, kErrTimeout);
             return;
         }
-        if (warp == 0) {
-            const double Q1 = (double)__ldcg(sc.acc + slot * 2 * kCand + lane);
-            const double Q2 = (double)__ldcg(sc.acc + slot * 2 * kCand + kCand + lane);
-            // RSS < D1 with RSS = (Q1 2^-36)^2 / (P Q2 2^-36)
-            const unsigned below = __ballot_sync(0xffffffffu, Q1 * Q1 * kFixInv2 < d1 * (double)P * Q2);
-            if (lane == 0) {
-                if (below == 0u) {
-                    // RSS stays >= D1 up to hi: in the first pass this takes the
-                    // whole remaining power (the last cycle); later it cannot
-                    // occur because hi was itself a candidate with RSS < D1.
-                    s_dphi = hi;
-                    s_done = 1;
-                    s_last = pass == 0;
-                    s_lo = lo;
-                    s_hi = hi;
-                    s_pass = pass;
-                } else {
-                    const int cc = __ffs(below) - 1;
-                    const double nhi = candidate(lo, hi, cc);
-                    s_lo = cc == 0 ? lo : candidate(lo, hi, cc - 1);
-                    s_hi = nhi;
-                    s_dphi = nhi;
-                    s_pass = pass + 1;
-                    s_done = s_pass >= passes;
-                    s_last = 0;
-                }
-            }
+        // every warp takes the same decision from the same totals
+        const float q1s = __ull2float_rn(__ldcg(sc.acc + slot * 2 * kCand + lane)) * 2.3283064365386963e-10f;
+        const float q2s = __ull2float_rn(__ldcg(sc.acc + slot * 2 * kCand + kCand + lane)) * 2.3283064365386963e-10f;
+        const unsigned below = __ballot_sync(0xffffffffu, q1s * q1s < cmp * q2s);
+        if (below == 0u) {
+            // RSS stays >= D1 up to hi: in the first pass this takes the whole
+            // remaining power (the last cycle); later it cannot occur because
+            // hi was itself a candidate with RSS < D1.
+            dphi = hi;
+            done = 1;
+            last = pass == 0;
+        } else {
+            const int cc = __ffs(below) - 1;
+            const double nlo = cc == 0 ? lo : scand[cc - 1];
+            hi = scand[cc];
+            lo = nlo;
+            dphi = hi;
+            pass += 1;
+            done = pass >= passes;
+            last = 0;
         }
-        __syncthreads();
-        lo = s_lo;
-        hi = s_hi;
-        dphi = s_dphi;
-        done = s_done;
-        last = s_last;
-        pass = s_pass;
-        __syncthreads();
+        __syncthreads();   // scand is rewritten by the next pass
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->llmax = llmax;
