@@ -374,13 +374,15 @@ static cudaError_t dalloc(T** p, size_t n)
     return cudaMalloc((void**)p, (n ? n : 1) * sizeof(T));
 }
 
-static smc_status check_device_error(smc_ctx* ctx)
+static smc_status check_device_error(smc_ctx* ctx, const Ctl& h)
 {
-    if (ctx->ctl_host->err & kErrTimeout) return set_err(ctx, SMC_ETIMEOUT, "a bounded device wait ran out");
-    if (ctx->ctl_host->err & kErrDegenerate) return set_err(ctx, SMC_EDEGENERATE, "a group has zero total weight");
-    if (ctx->ctl_host->err & kErrBounds) return set_err(ctx, SMC_ECUDA, "internal index check failed");
+    if (h.err & kErrTimeout) return set_err(ctx, SMC_ETIMEOUT, "a bounded device wait ran out");
+    if (h.err & kErrDegenerate) return set_err(ctx, SMC_EDEGENERATE, "a group has zero total weight");
+    if (h.err & kErrBounds) return set_err(ctx, SMC_ECUDA, "internal index check failed");
     return SMC_OK;
 }
+
+static smc_status check_device_error(smc_ctx* ctx) { return check_device_error(ctx, *ctx->ctl_host); }
 
 static smc_status sync_ctl(smc_ctx* ctx)
 {
@@ -659,8 +661,10 @@ smc_status smc_internal_enqueue_adapt(smc_ctx* ctx)
     return SMC_OK;
 }
 
-smc_status smc_internal_after_m(smc_ctx* ctx, int t_l, int R, int Tm, double phim, double rss,
-                                smc_cycle_info* info)
+// Host bookkeeping at the end of an M phase from the control block h read
+// back after it; `cycle` is the cycle that ends.
+static smc_status after_m_from(smc_ctx* ctx, const Ctl& h, int cycle, int t_l, int R, int Tm, double phim,
+                               double rss, smc_cycle_info* info)
 {
     const smc_config& c = ctx->cfg;
     const int P = ctx->P;
@@ -669,25 +673,31 @@ smc_status smc_internal_after_m(smc_ctx* ctx, int t_l, int R, int Tm, double phi
         if (st != SMC_OK) return st;
     }
     if (ctx->record) {
-        ctx->design_x.push_back(c.tempering == SMC_POWER ? ctx->ctl_host->phi : (double)t_l);
+        ctx->design_x.push_back(c.tempering == SMC_POWER ? h.phi : (double)t_l);
         ctx->design_R.push_back(R);
     }
     ctx->t_prev = t_l;
     ctx->msteps += R;
     ctx->evals += (double)R * (double)P * (double)Tm;
-    if (c.tempering == SMC_POWER ? ctx->ctl_host->last : (t_l >= ctx->T)) ctx->done = 1;
+    if (c.tempering == SMC_POWER ? h.last : (t_l >= ctx->T)) ctx->done = 1;
     if (info) {
-        info->cycle = ctx->cycle;
+        info->cycle = cycle;
         info->t = t_l;
         info->phi = phim;
         info->rss = rss;
         info->R = R;
-        info->h_tenths = ctx->ctl_host->h_tenths;
-        info->acc_rate = ctx->ctl_host->acc_n ? ctx->ctl_host->acc_sum / ctx->ctl_host->acc_n : 0.0;
+        info->h_tenths = h.h_tenths;
+        info->acc_rate = h.acc_n ? h.acc_sum / h.acc_n : 0.0;
         info->evals = (double)R * (double)P * (double)Tm;
         info->done = ctx->done;
     }
     return SMC_OK;
+}
+
+smc_status smc_internal_after_m(smc_ctx* ctx, int t_l, int R, int Tm, double phim, double rss,
+                                smc_cycle_info* info)
+{
+    return after_m_from(ctx, *ctx->ctl_host, ctx->cycle, t_l, R, Tm, phim, rss, info);
 }
 
 extern "C" {
@@ -822,7 +832,7 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
     }
     if (c->mutation == SMC_INDEP) CU(dalloc(&ctx->lq, Ps));
     CU(dalloc(&ctx->ctl, 1));
-    CU(cudaMallocHost((void**)&ctx->ctl_host, sizeof(Ctl)));
+    CU(cudaMallocHost((void**)&ctx->ctl_host, 2 * sizeof(Ctl)));
 
     // gather tables: rows of theta, ll, lp, state for both directions
     const int ng = c->mutation == SMC_MALA ? d : 0;
@@ -1136,6 +1146,45 @@ smc_status smc_mutate_time(smc_ctx* ctx, double* ms, uint64_t* launches, int res
     return SMC_OK;
 }
 
+// M phase of the current cycle (Algorithm 1, 2(c)): R Metropolis
+// iterations, R from the stopping rule (the RNE rule reads the control block
+// back after every iteration and may stop earlier), then the step-size update
+// of the last iteration.  *ran = iterations run.  Enqueues only, apart from the
+// RNE rule's read-backs.
+static smc_status m_phase(smc_ctx* ctx, int Tm, double phim, double rss, int forced, int* ran)
+{
+    const smc_config& c = ctx->cfg;
+    smc_status st;
+    if (c.h_reset_each_cycle) {
+        // the pending count (if any) was applied at the end of the last M phase
+        int h0 = c.h0_tenths;
+        CU(cudaMemcpyAsync(&ctx->ctl->h_tenths, &h0, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    if (c.mutation == SMC_MALA && c.tempering == SMC_DATA) {
+        st = refresh_gradient(ctx, Tm);
+        if (st != SMC_OK) return st;
+    }
+    const int R = ctx->replay ? ctx->design_R[ctx->cycle - 1] : smc_internal_R(ctx, rss);
+    const double E = forced ? c.e2 : c.e1;
+    int r = 0;
+    for (; r < R; ++r) {
+        st = m_iteration(ctx, r, Tm, phim);
+        if (st != SMC_OK) return st;
+        if (c.stop_rule == SMC_STOP_RNE) {
+            st = test_functions(ctx, 1);
+            if (st != SMC_OK) return st;
+            st = sync_ctl(ctx);
+            if (st != SMC_OK) return st;
+            if (ctx->ctl_host->mean_rne >= E) {
+                ++r;
+                break;
+            }
+        }
+    }
+    *ran = r;
+    return smc_internal_enqueue_adapt(ctx);
+}
+
 smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
 {
     if (!ctx) return SMC_EINVAL;
@@ -1214,42 +1263,71 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
     // ---- M phase ----
     const double phim = c.tempering == SMC_POWER ? ctx->phi : 1.0;
     const int Tm = c.tempering == SMC_POWER ? ctx->T : t_l;
-    if (c.h_reset_each_cycle) {
-        // the pending count (if any) was applied at the end of the last M phase
-        int h0 = c.h0_tenths;
-        CU(cudaMemcpyAsync(&ctx->ctl->h_tenths, &h0, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
-    }
-    if (c.mutation == SMC_MALA && c.tempering == SMC_DATA) {
-        st = refresh_gradient(ctx, Tm);
-        if (st != SMC_OK) return st;
-    }
-    const int R = ctx->replay ? ctx->design_R[ctx->cycle - 1] : smc_internal_R(ctx, rss);
-    const double E = forced ? c.e2 : c.e1;
     int r = 0;
-    for (; r < R; ++r) {
-        st = m_iteration(ctx, r, Tm, phim);
-        if (st != SMC_OK) return st;
-        if (c.stop_rule == SMC_STOP_RNE) {
-            st = test_functions(ctx, 1);
-            if (st != SMC_OK) return st;
-            st = sync_ctl(ctx);
-            if (st != SMC_OK) return st;
-            if (ctx->ctl_host->mean_rne >= E) {
-                ++r;
-                break;
-            }
-        }
-    }
-    st = smc_internal_enqueue_adapt(ctx);
+    st = m_phase(ctx, Tm, phim, rss, forced, &r);
     if (st != SMC_OK) return st;
     st = sync_ctl(ctx);
     if (st != SMC_OK) return st;
     return smc_internal_after_m(ctx, t_l, r, Tm, phim, rss, info);
 }
 
+// Power tempering, cycle after cycle with one host round trip per cycle:
+// while the run goes on, the next cycle's C and S phases are enqueued right
+// behind this cycle's M phase, and one synchronisation returns both the
+// M phase's control block (ctl_host[1]) and the next C phase's (ctl_host[0]).
+// The kernels and their order are those of smc_cycle; only the host waits
+// differently.
+static smc_status run_power_pipelined(smc_ctx* ctx, int max_cycles, smc_cycle_info* info, int* ncycles)
+{
+    int n = 0;
+    smc_cycle_info ci;
+    std::memset(&ci, 0, sizeof ci);
+    Ctl* hm = ctx->ctl_host + 1;
+    bool have_cs = false;   // this cycle's C and S phases are enqueued and read back
+    double rss = 1.0;
+    int forced = 0;
+    smc_status st = SMC_OK;
+    while (!ctx->done && (max_cycles <= 0 || n < max_cycles)) {
+        if (!have_cs) {
+            st = smc_internal_enqueue_cs(ctx);
+            if (st != SMC_OK) break;
+            st = sync_ctl(ctx);
+            if (st != SMC_OK) break;
+            smc_internal_after_cs(ctx, &rss, &forced);
+        }
+        const int cycle = ctx->cycle;
+        const double phim = ctx->phi;
+        int r = 0;
+        st = m_phase(ctx, ctx->T, phim, rss, forced, &r);
+        if (st != SMC_OK) break;
+        CU(cudaMemcpyAsync(hm, ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+        ctx->d2h += sizeof(Ctl);
+        // forced = this C phase took the remaining power (the last cycle)
+        have_cs = !forced && (max_cycles <= 0 || n + 1 < max_cycles);
+        if (have_cs) {
+            st = smc_internal_enqueue_cs(ctx);
+            if (st != SMC_OK) break;
+            st = smc_internal_enqueue_ctl_readback(ctx);
+            if (st != SMC_OK) break;
+        }
+        CU(cudaStreamSynchronize(ctx->stream));
+        // the error word is sticky: the later read-back carries every error
+        st = check_device_error(ctx, have_cs ? *ctx->ctl_host : *hm);
+        if (st != SMC_OK) break;
+        st = after_m_from(ctx, *hm, cycle, ctx->T, r, ctx->T, phim, rss, &ci);
+        if (st != SMC_OK) break;
+        ++n;
+        if (have_cs) smc_internal_after_cs(ctx, &rss, &forced);
+    }
+    if (info) *info = ci;
+    if (ncycles) *ncycles = n;
+    return st;
+}
+
 smc_status smc_run(smc_ctx* ctx, int max_cycles, smc_cycle_info* info, int* ncycles)
 {
     if (!ctx) return SMC_EINVAL;
+    if (ctx->cfg.tempering == SMC_POWER && !ctx->done) return run_power_pipelined(ctx, max_cycles, info, ncycles);
     int n = 0;
     smc_cycle_info ci;
     std::memset(&ci, 0, sizeof ci);

@@ -60,7 +60,7 @@ struct smc_ctx {
     double** gather_ptrs = nullptr;  // [2][nrows] device row-pointer tables
     int gather_rows = 0;
     Ctl* ctl = nullptr;
-    Ctl* ctl_host = nullptr;         // pinned
+    Ctl* ctl_host = nullptr;         // pinned, two blocks: [0] the latest read-back, [1] the M phase's (pipelined runs)
     // run state
     int cycle = 0, t_prev = 0, done = 0;
     double phi = 0.0;
