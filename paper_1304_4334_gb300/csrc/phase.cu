@@ -99,6 +99,8 @@ __device__ void cov_partial_body(const double* __restrict__ theta, int d, int P,
 __global__ void __launch_bounds__(kCovThreads) k_cov_partial(const double* __restrict__ theta, int d,
                                                             int P, double* __restrict__ part)
 {
+    pdl_trigger();
+    pdl_wait();
     cov_partial_body(theta, d, P, part, blockIdx.x, gridDim.x);
 }
 
@@ -442,14 +444,16 @@ cudaError_t launch_cov(const double* theta, int d, int P, double* part, int G, u
                        Ctl* ctl, int fixed_h_tenths, double acc_target, int hmin, int hmax, double* mean,
                        double* cov, double* L, cudaStream_t s, float* mean_f)
 {
-    k_cov_partial<<<G, kCovThreads, 0, s>>>(theta, d, P, part);
+    cudaError_t e = pdl_launch(k_cov_partial, dim3(G), dim3(kCovThreads), 0, s, theta, d, P, part);
     count_launch();
+    if (e != cudaSuccess) return e;
     const int nacc = d + d * (d + 1) / 2;
     const CovFinalArgs f{d, P, theta, (long long)P, nullptr, ctl, fixed_h_tenths, acc_target, hmin, hmax,
                          mean, mean_f, cov, L, 0};
-    k_cov_reduce<false><<<nacc, kCovThreads, 0, s>>>(part, G, nacc, part + (size_t)G * nacc, counter, f);
+    e = pdl_launch(k_cov_reduce<false>, dim3(nacc), dim3(kCovThreads), 0, s, (const void*)part, G, nacc,
+                   part + (size_t)G * nacc, counter, f);
     count_launch();
-    return cudaGetLastError();
+    return e;
 }
 
 // ----- covariance from the mutation kernel's 32-particle tiles -----
@@ -845,6 +849,7 @@ __device__ int upper_bound_u64(const uint64_t* a, int n, uint64_t u)
 
 __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
 {
+    pdl_trigger();   // the gather may launch and wait while this runs
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int N = a.N;
     double* ws = reinterpret_cast<double*>(sm_raw);                        // w, then q, then prefix r
@@ -1025,6 +1030,8 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t s)
 
 __global__ void k_gather(GatherArgs a)
 {
+    pdl_trigger();
+    pdl_wait();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.P) return;
     const int j = s / a.N;
@@ -1034,9 +1041,9 @@ __global__ void k_gather(GatherArgs a)
 
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s)
 {
-    k_gather<<<(a.P + 255) / 256, 256, 0, s>>>(a);
+    const cudaError_t e = pdl_launch(k_gather, dim3((a.P + 255) / 256), dim3(256), 0, s, a);
     count_launch();
-    return cudaGetLastError();
+    return e;
 }
 
 __global__ void k_cdata_select(const double* part, int G, int B, int s0, int T, int P, double d1,
@@ -1116,6 +1123,8 @@ cudaError_t launch_cdata_select(const double* part, int G, int B, int s0, int T,
 // log wtilde += log(J^-1 sum_j wbar_j(l-1)), and phi += dphi.
 __global__ void k_cycle_close(const double* gstat, const double* lw, int J, int N, int power, Ctl* ctl)
 {
+    pdl_trigger();
+    pdl_wait();
     const int lane = threadIdx.x;
     double M = -INFINITY;
     for (int j = lane; j < J; j += 32) M = fmax(M, gstat[3 * j]);
@@ -1146,9 +1155,9 @@ __global__ void k_cycle_close(const double* gstat, const double* lw, int J, int 
 cudaError_t launch_cycle_close(const double* gstat, const double* lw, int J, int N, int power,
                                Ctl* ctl, cudaStream_t s)
 {
-    k_cycle_close<<<1, 32, 0, s>>>(gstat, lw, J, N, power, ctl);
+    const cudaError_t e = pdl_launch(k_cycle_close, dim3(1), dim3(32), 0, s, gstat, lw, J, N, power, ctl);
     count_launch();
-    return cudaGetLastError();
+    return e;
 }
 
 // ===================================================== moments and estimators
