@@ -228,14 +228,17 @@ smc_status smc_design_replay(smc_ctx* ctx, int ncycles, const double* x, const i
  * Blackwell's paired FP32 instructions (one issue slot for both; results
  * bitwise those of one particle per thread).
  * smc_autotune times `iters` Metropolis iterations of each candidate shape
- * (random walk: 1 particle x 128, 64 or 32 threads per block; FP32 EGARCH
- * also 2 particles x 32, 64 or 128 threads, the pair's recursions in packed
- * FP32x2 instructions; MALA: 1 x 128 only) on a snapshot of the particles,
- * restores them, and keeps the fastest; outputs (host, nullable): the shape and
- * its time per iteration.  Results do not depend on the shape.
- * Smaller blocks split P particles into more blocks, which evens the load over
- * the SMs when P / threads is not a multiple of the SM count.
- * smc_set_launch_shape sets one directly (SMC_EINVAL for any other shape). */
+ * (random walk: 1 particle x 128, 64 or 32 threads per block, and the
+ * balanced block below; FP32 EGARCH also 2 particles x 32, 64, 128 threads and
+ * balanced, the pair's recursions in packed FP32x2 instructions; MALA: 1 x 128
+ * only) on a snapshot of the particles, restores them, and keeps the fastest;
+ * outputs (host, nullable): the shape and its time per iteration.  Results do
+ * not depend on the shape.  The balanced block spreads the particles' warps
+ * as evenly as possible over the SMs: 32 ceil(W / (S k)) threads for W warps,
+ * S SMs and the fewest blocks per SM k that keep it within 224 threads.
+ * smc_set_launch_shape sets one directly: ppt 1 or 2 (2 for the FP32 EGARCH
+ * random walk only), threads a multiple of 32 from 32 to 224; SMC_EINVAL
+ * otherwise. */
 smc_status smc_autotune(smc_ctx* ctx, int iters, int* ppt, int* threads, double* ms_per_iteration);
 smc_status smc_set_launch_shape(smc_ctx* ctx, int ppt, int threads);
 

@@ -50,9 +50,26 @@ cudaError_t launch_mutate_x2_f32_k2(const MutateArgs& a, int threads, cudaStream
 cudaError_t launch_mutate_x2_f32_k3(const MutateArgs& a, int threads, cudaStream_t s);
 cudaError_t launch_mutate_x2_f32_k4(const MutateArgs& a, int threads, cudaStream_t s);
 
+static bool valid_mut_threads(int t) { return t >= 32 && t <= kMutMaxThreads && t % 32 == 0; }
+
+// Block size that spreads P particles (ppt per thread) most evenly over the
+// SMs: the fewest blocks per SM k for which ceil(warps / (SMs k)) warps fit in
+// one block.  At 65,536 particles, two per thread, on 152 SMs: 7 warps, one
+// block per SM, where 64-thread blocks leave 56 SMs with 8 warps and 96 with 6.
+static int balanced_threads(int P, int ppt)
+{
+    const int warps = (P + 32 * ppt - 1) / (32 * ppt);
+    const int sms = device_sm_count();
+    for (int k = 1; k <= 64; ++k) {
+        const int b = (warps + sms * k - 1) / (sms * k);
+        if (b <= kMutMaxThreads / 32) return 32 * b;
+    }
+    return kMutMaxThreads;
+}
+
 cudaError_t launch_mutate_x2(const MutateArgs& a, int threads, cudaStream_t s)
 {
-    if (a.qmean) return cudaErrorInvalidValue;   // random walk only
+    if (a.qmean || !valid_mut_threads(threads)) return cudaErrorInvalidValue;   // random walk only
     count_launch();
     switch (a.m.K) {
     case 1: return launch_mutate_x2_f32_k1(a, threads, s);
@@ -88,7 +105,7 @@ cudaError_t launch_cdata(const CdataArgs& a, int precision, cudaStream_t s)
 cudaError_t launch_mutate(const MutateArgs& a, int precision, int threads, cudaStream_t s)
 {
     count_launch();
-    if (threads != 32 && threads != 64 && threads != kMutThreads) return cudaErrorInvalidValue;
+    if (!valid_mut_threads(threads)) return cudaErrorInvalidValue;
     if (a.m.kind == SMC_LINREG) return launch_mutate_linreg(a, threads, s);
     if (precision == SMC_FP32) {
         switch (a.m.K) {
@@ -521,9 +538,7 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
     a.err = &ctx->ctl->err;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool timed = ctx->profile == 1 || (ctx->profile == 2 && r == 0);
-    // a timed launch sits between two events, which serialise it anyway: it
-    // is launched plainly so that the events bracket the kernel alone
-    a.dependent = timed ? 0 : 1;
+    a.dependent = 0;   // see MutateArgs::dependent
     if (timed) {
         e0 = take_event(ctx);
         e1 = take_event(ctx);
@@ -983,14 +998,21 @@ smc_status smc_autotune(smc_ctx* ctx, int iters, int* ppt, int* threads, double*
     const Ctl saved = *ctx->ctl_host;
     struct Shape { int ppt, threads; };
     std::vector<Shape> cand = {{1, kMutThreads}};
+    auto add = [&](int pp, int t) {
+        for (const Shape& c : cand)
+            if (c.ppt == pp && c.threads == t) return;
+        cand.push_back({pp, t});
+    };
     if (ctx->cfg.mutation != SMC_MALA) {
-        cand.push_back({1, 64});
-        cand.push_back({1, 32});
+        add(1, 64);
+        add(1, 32);
+        add(1, balanced_threads(P, 1));
     }
     if (fp32_egarch) {
-        cand.push_back({2, 32});
-        cand.push_back({2, 64});
-        cand.push_back({2, 128});
+        add(2, 32);
+        add(2, 64);
+        add(2, 128);
+        add(2, balanced_threads(P, 2));
     }
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
@@ -1043,8 +1065,7 @@ smc_status smc_autotune(smc_ctx* ctx, int iters, int* ppt, int* threads, double*
 
 smc_status smc_set_launch_shape(smc_ctx* ctx, int ppt, int threads)
 {
-    if (!ctx || ppt < 1 || ppt > 2 || (threads != 32 && threads != 64 && threads != kMutThreads))
-        return SMC_EINVAL;
+    if (!ctx || ppt < 1 || ppt > 2 || !valid_mut_threads(threads)) return SMC_EINVAL;
     if (ppt == 2 && !(ctx->model.model == SMC_EGARCH && ctx->cfg.precision == SMC_FP32 &&
                       ctx->cfg.mutation == SMC_RW))
         return set_err(ctx, SMC_EINVAL, "two particles per thread needs the FP32 EGARCH random walk");

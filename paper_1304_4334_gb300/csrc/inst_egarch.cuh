@@ -8,7 +8,7 @@ namespace smc {
 
 inline int mutate_grid(int P, int threads = kMutThreads) { return (P + threads - 1) / threads; }
 
-// One particle per thread; threads = 32, 64 or 128 per block (the caller checks).
+// One particle per thread; threads = a multiple of 32 up to kMutMaxThreads (the caller checks).
 template <template <int, int> class Pol, int K>
 cudaError_t launch_mutate_k(const MutateArgs& a, int threads, cudaStream_t s)
 {

@@ -47,6 +47,9 @@ struct MutateArgs {
     int* err;
     // Host-side launch choice: nonzero launches the kernel as a programmatic
     // dependent of the preceding kernel (its blocks become resident early).
+    // The run leaves it off: blocks placed while the covariance step still
+    // occupies the SMs land unevenly, and the kernel runs as long as its most
+    // loaded SM (measured up to 35% slower).
     int dependent = 0;
 };
 
@@ -63,6 +66,17 @@ struct LoglikArgs {
 };
 
 constexpr int kMutThreads = 128;
+// Largest mutation block (threads, a multiple of 32): any multiple of 32 up to
+// this is a valid launch shape, so that P particles can be spread as evenly
+// as the warp granularity allows over the SMs.  The launch bounds also steer
+// the register allocation, and with it the speed (measured on the FP32
+// EGARCH(2,2) kernels, 65,536 particles in 224-thread blocks): one particle
+// per thread is fastest compiled for 256-thread blocks (48 registers,
+// 0.282 ms per launch against 0.292 ms with 56 registers under a 224 or
+// 128 bound, 0.288 ms at a 64-register cap), two per thread for 224 (111
+// registers, 0.297 ms; 80 registers under a 256 bound: 0.307 ms).
+constexpr int kMutMaxThreads = 224;
+constexpr int kMutBoundX1 = 256;
 
 // Probability integral transform draw (Section 4.1): the standardized shock
 // of Y_s ~ p(Y_s | y_1:s-1, theta), location + scale * e, so that
@@ -377,7 +391,7 @@ __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, 
 }
 
 template <class Pol, bool kIndep = false>
-__global__ void __launch_bounds__(kMutThreads) k_mutate(MutateArgs a)
+__global__ void __launch_bounds__(kMutBoundX1) k_mutate(MutateArgs a)
 {
     __shared__ MutateSmem<Pol> sm;
     mutate_tile<Pol, kIndep>(a, a.iter, blockIdx.x * blockDim.x, sm);
@@ -460,7 +474,7 @@ __device__ __forceinline__ void mutate_tile_x2(const MutateArgs& a, uint64_t ite
 }
 
 template <int K, int I>
-__global__ void __launch_bounds__(kMutThreads) k_mutate_x2(MutateArgs a)
+__global__ void __launch_bounds__(kMutMaxThreads) k_mutate_x2(MutateArgs a)
 {
     __shared__ MutateSmem<PolicyEgarchF32<K, I>> sm;
     mutate_tile_x2<K, I>(a, a.iter, blockIdx.x * 2 * blockDim.x, sm);

@@ -252,9 +252,9 @@ def test_rne_stopping_rule_run(S):
 
 
 def test_launch_shapes_give_identical_runs(S):
-    """Every launch shape (32-, 64- or 128-thread blocks, one or two particles
-    per thread) computes each particle's proposal, recursion and decision
-    exactly as one particle per thread in 128-thread blocks."""
+    """Every launch shape (blocks of any multiple of 32 threads up to 224, one
+    or two particles per thread) computes each particle's proposal, recursion
+    and decision exactly as one particle per thread in 128-thread blocks."""
     truth = I.WORKLOADS["egarch22_T5000"].truth
     y = I.simulate_egarch(truth, 700, seed=8)
     m = S.model_egarch(2, 2, True)
@@ -262,7 +262,7 @@ def test_launch_shapes_give_identical_runs(S):
     J, N = 16, 300   # P = 4800: ragged against 64/128/256-particle tiles
     th0 = I.draw_prior(mean, sd, lo, J * N, seed=9)
     out = []
-    shapes = [(1, 128), (1, 64), (1, 32), (2, 32), (2, 64), (2, 128)]
+    shapes = [(1, 128), (1, 64), (1, 32), (2, 32), (2, 64), (2, 128), (1, 96), (2, 224), (1, 224), (2, 160)]
     for ppt, thr in shapes:
         ctx = S.init(m, S.config_default(J=J, N=N, precision=S.FP32, seed=5), y, th0)
         ctx.set_launch_shape(ppt, thr)
@@ -275,34 +275,35 @@ def test_launch_shapes_give_identical_runs(S):
         np.testing.assert_allclose(ll, out[0][1][1], rtol=1e-12)
     ctx = S.init(m, S.config_default(J=J, N=N, precision=S.FP32, seed=5), y, th0)
     ppt, thr, ms = ctx.autotune(iters=1)
-    assert (ppt, thr) in shapes and ms > 0
+    assert ppt in (1, 2) and thr % 32 == 0 and 32 <= thr <= 224 and ms > 0
     ctx.run()
     assert ctx.log_ml()[0] == pytest.approx(out[0][0][0], rel=1e-12, abs=1e-9)
     ctx.close()
 
 
 def test_small_blocks_fp64_and_invalid_shapes(S):
-    """FP64 runs give the same particles with 32-thread blocks; shapes outside
-    the supported set are rejected."""
+    """FP64 runs give the same particles with 32- and 96-thread blocks; shapes
+    outside the supported set are rejected."""
     truth = I.WORKLOADS["egarch11_T500"].truth
     y = I.simulate_egarch(truth, 300, seed=2)
     m = S.model_egarch(1, 1, False)
     mean, sd, lo = S.model_prior(m)
     th0 = I.draw_prior(mean, sd, lo, 4 * 100, seed=3)
     out = []
-    for thr in (128, 32):
+    for thr in (128, 32, 96):
         ctx = S.init(m, S.config_default(J=4, N=100, precision=S.FP64, seed=1), y, th0)
         ctx.set_launch_shape(1, thr)
         for _ in range(3):
             ctx.cycle()
         out.append(ctx.particles())
         if thr == 32:
-            for bad in [(1, 96), (2, 32), (3, 64)]:   # FP64 has no paired shape
+            for bad in [(1, 100), (1, 256), (1, 0), (2, 32), (3, 64)]:   # FP64 has no paired shape
                 with pytest.raises(S.SMCError):
                     ctx.set_launch_shape(*bad)
         ctx.close()
-    np.testing.assert_array_equal(out[0][0], out[1][0])
-    np.testing.assert_array_equal(out[0][1], out[1][1])
+    for o in out[1:]:
+        np.testing.assert_array_equal(out[0][0], o[0])
+        np.testing.assert_array_equal(out[0][1], o[1])
 
 
 # ---------------------------------------------- log score and PIT (Section 4.1)
