@@ -38,7 +38,7 @@ MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT_GB300 = 152
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per k_mutate launch, by
 # (workload, particles per thread, threads per block)
-MUTATE_TRAFFIC = {("egarch22_T5000", 2, 64): 8_684_288 + 33_280}
+MUTATE_TRAFFIC = {("egarch22_T5000", 2, 64): 8_684_288 + 33_280, ("egarch22_T5000", 1, 224): 8_762_368 + 299_264}
 SM_MAX_MHZ_FALLBACK = 2070.0
 L2_FLUSH_BYTES = 256 << 20
 
