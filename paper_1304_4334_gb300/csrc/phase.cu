@@ -847,6 +847,46 @@ __device__ int upper_bound_u64(const uint64_t* a, int n, uint64_t u)
     return lo < n ? lo : n - 1;
 }
 
+// Block maximum of 64-bit keys (every thread receives it).
+__device__ __forceinline__ long long block_max_key(long long k, long long* red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    k = warp_max_key(k);
+    __syncthreads();
+    if (lane == 0) red[warp] = k;
+    __syncthreads();
+    k = warp_max_key(lane < (int)(blockDim.x >> 5) ? red[lane] : kNegInfKey);
+    return k;
+}
+
+// Block sums of a and b (every thread receives them) by a pairwise tree over
+// shared memory, in a fixed order; blockDim.x = kSelThreads.
+__device__ __forceinline__ void block_sum_tree2(double& a, double& b, double* t1, double* t2)
+{
+    const int tid = threadIdx.x;
+    t1[tid] = a;
+    t2[tid] = b;
+    __syncthreads();
+#pragma unroll
+    for (int h = kSelThreads / 2; h >= 32; h >>= 1) {
+        if (tid < h) {
+            t1[tid] += t1[tid + h];
+            t2[tid] += t2[tid + h];
+        }
+        __syncthreads();
+    }
+    if (tid < 32) {
+        double x = warp_sum(t1[tid]), y = warp_sum(t2[tid]);
+        if (tid == 0) {
+            t1[0] = x;
+            t2[0] = y;
+        }
+    }
+    __syncthreads();
+    a = t1[0];
+    b = t2[0];
+}
+
 __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
 {
     pdl_trigger();   // the gather may launch and wait while this runs
@@ -855,7 +895,8 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
     double* ws = reinterpret_cast<double*>(sm_raw);                        // w, then q, then prefix r
     uint64_t* qs = reinterpret_cast<uint64_t*>(sm_raw);
     uint32_t* cnt = reinterpret_cast<uint32_t*>(sm_raw + (size_t)N * sizeof(uint64_t));
-    __shared__ double redd[32];
+    __shared__ long long redk[32];
+    __shared__ double tree1[kSelThreads], tree2[kSelThreads];
     __shared__ uint64_t redu[32];
     __shared__ int bad;
     const int j = blockIdx.x;
@@ -864,18 +905,22 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
     if (tid == 0) bad = 0;
 
     // ---- weights ----
+    // Maxima as order-preserving integer keys and the two weight sums by a
+    // shared-memory tree: each FP64 instruction holds its pipe for ~64 cycles
+    // on this part, and a shuffle tree per warp costs every warp five of them.
     double wmax;
     if (a.mode == 2) {
-        double m = 0.0;
+        long long km = order_key(0.0);
         for (int n = tid; n < N; n += blockDim.x) {
             const double w = a.w[base + n];
             ws[n] = w;
-            if (w > m) m = w;
+            const long long k = order_key(w);
+            km = k > km ? k : km;
         }
-        wmax = block_max(m, redd);
+        wmax = key_value(block_max_key(km, redk));
     } else {
         const double dphi = a.mode == 0 ? a.ctl->dphi : 0.0;
-        double m = -INFINITY;
+        long long km = kNegInfKey;
         for (int n = tid; n < N; n += blockDim.x) {
             double lw;
             if (a.mode == 0) {
@@ -884,20 +929,21 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
             } else {
                 lw = a.logw[base + n];
             }
-            if (isnan(lw)) lw = -INFINITY;
+            const long long k = order_key(lw);   // NaN counts as -inf
+            if (k == kNegInfKey) lw = -INFINITY;
             ws[n] = lw;
-            if (lw > m) m = lw;
+            km = k > km ? k : km;
         }
-        const double lmax = block_max(m, redd);
+        const long long kmax = block_max_key(km, redk);
+        const double lmax = key_value(kmax);
         double s1 = 0.0, s2 = 0.0;
         for (int n = tid; n < N; n += blockDim.x) {
-            const double w = lmax == -INFINITY ? 0.0 : exp(ws[n] - lmax);
+            const double w = kmax == kNegInfKey ? 0.0 : exp(ws[n] - lmax);
             ws[n] = w;
             s1 += w;
             s2 += w * w;
         }
-        s1 = block_sum(s1, redd);
-        s2 = block_sum(s2, redd);
+        block_sum_tree2(s1, s2, tree1, tree2);
         if (tid == 0) {
             const double lwj = lmax + log(s1 / (double)N);
             a.lw[j] = lwj;
