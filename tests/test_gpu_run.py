@@ -281,6 +281,56 @@ def test_launch_shapes_give_identical_runs(S):
     ctx.close()
 
 
+@pytest.mark.parametrize("precision,record", [("fp32", False), ("fp64", True)])
+def test_pipelined_run_equals_cycle_by_cycle(S, precision, record):
+    """smc_run with power tempering enqueues the next cycle's C and S phases
+    behind each M phase (one host round trip per cycle); the same context
+    stepped with smc_cycle synchronises twice per cycle.  Both must produce
+    the same cycles, designs and particles bitwise, also when the run is
+    split by max_cycles."""
+    truth = I.WORKLOADS["egarch22_T5000"].truth
+    y = I.simulate_egarch(truth, 600, seed=11)
+    m = S.model_egarch(2, 2, True)
+    mean, sd, lo = S.model_prior(m)
+    J, N = 8, 512
+    th0 = I.draw_prior(mean, sd, lo, J * N, seed=12)
+    prec = S.FP32 if precision == "fp32" else S.FP64
+    out = []
+    for mode in ("run", "split", "cycle"):
+        ctx = S.init(m, S.config_default(J=J, N=N, precision=prec, seed=7), y, th0)
+        if record:
+            ctx.record_design()
+        infos = []
+        if mode == "run":
+            n, last = ctx.run()
+            infos = [n, last["cycle"], last["phi"], last["R"], last["h_tenths"], last["acc_rate"]]
+        elif mode == "split":
+            n1, _ = ctx.run(3)
+            n2, last = ctx.run()
+            infos = [n1 + n2, last["cycle"], last["phi"], last["R"], last["h_tenths"], last["acc_rate"]]
+        else:
+            n, last = 0, None
+            while True:
+                info = ctx.cycle()
+                if info is None:
+                    break
+                n, last = n + 1, info
+                if info["done"]:
+                    break
+            infos = [n, last["cycle"], last["phi"], last["R"], last["h_tenths"], last["acc_rate"]]
+        design = ctx.design() if record else None
+        out.append((infos, ctx.log_ml(), ctx.particles(), design))
+        ctx.close()
+    for infos, lml, parts, design in out[1:]:
+        assert infos == out[0][0]
+        assert lml == out[0][1]
+        for a, b in zip(parts, out[0][2]):
+            np.testing.assert_array_equal(a, b)
+        if record:
+            for k in ("x", "R", "L"):
+                np.testing.assert_array_equal(design[k], out[0][3][k])
+
+
 def test_small_blocks_fp64_and_invalid_shapes(S):
     """FP64 runs give the same particles with 32- and 96-thread blocks; shapes
     outside the supported set are rejected."""
