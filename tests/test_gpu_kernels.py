@@ -340,7 +340,11 @@ def test_cov_chol_rank_deficient(S):
 
 
 # ------------------------------------------------------------------ C phase
-@pytest.mark.parametrize("P,phi,spread", [(65536, 0.0, 30.0), (1024, 0.3, 5.0), (4096, 0.9, 200.0)])
+# 400,037 particles exceed the four tiles per warp kept in registers (152 blocks
+# x 16 warps x 4 x 32 = 311,296 on 152 SMs), so the rest go through scratch;
+# 33 leave most warps of the only block empty.
+@pytest.mark.parametrize("P,phi,spread", [(65536, 0.0, 30.0), (1024, 0.3, 5.0), (4096, 0.9, 200.0),
+                                          (400037, 0.2, 50.0), (33, 0.0, 3.0)])
 def test_power_search_matches_oracle(S, P, phi, spread):
     rng = np.random.default_rng(P)
     ll = -16000 + spread * rng.standard_normal(P)
