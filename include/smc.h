@@ -303,9 +303,10 @@ uint64_t smc_launch_count(void);
 /* Total device time (ms, CUDA events on the context's stream) and launch count
  * of the timed M-phase mutation launches since the context was created or the
  * timer last reset.  smc_profile(ctx, 1) times every launch; smc_profile(ctx, 2)
- * times the first launch of each M phase only, so that the other launches keep
- * their programmatic dependent launch (a recorded event between two kernels
- * serialises them); 0 turns timing off.  Other values: SMC_EINVAL. */
+ * times the first launch of each M phase only, so that the covariance steps
+ * after the other launches keep their programmatic dependent launch (a recorded
+ * event between two kernels serialises them); 0 turns timing off.  Other
+ * values: SMC_EINVAL. */
 smc_status smc_profile(smc_ctx* ctx, int enable);
 smc_status smc_mutate_time(smc_ctx* ctx, double* ms, uint64_t* launches, int reset);
 

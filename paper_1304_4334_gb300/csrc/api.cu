@@ -538,7 +538,6 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
     a.err = &ctx->ctl->err;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool timed = ctx->profile == 1 || (ctx->profile == 2 && r == 0);
-    a.dependent = 0;   // see MutateArgs::dependent
     if (timed) {
         e0 = take_event(ctx);
         e1 = take_event(ctx);

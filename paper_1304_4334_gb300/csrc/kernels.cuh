@@ -45,12 +45,6 @@ struct MutateArgs {
     unsigned long long* acc_count;   // += accepted proposals
     int* pending;                    // set to 1 (nullable): an acceptance count awaits its h update
     int* err;
-    // Host-side launch choice: nonzero launches the kernel as a programmatic
-    // dependent of the preceding kernel (its blocks become resident early).
-    // The run leaves it off: blocks placed while the covariance step still
-    // occupies the SMs land unevenly, and the kernel runs as long as its most
-    // loaded SM (measured up to 35% slower).
-    int dependent = 0;
 };
 
 struct LoglikArgs {
@@ -308,9 +302,6 @@ __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, 
     using Real = typename Pol::Real;
     using Obs = typename Pol::Obs;
     const int d = a.m.d;
-    // Under a dependent launch the block is resident before its predecessor
-    // ends; it waits here, before reading anything that kernel writes.
-    pdl_wait();
     for (int i = threadIdx.x; i < d * d; i += blockDim.x) sm.Ls[i] = (Real)a.L[i];
     if (threadIdx.x == 0) sm.acc_s = 0;
 
@@ -359,7 +350,12 @@ __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, 
         Pol::setup(mdl, a.m, full);
     }
     const bool ok = Pol::run(mdl, pipe, a.T, a.W);
-    pdl_trigger();   // the next kernel may launch once every block is here
+    // the covariance step that follows (a dependent launch) may start once
+    // every block is here; the mutation kernel itself is launched plainly:
+    // blocks placed early, while the covariance step still held the SMs,
+    // landed unevenly and the one-wave kernel ran as long as its most loaded
+    // SM (measured up to 35% slower)
+    pdl_trigger();
     double ll_new = ok ? mdl.finish(a.T) : -INFINITY;
     if (isnan(ll_new)) ll_new = -INFINITY;
     if (!ok && threadIdx.x == 0) raise_error(a.err, kErrTimeout);
@@ -406,7 +402,6 @@ __device__ __forceinline__ void mutate_tile_x2(const MutateArgs& a, uint64_t ite
 {
     using Pol = PolicyEgarchF32<K, I>;
     const int d = a.m.d;
-    pdl_wait();   // as in mutate_tile
     for (int i = threadIdx.x; i < d * d; i += blockDim.x) sm.Ls[i] = a.L[i];
     if (threadIdx.x == 0) sm.acc_s = 0;
     ObsPipe<float, kChunkF32> pipe{sm.obuf, sm.bars, (const float*)a.obs, (int64_t)a.T,
