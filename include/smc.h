@@ -421,8 +421,13 @@ smc_status smc_cov_chol(const double* theta, int d, int P, int h_tenths, double*
 
 /* Power tempering C phase: the increment dphi in (0, 1 - phi] at which the
  * pooled RSS of weights exp(dphi * ll) first falls below d1, by `passes`
- * k-ary passes of 32 candidates; 1 - phi if RSS(1 - phi) >= d1.  ll: device
- * [P].  Host outputs: dphi, rss (FP64 RSS at dphi).  Synchronises. */
+ * k-ary passes of 32 candidates (evenly spaced over the current bracket, the
+ * bracket narrowing to the first candidate below d1 and its predecessor);
+ * 1 - phi if RSS(1 - phi) >= d1.  The candidate weights are FP32
+ * exponentials whose sums are exact 64-bit fixed-point totals, so the result
+ * does not depend on the grid; RSS is compared with d1 to about 1e-7.  One
+ * cooperative launch.  ll: device [P] (NaN counts as -inf).  Host outputs:
+ * dphi, rss (FP64 RSS at dphi).  Synchronises. */
 smc_status smc_power_search(const double* ll, int P, double phi, double d1, int passes,
                             double* dphi, double* rss, void* stream);
 
@@ -432,7 +437,7 @@ smc_status smc_power_search(const double* ll, int P, double phi, double d1, int 
  * floor((k Q + U_k) / N), U_k = mulhi64(x, Q), with one Philox draw per group
  * (systematic, draw index 0) or per slot (stratified)) from weights w (device [J*N],
  * non-negative, any scale per group).  Integer fixed point: q_n =
- * floor(2^40 w_n / max w), counts floor(N q_n / Q), residual draws by
+ * floor(2^32 w_n / max w), counts floor(N q_n / Q), residual draws by
  * upper_bound on the integer residual prefix with mulhi64(x, R), x from
  * Philox4x64-10 at counter (group, draw, cycle, 3 << 32).  idx: device
  * [J*N] int32, group-local source index of each output slot, in particle
