@@ -1167,41 +1167,67 @@ cudaError_t launch_cdata_select(const double* part, int G, int B, int s0, int T,
 
 // Pooled RSS at the chosen power from per-group (max, sum, sum of squares),
 // log wtilde += log(J^-1 sum_j wbar_j(l-1)), and phi += dphi.
-__global__ void k_cycle_close(const double* gstat, const double* lw, int J, int N, int power, Ctl* ctl)
+// Four warps: warps 0-1 pool the groups' (max, sum w, sum w^2) into the RSS,
+// warps 2-3 the groups' log w-bar into log w-tilde; maxima as integer keys,
+// and the closing arithmetic split over three threads of different warps
+// (each FP64 instruction holds its scheduler's pipe for ~64 cycles).
+__global__ void __launch_bounds__(128) k_cycle_close(const double* gstat, const double* lw, int J, int N, int power,
+                                                     Ctl* ctl)
 {
     pdl_trigger();
     pdl_wait();
-    const int lane = threadIdx.x;
-    double M = -INFINITY;
-    for (int j = lane; j < J; j += 32) M = fmax(M, gstat[3 * j]);
-    M = warp_max(M);
-    double s1 = 0.0, s2 = 0.0;
-    for (int j = lane; j < J; j += 32) {
-        if (gstat[3 * j] == -INFINITY) continue;
-        const double e = exp(gstat[3 * j] - M);
-        s1 += gstat[3 * j + 1] * e;
-        s2 += gstat[3 * j + 2] * e * e;
+    __shared__ long long sk[4];
+    __shared__ double sa[4], sb[4];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool pool = warp < 2;   // else: log w-tilde
+    const int t = tid & 63;
+    long long km = kNegInfKey;
+    for (int j = t; j < J; j += 64) {
+        const long long k = order_key(pool ? gstat[3 * j] : lw[j]);
+        km = k > km ? k : km;
     }
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
-    double lm = -INFINITY;
-    for (int j = lane; j < J; j += 32) lm = fmax(lm, lw[j]);
-    lm = warp_max(lm);
-    double s = 0.0;
-    for (int j = lane; j < J; j += 32) s += exp(lw[j] - lm);
-    s = warp_sum(s);
-    if (lane != 0) return;
-    ctl->rss = s1 * s1 / ((double)J * (double)N * s2);
-    ctl->ltilde += lm + log(s / (double)J);
-    if (power) ctl->phi = ctl->last ? 1.0 : ctl->phi + ctl->dphi;
-    ctl->acc_sum = 0.0;
-    ctl->acc_n = 0;
+    km = warp_max_key(km);
+    if (lane == 0) sk[warp] = km;
+    __syncthreads();
+    const long long k0 = sk[pool ? 0 : 2], k1 = sk[pool ? 1 : 3];
+    const long long kmax = k0 > k1 ? k0 : k1;
+    const double mx = key_value(kmax);
+    double a = 0.0, b = 0.0;
+    if (kmax != kNegInfKey)
+        for (int j = t; j < J; j += 64) {
+            if (pool) {
+                const double m = gstat[3 * j];
+                if (order_key(m) == kNegInfKey) continue;
+                const double e = exp(m - mx);
+                a += gstat[3 * j + 1] * e;
+                b += gstat[3 * j + 2] * e * e;
+            } else {
+                a += exp(lw[j] - mx);
+            }
+        }
+    a = warp_sum(a);
+    if (pool) b = warp_sum(b);
+    if (lane == 0) {
+        sa[warp] = a;
+        sb[warp] = b;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double s1 = sa[0] + sa[1], s2 = sb[0] + sb[1];
+        ctl->rss = s1 * s1 / ((double)J * (double)N * s2);
+    } else if (tid == 64) {
+        ctl->ltilde += mx + log((sa[2] + sa[3]) / (double)J);
+    } else if (tid == 32) {
+        if (power) ctl->phi = ctl->last ? 1.0 : ctl->phi + ctl->dphi;
+        ctl->acc_sum = 0.0;
+        ctl->acc_n = 0;
+    }
 }
 
 cudaError_t launch_cycle_close(const double* gstat, const double* lw, int J, int N, int power,
                                Ctl* ctl, cudaStream_t s)
 {
-    const cudaError_t e = pdl_launch(k_cycle_close, dim3(1), dim3(32), 0, s, gstat, lw, J, N, power, ctl);
+    const cudaError_t e = pdl_launch(k_cycle_close, dim3(1), dim3(128), 0, s, gstat, lw, J, N, power, ctl);
     count_launch();
     return e;
 }
