@@ -538,6 +538,9 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
     a.err = &ctx->ctl->err;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool timed = ctx->profile == 1 || (ctx->profile == 2 && r == 0);
+    // a timed launch sits between two events, which serialise it anyway: it is
+    // launched plainly so that the events bracket the kernel alone
+    a.dependent = timed ? 0 : 1;
     if (timed) {
         e0 = take_event(ctx);
         e1 = take_event(ctx);

@@ -31,6 +31,7 @@ cudaError_t launch_mutate_k(const MutateArgs& a, int threads, cudaStream_t s)
     case 4: k = k_mutate<Pol<K, 4>>; break;
     default: return cudaErrorInvalidValue;
     }
+    if (a.dependent) return pdl_launch(k, g, threads, 0, s, a);
     k<<<g, threads, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -48,6 +49,7 @@ cudaError_t launch_mutate_x2_k(const MutateArgs& a, int threads, cudaStream_t s)
     case 4: k = k_mutate_x2<K, 4>; break;
     default: return cudaErrorInvalidValue;
     }
+    if (a.dependent) return pdl_launch(k, g, threads, 0, s, a);
     k<<<g, threads, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -45,6 +45,10 @@ struct MutateArgs {
     unsigned long long* acc_count;   // += accepted proposals
     int* pending;                    // set to 1 (nullable): an acceptance count awaits its h update
     int* err;
+    // Host-side launch choice: nonzero launches the kernel as a programmatic
+    // dependent of the preceding kernel (the covariance step lets it launch
+    // once only its final block remains).
+    int dependent = 0;
 };
 
 struct LoglikArgs {
@@ -302,6 +306,7 @@ __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, 
     using Real = typename Pol::Real;
     using Obs = typename Pol::Obs;
     const int d = a.m.d;
+    pdl_wait();   // under a dependent launch: nothing the covariance step writes is read before this
     for (int i = threadIdx.x; i < d * d; i += blockDim.x) sm.Ls[i] = (Real)a.L[i];
     if (threadIdx.x == 0) sm.acc_s = 0;
 
@@ -350,12 +355,7 @@ __device__ __forceinline__ void mutate_tile(const MutateArgs& a, uint64_t iter, 
         Pol::setup(mdl, a.m, full);
     }
     const bool ok = Pol::run(mdl, pipe, a.T, a.W);
-    // the covariance step that follows (a dependent launch) may start once
-    // every block is here; the mutation kernel itself is launched plainly:
-    // blocks placed early, while the covariance step still held the SMs,
-    // landed unevenly and the one-wave kernel ran as long as its most loaded
-    // SM (measured up to 35% slower)
-    pdl_trigger();
+    pdl_trigger();   // the covariance step that follows may launch once every block is here
     double ll_new = ok ? mdl.finish(a.T) : -INFINITY;
     if (isnan(ll_new)) ll_new = -INFINITY;
     if (!ok && threadIdx.x == 0) raise_error(a.err, kErrTimeout);
@@ -402,6 +402,7 @@ __device__ __forceinline__ void mutate_tile_x2(const MutateArgs& a, uint64_t ite
 {
     using Pol = PolicyEgarchF32<K, I>;
     const int d = a.m.d;
+    pdl_wait();   // as in mutate_tile
     for (int i = threadIdx.x; i < d * d; i += blockDim.x) sm.Ls[i] = a.L[i];
     if (threadIdx.x == 0) sm.acc_s = 0;
     ObsPipe<float, kChunkF32> pipe{sm.obuf, sm.bars, (const float*)a.obs, (int64_t)a.T,

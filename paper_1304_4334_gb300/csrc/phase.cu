@@ -377,7 +377,6 @@ __global__ void __launch_bounds__(kCovThreads) k_cov_reduce(const void* __restri
 {
     __shared__ double red[32];
     __shared__ int last;
-    pdl_trigger();   // the mutation kernel may launch while this runs
     pdl_wait();
     const int e = blockIdx.x;
     const double s = cov_entry_total<kTiles>(parts, nparts, nacc, e, f.d, f.tile_kd, red);
@@ -388,6 +387,12 @@ __global__ void __launch_bounds__(kCovThreads) k_cov_reduce(const void* __restri
     }
     __syncthreads();
     if (!last) return;
+    // Every other block has left: the mutation kernel that follows (a
+    // dependent launch) may now place its blocks, evenly over the nearly empty
+    // SMs, and they wait for this block's factor.  (Placed earlier, while the
+    // SMs were still unevenly busy, they landed unevenly and the one-wave
+    // kernel ran as long as its most loaded SM.)
+    pdl_trigger();
     __threadfence();
     if (threadIdx.x == 0) *counter = 0u;
     cov_final_body(tot, f.d, f.P, f.shift_in, (size_t)f.shift_stride, f.shift_f, f.ctl, f.fixed_h, f.target,
