@@ -379,10 +379,13 @@ def main():
     e2e = None
     if not args.no_e2e:
         e2e_time, e2e_evals, h2d, d2h = 0.0, 0.0, 0, 0
+        # the initial particles live in pinned host memory (a view of it is
+        # what smc_init copies from)
+        th0_host = torch.from_numpy(np.ascontiguousarray(th0)).pin_memory().numpy()
         for k in range(args.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            c2 = S.init(m, cfg, y, th0, stream=stream.cuda_stream)
+            c2 = S.init(m, cfg, y, th0_host, stream=stream.cuda_stream)
             c2.set_launch_shape(shape[0], shape[1])
             c2.run(args.cycles)
             c2.log_ml()
