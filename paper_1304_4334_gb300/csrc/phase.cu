@@ -1079,19 +1079,40 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-__global__ void k_gather(GatherArgs a)
+// The row pointers are staged in shared memory once per block, and each
+// thread issues the loads of eight rows before their stores (a plain loop
+// waits on every row's load: the compiler cannot tell the rows apart).
+constexpr int kGatherMaxRows = 2 * kMaxD + 2 + kMaxState;
+constexpr int kGatherBatch = 8;
+
+__global__ void __launch_bounds__(256) k_gather(GatherArgs a)
 {
     pdl_trigger();
+    __shared__ const double* srow[kGatherMaxRows];
+    __shared__ double* drow[kGatherMaxRows];
+    for (int r = threadIdx.x; r < a.nrows; r += blockDim.x) {
+        srow[r] = a.src[r];
+        drow[r] = a.dst[r];
+    }
     pdl_wait();
+    __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.P) return;
     const int j = s / a.N;
     const int src = j * a.N + a.idx[s];
-    for (int r = 0; r < a.nrows; ++r) a.dst[r][s] = a.src[r][src];
+    for (int r0 = 0; r0 < a.nrows; r0 += kGatherBatch) {
+        double v[kGatherBatch];
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u) v[u] = r0 + u < a.nrows ? srow[r0 + u][src] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kGatherBatch; ++u)
+            if (r0 + u < a.nrows) drow[r0 + u][s] = v[u];
+    }
 }
 
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s)
 {
+    if (a.nrows < 0 || a.nrows > kGatherMaxRows) return cudaErrorInvalidValue;
     const cudaError_t e = pdl_launch(k_gather, dim3((a.P + 255) / 256), dim3(256), 0, s, a);
     count_launch();
     return e;
