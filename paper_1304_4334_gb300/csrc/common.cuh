@@ -170,23 +170,6 @@ __device__ T block_sum(T v, T* scratch)
     return r;
 }
 
-__device__ inline double block_max(double v, double* scratch)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = (blockDim.x + 31) >> 5;
-    v = warp_max(v);
-    __syncthreads();
-    if (lane == 0) scratch[warp] = v;
-    __syncthreads();
-    double r = (threadIdx.x < (unsigned)nwarps) ? scratch[threadIdx.x] : -INFINITY;
-    if (warp == 0) r = warp_max(r);
-    if (threadIdx.x == 0) scratch[0] = r;
-    __syncthreads();
-    r = scratch[0];
-    __syncthreads();
-    return r;
-}
-
 // Inclusive block scan of one value per thread (u64).  scratch >= 32 elements.
 __device__ inline uint64_t block_inclusive_scan_u64(uint64_t v, uint64_t* scratch)
 {
