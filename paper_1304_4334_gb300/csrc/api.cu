@@ -452,10 +452,10 @@ static smc_status m_iteration(smc_ctx* ctx, int r, int Tm, double phi)
         // Sigma = h^2 V; the independent sampler takes V itself (h pinned at
         // 10 tenths for the factor, still updated from the acceptance rate)
         // and the pooled mean.
-        // After the first iteration of an M phase the previous mutation
+        // The S phase's gather (first iteration) or the previous mutation
         // launch has left the covariance tile sums of the current particles.
         const bool indep = c.mutation == SMC_INDEP;
-        if (r > 0 && ctx->tiles_ready)
+        if (ctx->tiles_ready)
             CU(launch_cov_tiles(ctx->covtile, ctx->ntiles, ctx->tile_kd, d, P, ctx->cov_tot, ctx->cov_counter,
                                 ctx->covshift_f, ctx->qmean, ctx->ctl, indep ? 10 : 0, c.acc_target,
                                 c.hmin_tenths, c.hmax_tenths, ctx->L, ctx->stream));
@@ -620,7 +620,15 @@ static smc_status s_phase(smc_ctx* ctx, int mode)
     g.nrows = ctx->gather_rows;
     g.src = ctx->gather_ptrs + (size_t)ctx->cur * ctx->gather_rows * 2;
     g.dst = ctx->gather_ptrs + (size_t)ctx->cur * ctx->gather_rows * 2 + ctx->gather_rows;
+    // the next M phase's first covariance step takes its sums from the gather
+    const bool tiles = ctx->covtile && !ctx->replay;
+    g.covtile = tiles ? ctx->covtile : nullptr;
+    g.covshift = ctx->covshift_f;
+    g.ntiles = ctx->ntiles;
+    g.d = ctx->d;
+    g.tile_kd = ctx->tile_kd;
     CU(launch_gather(g, ctx->stream));
+    ctx->tiles_ready = tiles;
     ctx->cur ^= 1;
     return SMC_OK;
 }

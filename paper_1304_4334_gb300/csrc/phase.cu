@@ -1,5 +1,6 @@
 // C-phase search, S phase, covariance/Cholesky and estimator kernels.
 #include "phase.cuh"
+#include "covtile.cuh"
 
 #include <cstdio>
 
@@ -401,14 +402,14 @@ __global__ void __launch_bounds__(kCovThreads) k_cov_reduce(const void* __restri
 
 
 // ----- batched covariance: one launch per stage for many particle sets -----
-// Iteration 0 of a cycle takes block partials of theta; later iterations take
-// the tile sums the mutation kernel left (when the job has them), exactly as
-// the single-run path does.
+// A job with tile sums takes them at every iteration (the S phase's gather
+// leaves them for iteration 0, the mutation kernel for the later ones);
+// otherwise block partials of theta, exactly as the single-run path does.
 __global__ void __launch_bounds__(kCovThreads) k_cov_partial_batch(const CovJob* __restrict__ jobs,
                                                                   const int* iter)
 {
     const CovJob& j = jobs[blockIdx.y];
-    if ((int)blockIdx.x >= j.G || *iter >= j.R || (*iter > 0 && j.tiles)) return;
+    if ((int)blockIdx.x >= j.G || *iter >= j.R || j.tiles) return;
     cov_partial_body(j.theta, j.d, j.P, j.part, blockIdx.x, j.G);
 }
 
@@ -419,7 +420,7 @@ __global__ void __launch_bounds__(kCovThreads) k_cov_combine_batch(const CovJob*
     const int nacc = j.d + j.d * (j.d + 1) / 2;
     const int e = blockIdx.x;
     if (e >= nacc || *iter >= j.R) return;
-    const double s = (*iter > 0 && j.tiles) ? cov_entry_total<true>(j.tiles, j.ntiles, nacc, e, j.d, j.tile_kd, red)
+    const double s = j.tiles ? cov_entry_total<true>(j.tiles, j.ntiles, nacc, e, j.d, j.tile_kd, red)
                                             : cov_entry_total<false>(j.part, j.G, nacc, e, j.d, 0, red);
     if (threadIdx.x == 0) j.part[(size_t)j.G * nacc + e] = s;
 }
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(kCovThreads) k_cov_final_batch(const CovJob* _
     const CovJob& j = jobs[blockIdx.x];
     if (*iter >= j.R) return;
     const int nacc = j.d + j.d * (j.d + 1) / 2;
-    const bool tiles = *iter > 0 && j.tiles;
+    const bool tiles = j.tiles != nullptr;
     cov_final_body(j.part + (size_t)j.G * nacc, j.d, j.P, j.theta, (size_t)j.P, tiles ? j.shift_f : nullptr,
                    j.ctl, 0, j.target, j.hmin, j.hmax, j.mean, j.shift_f, nullptr, j.L);
 }
@@ -1081,39 +1082,69 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t s)
 
 // The row pointers are staged in shared memory once per block, and each
 // thread issues the loads of eight rows before their stores (a plain loop
-// waits on every row's load: the compiler cannot tell the rows apart).
+// waits on every row's load: the compiler cannot tell the rows apart).  With
+// kD > 0 the warps then form the covariance tile sums of the particles they
+// wrote (cov_tile_sums<kD>, as the mutation kernel's epilogue does).
 constexpr int kGatherMaxRows = 2 * kMaxD + 2 + kMaxState;
 constexpr int kGatherBatch = 8;
 
+template <int kD>
 __global__ void __launch_bounds__(256) k_gather(GatherArgs a)
 {
     pdl_trigger();
     __shared__ const double* srow[kGatherMaxRows];
     __shared__ double* drow[kGatherMaxRows];
+    __shared__ float shift[kD > 0 ? kD : 1];
     for (int r = threadIdx.x; r < a.nrows; r += blockDim.x) {
         srow[r] = a.src[r];
         drow[r] = a.dst[r];
     }
     pdl_wait();
     __syncthreads();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.P) return;
-    const int j = s / a.N;
-    const int src = j * a.N + a.idx[s];
-    for (int r0 = 0; r0 < a.nrows; r0 += kGatherBatch) {
-        double v[kGatherBatch];
-#pragma unroll
-        for (int u = 0; u < kGatherBatch; ++u) v[u] = r0 + u < a.nrows ? srow[r0 + u][src] : 0.0;
-#pragma unroll
-        for (int u = 0; u < kGatherBatch; ++u)
-            if (r0 + u < a.nrows) drow[r0 + u][s] = v[u];
+    if constexpr (kD > 0) {
+        if ((int)threadIdx.x < a.d) {
+            const float v = (float)srow[threadIdx.x][a.idx[0]];   // slot 0 of group 0
+            shift[threadIdx.x] = v;
+            if (blockIdx.x == 0) a.covshift[threadIdx.x] = v;
+        }
+        __syncthreads();
     }
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = s < a.P;
+    if (act) {
+        const int j = s / a.N;
+        const int src = j * a.N + a.idx[s];
+        for (int r0 = 0; r0 < a.nrows; r0 += kGatherBatch) {
+            double v[kGatherBatch];
+#pragma unroll
+            for (int u = 0; u < kGatherBatch; ++u) v[u] = r0 + u < a.nrows ? srow[r0 + u][src] : 0.0;
+#pragma unroll
+            for (int u = 0; u < kGatherBatch; ++u)
+                if (r0 + u < a.nrows) drow[r0 + u][s] = v[u];
+        }
+    }
+    if constexpr (kD > 0) cov_tile_sums<kD>(drow[0], (size_t)a.P, a.d, shift, a.covtile, a.ntiles, s, act);
 }
 
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s)
 {
     if (a.nrows < 0 || a.nrows > kGatherMaxRows) return cudaErrorInvalidValue;
-    const cudaError_t e = pdl_launch(k_gather, dim3((a.P + 255) / 256), dim3(256), 0, s, a);
+    const int kd = a.covtile ? a.tile_kd : 0;
+    if (kd > 0 && (a.d < 1 || a.d > kd || !a.covshift || a.nrows < a.d)) return cudaErrorInvalidValue;
+    void (*k)(GatherArgs) = nullptr;
+    switch (kd) {
+    case 0: k = k_gather<0>; break;
+    case 5: k = k_gather<5>; break;
+    case 8: k = k_gather<8>; break;
+    case 11: k = k_gather<11>; break;
+    case 14: k = k_gather<14>; break;
+    case 17: k = k_gather<17>; break;
+    case 20: k = k_gather<20>; break;
+    case 23: k = k_gather<23>; break;
+    case 26: k = k_gather<26>; break;
+    default: return cudaErrorInvalidValue;
+    }
+    const cudaError_t e = pdl_launch(k, dim3((a.P + 255) / 256), dim3(256), 0, s, a);
     count_launch();
     return e;
 }

@@ -105,9 +105,16 @@ cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
 struct GatherArgs {
     const int32_t* idx;
     int N, P;
-    int nrows;                 // rows of length P to gather
+    int nrows;                 // rows of length P to gather (theta's d rows first)
     const double* const* src;  // device array of nrows row pointers
     double* const* dst;        // device array of nrows row pointers
+    // Covariance tile sums of the gathered particles for the next M phase's
+    // first covariance step (nullable): the same 32-particle tiles and layout
+    // as the mutation kernel's, about the shift theta of the particle placed
+    // in slot 0 (rounded to FP32), which is also written to covshift.
+    float* covtile = nullptr;
+    float* covshift = nullptr;
+    int ntiles = 0, d = 0, tile_kd = 0;
 };
 cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s);
 
