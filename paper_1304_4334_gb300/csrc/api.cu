@@ -948,6 +948,7 @@ static smc_status start_run(smc_ctx* ctx, const double* theta0, int theta0_on_de
     ctx->cycle = 0;
     ctx->t_prev = 0;
     ctx->done = 0;
+    ctx->tiles_ready = false;   // the tile sums describe the previous particles
     ctx->phi = 0.0;
     ctx->msteps = 0;
     ctx->evals = 0.0;
