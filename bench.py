@@ -36,9 +36,13 @@ if ROOT not in sys.path:
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT_GB300 = 152
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per k_mutate launch, by
-# (workload, particles per thread, threads per block)
-MUTATE_TRAFFIC = {("egarch22_T5000", 2, 64): 8_684_288 + 33_280, ("egarch22_T5000", 1, 224): 8_762_368 + 299_264}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the current
+# mutation kernel, by (workload, particles per thread, threads per block).
+# Empty: both kernels changed after their last captures (the paired one's
+# launch bound, the single one's entry wait of a dependent launch), whose
+# figures, 8.72 MB (2 x 64) and 9.06 MB (1 x 224) per launch, are in
+# profiles/; traffic is reported as null until they are captured again.
+MUTATE_TRAFFIC = {}
 SM_MAX_MHZ_FALLBACK = 2070.0
 L2_FLUSH_BYTES = 256 << 20
 
@@ -400,8 +404,8 @@ def main():
 
     # ---- roofline of the dominant kernel (fused RW mutate) ----
     # DRAM bytes (read + write) of one mutate launch from an ncu capture of the
-    # same kernel, workload and launch shape (profiles/k_mutate_x2_egarch22_T5000.md);
-    # None where no capture of the current kernel exists.
+    # same kernel, workload and launch shape (profiles/); None where no capture
+    # of the current kernel exists.
     traffic = MUTATE_TRAFFIC.get((args.workload, shape[0], shape[1])) if not mala else None
     mhz, src = sm_max_mhz()
     paired = shape[0] == 2
