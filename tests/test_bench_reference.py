@@ -21,3 +21,21 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["config"]["workload"] == "egarch22_T5000" and line["data"] == "synthetic"
+
+
+def test_roofline_operation_counts():
+    """The ALU bound bench.py reports: the per-observation counts of the design
+    table ((K,I) = (2,2) with gamma: 20 FP32 + 2 SFU; I = 1 has no mixture
+    exponential) and the three limits at 152 SMs x 2070 MHz."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.alu_ops_per_eval(2, 2, True) == (20, 2)
+    assert bench.alu_ops_per_eval(1, 1, False) == (1 + 2 + 1 + 1 + 2 + 1, 1)
+    assert bench.alu_ops_per_eval(3, 4, True) == (1 + 9 + 3 + 1 + 2 + 20, 5)
+    f = 152 * 2070e6
+    peak, pipe = bench.alu_peak_evals(2, 2, True, 152, 2070.0)
+    assert pipe == "issue" and abs(peak - f * 128 / 22) < 1e-3 * peak
+    peak2, pipe2 = bench.alu_peak_evals(2, 2, True, 152, 2070.0, paired=True)
+    assert pipe2 == "fp32" and abs(peak2 - f * 128 / 20) < 1e-3 * peak2
+    fm, mm = bench.mala_ops_per_eval(2, 2, True)
+    assert fm > 20 and mm > 2
