@@ -198,6 +198,15 @@ smc_status smc_transfer_bytes(smc_ctx* ctx, uint64_t* h2d, uint64_t* d2h);
  * (Section 4.2).  Host outputs; any may be NULL. */
 smc_status smc_log_ml(smc_ctx* ctx, double* log_ml, double* nse, double* log_ml_tilde);
 
+/* Per-group state of the estimators of Section 4.2 (host outputs of J doubles,
+ * nullable; synchronises): a[j] = the sum over the completed cycles of
+ * log wbar_j(l-1), the group's log marginal-likelihood accumulator, so that
+ * smc_log_ml's log wbar^(J,N) = log J^-1 sum_j exp(a_j); lw[j] = log wbar_j(l-1)
+ * of the last completed cycle, the log of the mean over the group's N
+ * particles of the weights w_jn(l-1) that its C phase formed ((C_phase_compute);
+ * in power tempering w = exp(dphi l(theta))). */
+smc_status smc_group_estimators(smc_ctx* ctx, double* a, double* lw);
+
 /* Posterior moments at the current particles: for each free parameter and,
  * for EGARCH, the test functions g1 (log volatility), g2 (E eps^3) and g3
  * (P(Y_t+1 < -0.03)) of Section 5.2: mean, s.d., NSE (NSE_def) and RNE.
@@ -299,6 +308,26 @@ smc_status smc_describe(const smc_ctx* ctx, smc_model* m, smc_config* c, int* T)
  * has no counterpart; it exists so that the timeout path can be exercised
  * without faulting or hanging the device. */
 smc_status smc_wait_selftest(uint64_t limit_ns, int complete, void* stream);
+
+/* Peak rates of the ALU pipes of the current device, measured by a
+ * microbenchmark (the paper has no counterpart: the likelihood kernels are
+ * bound by plain FP32/SFU arithmetic and instruction issue, and their roofline
+ * needs these rates on the part at hand).  Each test runs one block of 1024
+ * threads on every SM, each thread eight independent chains of one operation.
+ * Outputs (host struct): lane operations per SM and clock for ffma
+ * (fma.rn.f32), ffma2 (fma.rn.f32x2, two lane operations per instruction),
+ * ex2 and lg2 (ex2/lg2.approx.ftz.f32, each with one FP32 operand fix-up on
+ * another pipe) and dfma (fma.rn.f64); issue = warp instructions per SM and
+ * clock with an FFMA and a logic operation on its result in turn; sm_mhz = the SM clock during
+ * the tests (cycle counter over the global nanosecond timer); sms = SM count.
+ * Takes about 10 ms; allocates and frees a few bytes of device memory;
+ * synchronises `stream`.  SMC_ECUDA without a usable GPU. */
+typedef struct {
+    int sms;
+    double ffma, ffma2, ex2, lg2, dfma, issue;
+    double sm_mhz;
+} smc_peak_rates;
+smc_status smc_peaks(smc_peak_rates* out, void* stream);
 
 /* Number of kernel launches this library has issued in this process. */
 uint64_t smc_launch_count(void);
@@ -456,12 +485,16 @@ smc_status smc_group_moments(const double* g, int nf, int J, int N, double* out,
  * device memory while they run (a framework that reserves the device memory
  * budget up front, or a latency-bound loop that must not wait on the memory
  * pool).  The paper has no counterpart: this is a deployment variant.  Its
- * partial-sum scratch is a fixed array inside the library (about 1.1 MB per
+ * partial-sum scratch is a fixed array inside the library (about 2.3 MB per
  * device that uses it, held until the process exits), so it calls no
- * allocator.  Limits: 1 <= d <= SMC_MAX_D, P >= 2; other sizes return
- * SMC_EINVAL.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls on a device share the array:
+ * allocator.  It splits the particles over the same blocks as smc_cov_chol
+ * (at most 512 blocks: identical results on any device with up to 256 SMs,
+ * equal within FP rounding of the sums beyond).  Limits: 1 <= d <= SMC_MAX_D,
+ * P >= 2; other sizes return SMC_EINVAL.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current and keeps it for the life of the process; make that first call
+ * before any stream capture, and do not call this entry point after a
+ * cudaDeviceReset in the same process.  All calls on a device share the array:
  * calls whose kernels overlap on the GPU (unordered streams) race on it.
  * Every partial sum read in a call is written earlier in the same call and
  * the reduction's counter (the array's last word) is back at zero when a call

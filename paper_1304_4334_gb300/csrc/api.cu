@@ -1390,6 +1390,22 @@ smc_status smc_log_ml(smc_ctx* ctx, double* log_ml, double* nse, double* log_ml_
     return SMC_OK;
 }
 
+smc_status smc_group_estimators(smc_ctx* ctx, double* a, double* lw)
+{
+    if (!ctx) return SMC_EINVAL;
+    const size_t bytes = (size_t)ctx->cfg.J * sizeof(double);
+    if (a) {
+        CU(cudaMemcpyAsync(a, ctx->a, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        ctx->d2h += bytes;
+    }
+    if (lw) {
+        CU(cudaMemcpyAsync(lw, ctx->lw, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        ctx->d2h += bytes;
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    return SMC_OK;
+}
+
 smc_status smc_moments(smc_ctx* ctx, double* out, int* nf)
 {
     if (!ctx || !out) return SMC_EINVAL;

@@ -59,6 +59,11 @@ class smc_config(C.Structure):
                 ("pit", C.c_int)]
 
 
+class smc_peak_rates(C.Structure):
+    _fields_ = [("sms", C.c_int), ("ffma", C.c_double), ("ffma2", C.c_double), ("ex2", C.c_double),
+                ("lg2", C.c_double), ("dfma", C.c_double), ("issue", C.c_double), ("sm_mhz", C.c_double)]
+
+
 class smc_cycle_info(C.Structure):
     _fields_ = [("cycle", C.c_int), ("t", C.c_int), ("phi", C.c_double), ("rss", C.c_double),
                 ("R", C.c_int), ("h_tenths", C.c_int), ("acc_rate", C.c_double),
@@ -92,6 +97,8 @@ def _declare(L):
     L.smc_describe.argtypes = [vp, P(smc_model), P(smc_config), P(C.c_int)]
     L.smc_pit.argtypes = [vp, dp, C.c_int]
     L.smc_moments.argtypes = [vp, dp, P(C.c_int)]
+    L.smc_group_estimators.argtypes = [vp, dp, dp]
+    L.smc_peaks.argtypes = [P(smc_peak_rates), vp]
     L.smc_get_particles.argtypes = [vp, dp, dp, dp, dp]
     L.smc_launch_count.argtypes = []
     L.smc_launch_count.restype = C.c_uint64
@@ -220,6 +227,15 @@ def config_default(**kw):
     return c
 
 
+def peaks(stream=None):
+    """Measured ALU pipe rates of the device (smc_peaks): lane operations per SM
+    and clock for ffma, ffma2, ex2, lg2, dfma; warp instructions per SM and
+    clock for issue; the SM clock (MHz) during the tests; the SM count."""
+    r = smc_peak_rates()
+    _check(lib().smc_peaks(C.byref(r), _stream(stream)))
+    return {k: getattr(r, k) for k, _ in smc_peak_rates._fields_}
+
+
 def launch_count():
     return int(lib().smc_launch_count())
 
@@ -293,6 +309,13 @@ class Ctx:
         a, b, c = C.c_double(), C.c_double(), C.c_double()
         _check(lib().smc_log_ml(self.h, C.byref(a), C.byref(b), C.byref(c)), self.h)
         return a.value, b.value, c.value
+
+    def group_estimators(self):
+        """(a_j, log wbar_j(l-1) of the last cycle) per group (smc_group_estimators)."""
+        a = np.zeros(self.cfg.J)
+        lw = np.zeros(self.cfg.J)
+        _check(lib().smc_group_estimators(self.h, _dptr(a), _dptr(lw)), self.h)
+        return a, lw
 
     def log_score(self):
         """(log p(y_{b+1:T} | y_1:b), NSE) for the configured burn-in b."""
