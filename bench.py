@@ -3,10 +3,14 @@
 
 Metric: M-phase particle x observation likelihood evaluations per second.  One
 step is one whole simulator run (Algorithm 2: prior draws -> C, S, M cycles ->
-log marginal likelihood) on the workload of Section 5's shape: EGARCH with
-K = 2 factors and I = 2 mixture components, T = 5000 synthetic daily returns,
-J = 64 groups x N = 1024 particles, FP32 recursion with FP64 accumulators,
-random-walk Metropolis adapted toward 0.25 acceptance, power tempering.
+log marginal likelihood).  Default workload: the largest one-GPU shape, EGARCH
+with K = 3 factors and I = 4 mixture components (23 parameters, Table 1),
+T = 20000 synthetic daily returns with heavy-tailed mixture shocks, J = 128
+groups x N = 8192 particles (about 1M), FP32 recursion with FP64 accumulators,
+random-walk Metropolis adapted toward 0.25 acceptance, power tempering; its
+`equal_nse` entry compares FP32 random-walk and FP32 MALA runs at equal log-ML
+NSE.  `--workload egarch22_T5000` runs Section 5's own J = 64 x N = 1024,
+K = 2, I = 2, T = 5000 shape.
 `value` = sum over steps of the M-phase evaluations / summed step time, with
 the observations and prior draws resident in HBM; `e2e` repeats the run through
 the public API from host buffers (context creation, host->device copies of
@@ -15,7 +19,8 @@ region).  Each step's device time is bracketed by CUDA events on the run's
 stream; L2 is flushed between steps by writing a 256 MB buffer.
 
 `--impl reference` times the FP64 CPU oracle on the host cores instead (bounded
-sample: one Metropolis iteration over a subsample of particles per step).
+sample: random-walk Metropolis iterations over a subsample of particles per
+step).  `--peaks` prints the measured ALU pipe rates (smc_peaks) and exits.
 Multi-GPU: independent replicas, one per rank (the path has no exchange step).
 """
 from __future__ import annotations
@@ -53,13 +58,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="egarch22_T5000")
+    ap.add_argument("--workload", default="egarch34_T20000")
+    ap.add_argument("--peaks", action="store_true", help="print the measured ALU pipe rates and exit")
+    ap.add_argument("--precision", action="store_true",
+                    help="print the FP32 path's measured error against FP64 for each result and exit")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cycles", type=int, default=0, help="cap on cycles per run (0 = full run; profiling only)")
     ap.add_argument("--no-equal-nse", action="store_true")
     ap.add_argument("--launch-shape", default="", help="PPT,THREADS: fixed mutation launch shape instead of autotuning")
     ap.add_argument("--equal-nse-seeds", type=int, default=3)
+    ap.add_argument("--particles", default="", help="J,N: override the workload's groups x particles (profiling only)")
     return ap.parse_args()
 
 
@@ -90,17 +99,25 @@ def mala_ops_per_eval(K, I, gamma):
     return fp32, mufu
 
 
-def alu_peak_evals(K, I, gamma, sms, mhz, paired=False, mala=False):
-    """Evaluations/s bound at the given SM clock from the FP32 pipe (128
-    lanes/clk/SM), the SFU (32 lanes/clk/SM for ex2/lg2 on this part: the
-    profiled kernels' XU-pipe share against their known SFU rate) and
-    instruction issue (4 x 32 lanes/clk/SM, each instruction once).  With
-    paired FP32 instructions (two particles per thread) an FP32 instruction
-    carries two lanes' work, so issue counts fp32/2 + mufu per evaluation while
-    the FP32 pipe still bounds fp32."""
+NOMINAL_RATES = {"ffma": 128.0, "ffma2": 128.0, "ex2": 32.0, "issue": 4.0}
+
+
+def alu_peak_evals(K, I, gamma, sms, mhz, paired=False, mala=False, rates=None):
+    """Evaluations/s bound at the given SM clock from the FP32 pipe, the SFU
+    (ex2/lg2) and instruction issue.  `rates` are per SM and clock: lane
+    operations of FFMA ("ffma"), of the paired FFMA2 ("ffma2") and of MUFU.EX2
+    ("ex2"), and warp instructions issued ("issue"); by default the nominal
+    128 / 128 / 32 lanes and 4 warp instructions (4 schedulers x 32 lanes, each
+    instruction once), else the measured rates of smc_peaks.  With paired FP32
+    instructions (two particles per thread) an FP32 instruction carries two
+    lanes' work, so issue counts fp32/2 + mufu per evaluation while the FP32
+    pipe (at the FFMA2 rate) still bounds fp32."""
+    r = dict(NOMINAL_RATES)
+    if rates:
+        r.update({k: v for k, v in rates.items() if k in r and v})
     fp32, mufu = (mala_ops_per_eval if mala else alu_ops_per_eval)(K, I, gamma)
-    limits = {"issue": 128.0 / ((fp32 / 2.0 if paired else fp32) + mufu),
-              "fp32": 128.0 / fp32, "mufu": 32.0 / mufu}
+    limits = {"issue": 32.0 * r["issue"] / ((fp32 / 2.0 if paired else fp32) + mufu),
+              "fp32": (r["ffma2"] if paired else r["ffma"]) / fp32, "mufu": r["ex2"] / mufu}
     pipe = min(limits, key=limits.get)
     return sms * mhz * 1e6 * limits[pipe], pipe
 
@@ -177,17 +194,34 @@ def dist_setup(args):
 
 
 # -------------------------------------------------------------- CPU oracle
-def cpu_oracle_rate(w, y, budget_s=12.0, sample=256):
+def host_cpu():
+    """CPU model of the host (read-only, /proc/cpuinfo or lscpu)."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        d = {a.strip(): b.strip() for a, b in (l.split(":", 1) for l in out.splitlines() if ":" in l)}
+        return " ".join(x for x in (d.get("Vendor ID"), d.get("Model name")) if x) or "unknown"
+    except Exception:
+        return "unknown"
+
+
+def cpu_oracle_rate(w, y, budget_s=12.0, sample=256, threads=None):
     """The FP64 oracle's M-phase rate (one random-walk Metropolis iteration over
-    `sample` posterior-like particles x all T observations per call), on every
-    host core, repeated for about `budget_s` seconds."""
+    `sample` posterior-like particles x all T observations per call), on
+    `threads` host threads (default: every core), repeated for about
+    `budget_s` seconds."""
     import numpy as np
     import oracle as O
     from paper_1304_4334_gb300 import inputs as I
 
     spec = O.ModelSpec(K=w.K, I=w.I, gamma=w.gamma)
     th = I.posterior_cloud(I.theta_of_truth(w.truth, I_model=w.I, gamma=w.gamma), sample, 0.02, seed=5)
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     ll, st = O.loglik(spec, y, th, with_state=True, nthreads=cores)
     lp = O.logprior(spec, th)
     _, V = O.mean_cov(th)
@@ -201,8 +235,41 @@ def cpu_oracle_rate(w, y, budget_s=12.0, sample=256):
         if el >= budget_s:
             break
     return {"value": evals / el, "unit": "particle*obs lik evals/s", "cores": cores, "kind": "oracle",
+            "cpu": host_cpu(),
             "sample": f"{it} random-walk Metropolis iterations x {sample} particles x T={len(y)} "
-                      f"({w.name}), FP64 C oracle, {cores} OpenMP threads, {el:.1f} s"}
+                      f"({w.name}), FP64 C oracle, {cores} OpenMP thread{'s' if cores > 1 else ''}, {el:.1f} s"}
+
+
+def cpu_oracle_full_run(threads=None):
+    """The FP64 oracle's whole adaptive run on the small EGARCH(1,1) workload
+    (K = 1, I = 1, no leverage, T = 500, J = 4 x N = 256, FP64 random walk,
+    10 Metropolis iterations per M phase), timed on the host cores."""
+    import oracle as O
+    from paper_1304_4334_gb300 import inputs as I
+
+    w = I.WORKLOADS["egarch11_T500"]
+    y = w.data()
+    spec = O.ModelSpec(K=1, I=1, gamma=False)
+    th0 = I.draw_prior(*O.table1_prior(1, 1, False), w.P, seed=w.prior_seed)
+    cores = threads or os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = O.smc_run(spec, y, th0, w.J, w.N, rbar=w.rbar, kappa=w.kappa, seed=7, nthreads=cores)
+    el = time.perf_counter() - t0
+    return {"workload": w.name, "seconds": el, "cores": cores, "cycles": r["cycles"],
+            "metropolis_steps": r["metropolis_steps"], "log_ml": r["log_ml"], "nse": r["log_ml_nse"],
+            "value": r["evals"] / el, "unit": "particle*obs lik evals/s"}
+
+
+def cpu_baseline_leg(w, y):
+    """The oracle on the host cores: M-phase rate with every core (OpenMP over
+    particles; the headline) and with one thread, plus the small workload's
+    whole run in both modes."""
+    cpu = cpu_oracle_rate(w, y)
+    one = cpu_oracle_rate(w, y, budget_s=6.0, sample=64, threads=1)
+    cpu["single_thread"] = {"value": one["value"], "sample": one["sample"]}
+    cpu["full_run_egarch11_T500"] = {"all_cores": cpu_oracle_full_run(),
+                                     "single_thread": cpu_oracle_full_run(threads=1)}
+    return cpu
 
 
 def run_reference(args, world, rank):
@@ -280,6 +347,83 @@ def equal_nse_comparison(S, w, y, th0, stream, seeds):
     return out
 
 
+# ---------------------------------------------------- FP32 error per result
+def _err_stats(x, ref):
+    import numpy as np
+    ok = np.isfinite(ref) & (ref > -1e7)
+    ab = np.abs(x[ok] - ref[ok])
+    rel = ab / np.abs(ref[ok])
+    return {"n": int(ok.sum()), "rel_max": float(rel.max()), "rel_median": float(np.median(rel)),
+            "abs_max": float(ab.max()), "abs_median": float(np.median(ab)),
+            "share_rel_le_1e-4": float((rel <= 1e-4).mean())}
+
+
+def precision_report(S, I, P=2048, seeds=2):
+    """The FP32 path's error against FP64, per result (the FP32 mode of the
+    precision contract: recursion in FP32, log likelihood, log weights and
+    estimators in FP64), on the two FP32 workload shapes:
+    - log likelihood of P particles over the full series, from the stand-alone
+      likelihood kernel (which carries 1 - alpha) and from the mutation kernel
+      (a zero-step random-walk iteration from a log likelihood of -inf accepts
+      theta itself and stores its log likelihood), against the FP64 oracle:
+      posterior-like particles (theta_true + N(0, 0.05^2)) and raw prior draws;
+    - whole runs (J = 64 x N = 256) in FP32 and in FP64 on the GPU from the same
+      prior draws and seed: log ML difference (absolute and in units of the FP64
+      run's NSE) and the largest posterior-mean difference over the parameters
+      (in units of the FP64 run's NSE of that mean)."""
+    import numpy as np
+    import torch
+    import oracle as O
+    out = {"what": "FP32 path vs FP64 per result", "shapes": {}}
+    cores = os.cpu_count() or 1
+    for name in ("egarch22_T5000", "egarch34_T20000"):
+        w = I.WORKLOADS[name]
+        y = w.data()
+        spec = O.ModelSpec(K=w.K, I=w.I, gamma=w.gamma)
+        m = S.model_egarch(w.K, w.I, w.gamma)
+        mean, sd, lo = S.model_prior(m)
+        yd = torch.as_tensor(y, dtype=torch.float32, device="cuda")
+        rec = {"K": w.K, "I": w.I, "T": w.T}
+        clouds = {"posterior_like": I.posterior_cloud(I.theta_of_truth(w.truth, I_model=w.I, gamma=w.gamma),
+                                                      P, 0.05, seed=3),
+                  "prior_draws": I.draw_prior(mean, sd, lo, P, seed=w.prior_seed + 99)}
+        for cname, th in clouds.items():
+            ll_o = O.loglik(spec, y, th, nthreads=cores)
+            theta = torch.as_tensor(np.ascontiguousarray(th.T), device="cuda")
+            ll = torch.empty(P, dtype=torch.float64, device="cuda")
+            S.loglik(m, S.FP32, yd, theta, ll)
+            llm = torch.full((P,), -math.inf, dtype=torch.float64, device="cuda")
+            lpm = torch.as_tensor(O.logprior(spec, th), device="cuda")
+            tm = theta.clone()
+            S.mutate_rw(m, S.FP32, yd, tm, llm, lpm, None,
+                        torch.zeros((spec.d, spec.d), dtype=torch.float64, device="cuda"), 1.0, 5, 1, 0)
+            torch.cuda.synchronize()
+            rec[f"loglik_{cname}"] = {"likelihood_kernel": _err_stats(ll.cpu().numpy(), ll_o),
+                                      "mutation_kernel": _err_stats(llm.cpu().numpy(), ll_o)}
+        runs = []
+        J, N = 64, 256
+        for k in range(seeds):
+            th0 = I.draw_prior(mean, sd, lo, J * N, seed=w.prior_seed + 500 + k)
+            res = {}
+            for prec in (S.FP64, S.FP32):
+                ctx = S.init(m, S.config_default(J=J, N=N, precision=prec, seed=77 + k), y, th0)
+                t0 = time.perf_counter()
+                ctx.run()
+                lml = ctx.log_ml()
+                el = time.perf_counter() - t0
+                res[prec] = (lml, ctx.moments(), el)
+                ctx.close()
+            (l64, n64, _), m64, t64 = res[S.FP64]
+            (l32, n32, _), m32, t32 = res[S.FP32]
+            dm = np.abs(m32[:, 0] - m64[:, 0]) / m64[:, 2]
+            runs.append({"log_ml_fp64": l64, "nse_fp64": n64, "log_ml_fp32": l32, "nse_fp32": n32,
+                         "log_ml_diff": l32 - l64, "log_ml_diff_in_nse": (l32 - l64) / n64,
+                         "max_mean_diff_in_nse": float(dm.max()), "seconds_fp64": t64, "seconds_fp32": t32})
+        rec["runs_same_seed_J64_N256"] = runs
+        out["shapes"][name] = rec
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -301,9 +445,22 @@ def main():
     from paper_1304_4334_gb300 import inputs as I
     from paper_1304_4334_gb300 import smc as S
 
+    if args.peaks:
+        if rank == 0:
+            print(json.dumps({"peaks": S.peaks(), "unit": "lane operations per SM and clock "
+                              "(issue: warp instructions per SM and clock)"}), flush=True)
+        return
+    if args.precision:
+        if rank == 0:
+            print(json.dumps(precision_report(S, I)), flush=True)
+        return
     if args.workload == "batched32":
         return run_batched(args, world, rank, local)
     w = I.WORKLOADS[args.workload]
+    if args.particles:
+        import dataclasses
+        J_, N_ = (int(v) for v in args.particles.split(","))
+        w = dataclasses.replace(w, J=J_, N=N_)
     y = w.data()
     m = S.model_egarch(w.K, w.I, w.gamma)
     mean, sd, lo = S.model_prior(m)
@@ -324,6 +481,8 @@ def main():
     else:
         shape = ctx.autotune(iters=2) if not mala else (1, 128, None)
     seed_of = lambda k: 1 + rank + 7919 * k
+    # ALU pipe rates of this device (a few ms of microbenchmark kernels)
+    rates = {k: v for k, v in S.peaks(stream.cuda_stream).items() if k != "sms"}
 
     def one_run(k):
         ctx.reset(th0_dev, seed_of(k), theta0_on_device=True)
@@ -410,13 +569,20 @@ def main():
     mhz, src = sm_max_mhz()
     paired = shape[0] == 2
     # MALA's bound counts its forward, recomputation and reverse sweep per
-    # evaluation (mala_ops_per_eval)
-    peak, pipe = alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, mhz, paired, mala)
+    # evaluation (mala_ops_per_eval).  The pipe rates per SM and clock are
+    # those the microbenchmark measured on this device before the timed region
+    # (smc_peaks), at the maximum SM clock; the nominal rates give a second bound.
+    peak, pipe = alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, mhz, paired, mala, rates=rates)
+    peak_nom, pipe_nom = alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, mhz, paired, mala)
     avg_launch_s = (mut_ms / mut_n) / 1e3 if mut_n else float("nan")
     achieved = w.P * w.T / avg_launch_s if mut_n else float("nan")
     fp32_ops, mufu_ops = (mala_ops_per_eval if mala else alu_ops_per_eval)(w.K, w.I, w.gamma)
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
-            "frac": achieved / peak, "traffic": traffic, "pipe": pipe, "peak_source": f"{src} SM clock {mhz:.0f} MHz x {SM_COUNT_GB300} SMs",
+            "frac": achieved / peak, "traffic": traffic, "pipe": pipe,
+            "peak_source": (f"pipe rates measured by smc_peaks on this device x {src} SM clock "
+                            f"{mhz:.0f} MHz x {SM_COUNT_GB300} SMs"),
+            "measured_rates": rates, "peak_nominal": peak_nom / 1e9, "pipe_nominal": pipe_nom,
+            "frac_nominal": achieved / peak_nom,
             "ops_per_eval": {"fp32": fp32_ops, "mufu": mufu_ops},
             "kernel": (f"k_mutate_mala<GradEgarch<float,{w.K},{w.I}>>" if mala
                        else f"k_mutate_x2<{w.K},{w.I}>" if paired
@@ -428,11 +594,11 @@ def main():
                              "autotune_ms_per_iteration": shape[2]}}
     if clk.get("sm_mhz"):
         roof["frac_at_median_clock"] = achieved / alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, clk["sm_mhz"],
-                                                                 paired, mala)[0]
+                                                                 paired, mala, rates=rates)[0]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_oracle_rate(w, y)
+        cpu = cpu_baseline_leg(w, y)
     eq = None
     if rank == 0 and not args.no_equal_nse and args.cycles == 0 and w.name in ("egarch22_T5000", "egarch34_T20000"):
         eq = equal_nse_comparison(S, w, y, th0, stream, args.equal_nse_seeds)
@@ -441,10 +607,11 @@ def main():
         line = {"metric": "M-phase particle*obs lik evals/s", "value": value,
                 "unit": "particle*obs lik evals/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": w.precision,
                 "data": "synthetic",
                 "config": {"workload": w.name, "K": w.K, "I": w.I, "T": w.T, "J": w.J, "N": w.N,
-                           "precision": "fp32 recursion, fp64 accumulators", "tempering": "power",
+                           "precision": ("fp32 recursion, fp64 accumulators" if w.precision == "f32"
+                                         else "fp64 throughout"), "tempering": "power",
                            "sampler": w.mutation, "stop_rule": f"deterministic Rbar={w.rbar} kappa={w.kappa}",
                            "cycles_per_run": cycles, "metropolis_steps_per_run": msteps,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},

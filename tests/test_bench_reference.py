@@ -20,7 +20,7 @@ def test_reference_arm_json_line():
     assert line["higher_is_better"] is True and line["steps"] == 1 and line["warmup"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
-    assert line["config"]["workload"] == "egarch22_T5000" and line["data"] == "synthetic"
+    assert line["config"]["workload"] == "egarch34_T20000" and line["data"] == "synthetic"
 
 
 def test_roofline_operation_counts():
@@ -39,3 +39,8 @@ def test_roofline_operation_counts():
     assert pipe2 == "fp32" and abs(peak2 - f * 128 / 20) < 1e-3 * peak2
     fm, mm = bench.mala_ops_per_eval(2, 2, True)
     assert fm > 20 and mm > 2
+    # measured rates replace the nominal ones pipe by pipe
+    peak3, pipe3 = bench.alu_peak_evals(2, 2, True, 152, 2070.0, rates={"issue": 3.0, "ffma": 100.0})
+    assert pipe3 == "issue" and abs(peak3 - f * 96 / 22) < 1e-3 * peak3
+    peak4, pipe4 = bench.alu_peak_evals(3, 4, True, 152, 2070.0, rates={"ex2": 8.0})
+    assert pipe4 == "mufu" and abs(peak4 - f * 8 / 5) < 1e-3 * peak4
