@@ -29,8 +29,8 @@ constexpr double kSqrt2OverPi = 0.79788456080286535588;
 constexpr double kLn2 = 0.69314718055994530942;
 constexpr double kLog2e = 1.44269504088896340736;
 constexpr double kSfac = 0.84932180028801904272;       // (log2(e) / 2)^1/2
-constexpr double kLog2Sfac = -0.23556494171288733624;  // log2 of kSfac
-constexpr double kLogSfac = -0.16328232405373808766;   // ln of kSfac
+constexpr double kLog2Sfac = -0.23561681352755119288;  // log2 of kSfac
+constexpr double kLogSfac = -0.16331712998914049120;   // ln of kSfac
 
 // Device view of a model, passed by value in kernel parameters so that every
 // thread reads it through the uniform constant path.
@@ -173,10 +173,20 @@ __device__ __forceinline__ void egarch_transform(const Real* th, int has_gamma,
 // so it overlaps the previous exponential) and the shock terms, which keeps
 // the per-observation dependency chain to two FMAs, one add, one ex2 and one
 // multiply.
-template <int K, int I>
+//
+// kDelta (the stand-alone likelihood and the data-tempering C phase, which
+// see raw prior draws): alpha_k = tanh(theta_3k) close to 1 loses most of
+// 1 - alpha_k when rounded to FP32 (its ulp is 6e-8, so 1 - alpha = 1e-3 keeps
+// only ~4 digits), and the recursion's long memory 1 / (1 - alpha) turns that
+// into a systematic error of the volatility level.  This form carries
+// delta_k = 1 - alpha_k = 2 / (1 + e^(2 theta_3k)), formed directly in FP32
+// (relative error ~1e-7), and updates alpha v as v - delta v (one FMA, single
+// rounding); lsy2p then stays out of the first factor and enters log2 h as
+// its own term.  Two more FP32 operations per observation.
+template <int K, int I, bool kDelta = false>
 struct EgarchF32 {
     float mu, lsy2p;                       // mu_Y; log2 sigma_Y - log2 s
-    float al[K], be[K], ga[K], nb[K];      // alpha; beta, gamma in scaled units; constant term
+    float al[K], be[K], ga[K], nb[K];      // alpha (kDelta: 1 - alpha); beta, gamma in scaled units; constant term
     float a[I], b[I], c[I];                // 1/sigma_i; -mu_i s / sigma_i; log2(p_i / sigma_i)
     float v0[K];                           // state after the first observation's update
     float v[K], es;                        // recursion state (scaled units; v[0] includes lsy2p)
@@ -192,15 +202,18 @@ struct EgarchF32 {
         lsy2p = q.log_sigma_y * (float)kLog2e - (float)kLog2Sfac;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            al[k] = q.alpha[k];
+            // theta_3k sits at index 2 + k (Table 1 order)
+            al[k] = kDelta ? 2.0f / (1.0f + expf(2.0f * th[2 + k])) : q.alpha[k];
             be[k] = q.beta[k] * (float)(kLog2e / 2.0 / kSfac);
             ga[k] = q.gamma[k] * (float)(kLog2e / 2.0 / kSfac);
             const float c0 = -q.beta[k] * (float)(kSqrt2OverPi * kLog2e / 2.0);
             nb[k] = c0;
             v0[k] = eps0_zero ? c0 : 0.0f;
         }
-        nb[0] = fmaf(1.0f - al[0], lsy2p, nb[0]);
-        v0[0] += lsy2p;
+        if constexpr (!kDelta) {
+            nb[0] = fmaf(1.0f - al[0], lsy2p, nb[0]);
+            v0[0] += lsy2p;
+        }
 #pragma unroll
         for (int i = 0; i < I; ++i) {
             a[i] = 1.0f / q.sig[i];
@@ -224,7 +237,10 @@ struct EgarchF32 {
     {
         float vp[K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) vp[k] = fmaf(al[k], v[k], nb[k]);
+        for (int k = 0; k < K; ++k) {
+            if constexpr (kDelta) vp[k] = fmaf(-al[k], v[k], v[k]) + nb[k];
+            else vp[k] = fmaf(al[k], v[k], nb[k]);
+        }
         const float ae = fabsf(es);
 #pragma unroll
         for (int k = 0; k < K; ++k) v[k] = fmaf(be[k], ae, fmaf(ga[k], es, vp[k]));
@@ -233,7 +249,7 @@ struct EgarchF32 {
     // e = log2 h_t - log2 s
     __device__ __forceinline__ float log2h() const
     {
-        float e = v[0];
+        float e = kDelta ? lsy2p + v[0] : v[0];
 #pragma unroll
         for (int k = 1; k < K; ++k) e += v[k];
         return e;
@@ -292,7 +308,7 @@ struct EgarchF32 {
     {
 #pragma unroll
         for (int k = 0; k < K; ++k) v[k] = (float)(st[k] * (kLog2e / 2.0));
-        v[0] += lsy2p;
+        if constexpr (!kDelta) v[0] += lsy2p;
         es = (float)(st[K] * kSfac);
     }
 
@@ -350,7 +366,7 @@ struct EgarchF32 {
 
     __device__ __forceinline__ void state_out(double* st) const
     {
-        st[0] = (double)(v[0] - lsy2p) * (2.0 * kLn2);
+        st[0] = (double)(kDelta ? v[0] : v[0] - lsy2p) * (2.0 * kLn2);
 #pragma unroll
         for (int k = 1; k < K; ++k) st[k] = (double)v[k] * (2.0 * kLn2);
         st[K] = (double)es / kSfac;
@@ -545,8 +561,8 @@ constexpr int kChunkF64 = 512;    // elements per staged chunk (4 KB)
 // through `pipe`.  Every thread of the block must call it (it contains block
 // barriers); `active` selects whose result matters.  Returns false on a
 // staging timeout.
-template <int K, int I>
-__device__ __forceinline__ bool run_egarch_f32(EgarchF32<K, I>& mdl, ObsPipe<float, kChunkF32>& pipe,
+template <int K, int I, bool kDelta>
+__device__ __forceinline__ bool run_egarch_f32(EgarchF32<K, I, kDelta>& mdl, ObsPipe<float, kChunkF32>& pipe,
                                                int T)
 {
     for (int c = 0; c < pipe.nchunks; ++c) {
