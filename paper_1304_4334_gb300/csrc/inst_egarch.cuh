@@ -84,7 +84,9 @@ cudaError_t launch_cdata_k(const CdataArgs& a, cudaStream_t s)
 
 }  // namespace smc
 
-#define SMC_INSTANTIATE_EGARCH(TAG, POL, K)                                                     \
+// POL: the mutation kernels' policy; POL_EVAL: the stand-alone likelihood's
+// and the data-tempering C phase's.
+#define SMC_INSTANTIATE_EGARCH(TAG, POL, POL_EVAL, K)                                           \
     namespace smc {                                                                             \
     cudaError_t launch_mutate_##TAG##_k##K(const MutateArgs& a, int threads, cudaStream_t s)    \
     {                                                                                           \
@@ -92,10 +94,10 @@ cudaError_t launch_cdata_k(const CdataArgs& a, cudaStream_t s)
     }                                                                                           \
     cudaError_t launch_loglik_##TAG##_k##K(const LoglikArgs& a, cudaStream_t s)                 \
     {                                                                                           \
-        return launch_loglik_k<POL, K>(a, s);                                                   \
+        return launch_loglik_k<POL_EVAL, K>(a, s);                                              \
     }                                                                                           \
     cudaError_t launch_cdata_##TAG##_k##K(const CdataArgs& a, cudaStream_t s)                   \
     {                                                                                           \
-        return launch_cdata_k<POL, K>(a, s);                                                    \
+        return launch_cdata_k<POL_EVAL, K>(a, s);                                               \
     }                                                                                           \
     }

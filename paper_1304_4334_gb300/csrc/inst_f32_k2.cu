@@ -1,6 +1,6 @@
 // FP32 EGARCH kernels with K = 2 volatility factors, I = 1..4 mixture components.
 #include "inst_egarch.cuh"
-SMC_INSTANTIATE_EGARCH(f32, PolicyEgarchF32, 2)
+SMC_INSTANTIATE_EGARCH(f32, PolicyEgarchF32, PolicyEgarchF32Delta, 2)
 namespace smc {
 cudaError_t launch_mutate_x2_f32_k2(const MutateArgs& a, int threads, cudaStream_t s)
 {

@@ -131,12 +131,12 @@ __device__ __forceinline__ void pit_setup_egarch(const ModelDev& m, const double
     }
 }
 
-template <int K, int I>
-struct PolicyEgarchF32 {
+template <int K, int I, bool kDelta>
+struct PolicyEgarchF32T {
     using Real = float;
     using Obs = float;
     static constexpr int kChunk = kChunkF32;
-    using Model = EgarchF32<K, I>;
+    using Model = EgarchF32<K, I, kDelta>;
     static constexpr int kNs = K + 1;
     static constexpr int kMaxFree = I == 1 ? 2 + 3 * K : 2 + 3 * K + 3 * I;   // Table 1
     __device__ static void setup(Model& mdl, const ModelDev& m, const Real* full)
@@ -156,6 +156,14 @@ struct PolicyEgarchF32 {
     // observed standardized shock after logdens of observation s
     __device__ static double obs_shock(const Model& mdl, const Obs*, int, int) { return (double)mdl.es * (1.0 / kSfac); }
 };
+
+// The FP32 recursion of the M phase (alpha v as one FMA) and, for the kernels
+// that see raw prior draws (the stand-alone likelihood and the data-tempering
+// C phase), the form that carries 1 - alpha (EgarchF32's kDelta).
+template <int K, int I>
+struct PolicyEgarchF32 : PolicyEgarchF32T<K, I, false> {};
+template <int K, int I>
+struct PolicyEgarchF32Delta : PolicyEgarchF32T<K, I, true> {};
 
 template <int K, int I>
 struct PolicyEgarchF64 {

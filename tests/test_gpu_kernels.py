@@ -68,12 +68,14 @@ def test_loglik_fp32_matches_oracle(S, K, I_, gamma, T, P):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_loglik_prior_draws(S, precision):
     """Raw prior draws reach extreme volatility dynamics.  FP64 must match to
-    1e-9 relative.  In FP32 a draw with persistence 1 - alpha ~ 1e-3 and a
-    large beta amplifies the FP32 rounding of alpha and eps through the
-    recursion (an FP32 emulation in numpy shows the same error), so for raw
-    prior draws the bound is stated against sum_t |l_t|: at most 5e-3 of it
-    (1.4e-3 is the worst seen), with 90% of draws within 1e-4 relative
-    (94% measured).
+    1e-9 relative.  The FP32 likelihood kernel carries 1 - alpha_k itself
+    (alpha close to 1 would lose it in FP32 rounding), which leaves the
+    draws whose recursion amplifies any rounding: a large beta_k feeds each
+    shock's error back into the next volatility, and a likelihood that is a
+    small difference of large terms (|sum_t l_t| << sum_t |l_t|) shows its
+    absolute error as a large relative one.  The bound for raw prior draws is
+    therefore 99% of draws within 1e-4 relative and every draw within 1e-3 of
+    sum_t |l_t|; the measured figures are printed.
     Where the oracle value is below -1e7 (a weight of zero at any precision)
     FP32 may saturate to -inf."""
     prec = S.FP64 if precision == "fp64" else S.FP32
@@ -91,9 +93,12 @@ def test_loglik_prior_draws(S, precision):
                        frac_prior=1.0)
         mag = np.array([np.abs(O.loglik_terms(spec, y, th[n])).sum() for n in range(1000)])
         err = np.abs(ll - ll_o)
-        assert np.all(err[sane] <= 5e-3 * mag[sane]), (err[sane] / mag[sane]).max()
+        rel = err[sane] / np.abs(ll_o[sane])
+        print(f"FP32 raw prior draws: max rel {rel.max():.2e}, median {np.median(rel):.2e}, "
+              f"share <= 1e-4 {(rel <= 1e-4).mean():.4f}, max err / sum|l_t| {(err[sane] / mag[sane]).max():.2e}")
+        assert np.all(err[sane] <= 1e-3 * mag[sane]), (err[sane] / mag[sane]).max()
         within = err[sane] <= 1e-4 * np.abs(ll_o[sane]) + 1e-4
-        assert within.mean() >= 0.9, within.mean()
+        assert within.mean() >= 0.99, within.mean()
     assert np.all(ll[~sane] < -1e6)
 
 
