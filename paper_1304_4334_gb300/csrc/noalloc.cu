@@ -9,12 +9,21 @@
 // cudaMallocAsync.  The caller still passes theta and the outputs.
 //
 // The scratch is one file-scope __device__ array, so every process that loads
-// the library holds it on every device it uses until exit (about 1.1 MB).
+// the library holds it on every device it uses until exit (about 2.3 MB).
 // All calls on a device share it and it keeps the last call's contents: each
 // call writes every partial sum it later reads, and the reduction's counter in
 // the last element returns to zero at the end of each call, so nothing needs
 // clearing; but two calls whose kernels overlap on the GPU (different streams
 // without ordering between them) race on it and must not be issued.
+// Back-to-back calls on one stream are ordered although the reduction kernel
+// lets the next launch start early (programmatic dependent launch): both the
+// partial-sum kernel and the reduction wait for their predecessor
+// (griddepcontrol.wait) before their first access to the array, and any kernel
+// added to this path must do the same.
+// The block count is the allocating entry point's (cov_grid: at most two blocks
+// per SM), so on any device with up to 256 SMs both split the particles the
+// same way and their results are identical; beyond that it is capped at
+// kNoAllocCovBlocks and the results agree within FP rounding of the sums.
 #include "../../include/smc.h"
 #include "phase.cuh"
 
@@ -24,7 +33,7 @@ namespace smc {
 
 // Block partials of the covariance kernel: at most kNoAllocCovBlocks blocks
 // plus one row of totals, each row holding d + d(d+1)/2 sums for d <= kMaxD.
-constexpr int kNoAllocCovBlocks = 256;
+constexpr int kNoAllocCovBlocks = 512;
 constexpr int kNoAllocCovRow = kMaxD + kMaxD * (kMaxD + 1) / 2;
 constexpr size_t kNoAllocScratchDoubles = (size_t)(kNoAllocCovBlocks + 1) * kNoAllocCovRow;
 
@@ -40,7 +49,10 @@ double* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  The host-side
 // name of a __device__ variable is only a stand-in, so the address is looked up
-// once per device (with that device current) and cached.
+// once per device (with that device current) and cached.  The cache assumes the
+// device's context lives as long as the process: after cudaDeviceReset (which
+// unloads the module holding the array) the cached address is stale, so this
+// entry point must not be called again in that process.
 cudaError_t scratch_on_current_device(double** out)
 {
     int dev = 0;
