@@ -37,7 +37,7 @@ def _linreg():
 @pytest.mark.parametrize("tempering", ["power", "data"])
 def test_hybrid_on_gpu(S, tempering):
     X, y, m0, s0, lml, mn, Vn = _linreg()
-    J, N = 16, 512
+    J, N = 32, 256
     m = S.model_linreg(3, 1.0, m0, s0)
     tm = S.POWER if tempering == "power" else S.DATA
     th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), J * N, seed=5)
@@ -65,12 +65,12 @@ def test_hybrid_on_gpu(S, tempering):
     lm, nse, _ = c.log_ml()
     mom = c.moments()
     c.close()
-    assert abs(lm - lml) < 4.0 * nse + 0.02, (lm, lml, nse)
+    assert abs(lm - lml) < 3 * nse, (lm, lml, nse)
     for i in range(3):
-        assert abs(mom[i, 0] - mn[i]) < 4.0 * mom[i, 2] + 1e-4
+        assert abs(mom[i, 0] - mn[i]) < 3 * mom[i, 2]
     # the oracle replaying the GPU's design
     spec = O.ModelSpec(model=O.LINREG, p=3, sigma=1.0, prior_mean=m0, prior_sd=s0)
     r = O.smc_run(spec, y, th1, J, N, X=X, tempering=1 if tempering == "power" else 0, seed=99,
                   design=design)
     assert r["status"] == 0 and r["cycles"] == len(design["x"])
-    assert abs(r["log_ml"] - lm) < 4.0 * math.hypot(r["log_ml_nse"], nse) + 0.02
+    assert abs(r["log_ml"] - lm) < 3 * math.hypot(r["log_ml_nse"], nse)

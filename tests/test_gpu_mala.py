@@ -187,7 +187,7 @@ def _linreg():
 @pytest.mark.parametrize("tempering", ["power", "data"])
 def test_mala_linreg_run_matches_closed_form(S, tempering):
     X, y, m0, s0, lml, mn, Vn = _linreg()
-    J, N = 16, 512
+    J, N = 32, 256
     m = S.model_linreg(3, 1.0, m0, s0)
     c = S.config_default(J=J, N=N, precision=S.FP64, mutation=S.MALA, acc_target=0.5, seed=17,
                          tempering=S.POWER if tempering == "power" else S.DATA)
@@ -197,9 +197,9 @@ def test_mala_linreg_run_matches_closed_form(S, tempering):
     lm, nse, _ = ctx.log_ml()
     mom = ctx.moments()
     ctx.close()
-    assert abs(lm - lml) < 3.5 * nse + 0.02, (lm, lml, nse)
+    assert abs(lm - lml) < 3 * nse, (lm, lml, nse)
     for i in range(3):
-        assert abs(mom[i, 0] - mn[i]) < 3.5 * mom[i, 2] + 1e-4
+        assert abs(mom[i, 0] - mn[i]) < 3 * mom[i, 2]
         assert mom[i, 1] == pytest.approx(math.sqrt(Vn[i, i]), rel=0.1)
 
 
@@ -215,7 +215,7 @@ def test_mala_one_parameter_egarch_matches_quadrature(S):
     Z = integrate.simpson(wq, dx=grid[1] - grid[0])
     lml = mx + math.log(Z)
     pmean = integrate.simpson(wq * grid, dx=grid[1] - grid[0]) / Z
-    J, N = 16, 256
+    J, N = 32, 128
     m = S.model_egarch(1, 1, True, free_idx=[1], theta_fixed=th_true)
     c = S.config_default(J=J, N=N, precision=S.FP32, mutation=S.MALA, acc_target=0.5, seed=3)
     th0 = I.draw_prior([math.log(0.01)], [1.0], [-np.inf], J * N, seed=41)
@@ -224,8 +224,8 @@ def test_mala_one_parameter_egarch_matches_quadrature(S):
     lm, nse, _ = ctx.log_ml()
     mom = ctx.moments()
     ctx.close()
-    assert abs(lm - lml) < 3.5 * nse + 0.01, (lm, lml, nse)
-    assert abs(mom[0, 0] - pmean) < 3.5 * mom[0, 2] + 1e-4
+    assert abs(lm - lml) < 3 * nse, (lm, lml, nse)
+    assert abs(mom[0, 0] - pmean) < 3 * mom[0, 2]
 
 
 def test_mala_and_rw_runs_agree(S):
@@ -233,7 +233,7 @@ def test_mala_and_rw_runs_agree(S):
     y = I.simulate_egarch(truth, 800, seed=8)
     m = S.model_egarch(2, 2, True)
     mean, sd, lo = S.model_prior(m)
-    J, N = 16, 512
+    J, N = 32, 256
     th0 = I.draw_prior(mean, sd, lo, J * N, seed=9)
     res = {}
     for mut in (S.RW, S.MALA):
@@ -245,6 +245,6 @@ def test_mala_and_rw_runs_agree(S):
         ctx.close()
     (lr, nr, _), mr = res[S.RW]
     (lm_, nm, _), mm = res[S.MALA]
-    assert abs(lr - lm_) < 4 * math.hypot(nr, nm) + 0.05, (lr, lm_, nr, nm)
+    assert abs(lr - lm_) < 3 * math.hypot(nr, nm), (lr, lm_, nr, nm)
     for f in range(mr.shape[0]):
-        assert abs(mr[f, 0] - mm[f, 0]) < 4 * math.hypot(mr[f, 2], mm[f, 2]) + 1e-3, f
+        assert abs(mr[f, 0] - mm[f, 0]) < 3 * math.hypot(mr[f, 2], mm[f, 2]), f

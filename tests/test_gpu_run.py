@@ -40,7 +40,7 @@ def _linreg(T=60, seed=3):
                                                 ("systematic", "data")])
 def test_linreg_run_matches_closed_form(S, resampler, tempering):
     X, y, m0, s0, lml, mn, Vn = _linreg()
-    J, N = 16, 512
+    J, N = 32, 256
     m = S.model_linreg(3, 1.0, m0, s0)
     c = S.config_default(J=J, N=N, precision=S.FP64, seed=11,
                          tempering=S.POWER if tempering == "power" else S.DATA,
@@ -53,11 +53,12 @@ def test_linreg_run_matches_closed_form(S, resampler, tempering):
     if tempering == "data":
         assert info["t"] == len(y)
     lm, nse, lt = ctx.log_ml()
-    assert abs(lm - lml) < 3.5 * nse + 0.02, (lm, lml, nse)
-    assert abs(lt - lml) < 5 * nse + 0.03
+    assert abs(lm - lml) < 3 * nse, (lm, lml, nse)
+    # log wtilde has no NSE of its own; its spread is that of log wbar
+    assert abs(lt - lml) < 4 * nse
     mom = ctx.moments()
     for i in range(3):
-        assert abs(mom[i, 0] - mn[i]) < 3.5 * mom[i, 2] + 1e-4
+        assert abs(mom[i, 0] - mn[i]) < 3 * mom[i, 2]
         assert mom[i, 1] == pytest.approx(math.sqrt(Vn[i, i]), rel=0.1)
     ctx.close()
 
@@ -68,7 +69,7 @@ def test_linreg_independent_sampler_matches_closed_form(S, tempering):
     population) reaches the exact log ML and posterior means; the hybrid
     design cannot be recorded for it."""
     X, y, m0, s0, lml, mn, Vn = _linreg()
-    J, N = 16, 512
+    J, N = 32, 256
     m = S.model_linreg(3, 1.0, m0, s0)
     c = S.config_default(J=J, N=N, precision=S.FP64, seed=12, mutation=S.INDEP,
                          tempering=S.POWER if tempering == "power" else S.DATA)
@@ -77,10 +78,10 @@ def test_linreg_independent_sampler_matches_closed_form(S, tempering):
     n, info = ctx.run()
     assert info["done"] == 1
     lm, nse, lt = ctx.log_ml()
-    assert abs(lm - lml) < 3.5 * nse + 0.02, (lm, lml, nse)
+    assert abs(lm - lml) < 3 * nse, (lm, lml, nse)
     mom = ctx.moments()
     for i in range(3):
-        assert abs(mom[i, 0] - mn[i]) < 3.5 * mom[i, 2] + 1e-4
+        assert abs(mom[i, 0] - mn[i]) < 3 * mom[i, 2]
     ctx.close()
     ctx = S.init(m, c, y, th0, X=X)
     with pytest.raises(S.SMCError):
@@ -95,7 +96,7 @@ def test_independent_sampler_egarch_matches_oracle_run(S):
     y = w.data()[:300]
     m = S.model_egarch(1, 1, False)
     mean, sd, lo = S.model_prior(m)
-    J, N = 8, 256
+    J, N = 32, 128
     th0 = I.draw_prior(mean, sd, lo, J * N, seed=71)
     ctx = S.init(m, S.config_default(J=J, N=N, precision=S.FP64, seed=3, mutation=S.INDEP), y, th0)
     ctx.run()
@@ -105,7 +106,7 @@ def test_independent_sampler_egarch_matches_oracle_run(S):
     r = O.smc_run(spec, y, th0, J, N, tempering=1, mutation=O.INDEP, seed=3, nthreads=8)
     assert r["status"] == 0
     comb = math.hypot(nse, r["log_ml_nse"])
-    assert abs(lm - r["log_ml"]) < 4 * comb + 0.02, (lm, r["log_ml"], comb)
+    assert abs(lm - r["log_ml"]) < 3 * comb, (lm, r["log_ml"], comb)
 
 
 @pytest.mark.parametrize("precision,tempering", [("fp64", "power"), ("fp32", "power"), ("fp32", "data")])
@@ -122,7 +123,7 @@ def test_one_parameter_egarch_matches_quadrature(S, precision, tempering):
     Z = integrate.simpson(wq, dx=dx)
     lml = mx + math.log(Z)
     pmean = integrate.simpson(wq * grid, dx=dx) / Z
-    J, N = 16, 256
+    J, N = 32, 128
     m = S.model_egarch(1, 1, True, free_idx=[1], theta_fixed=th_true)
     c = S.config_default(J=J, N=N, precision=S.FP64 if precision == "fp64" else S.FP32, seed=3,
                          tempering=S.POWER if tempering == "power" else S.DATA)
@@ -131,8 +132,8 @@ def test_one_parameter_egarch_matches_quadrature(S, precision, tempering):
     ctx.run()
     lm, nse, _ = ctx.log_ml()
     mom = ctx.moments()
-    assert abs(lm - lml) < 3.5 * nse + 0.01, (lm, lml, nse)
-    assert abs(mom[0, 0] - pmean) < 3.5 * mom[0, 2] + 1e-4
+    assert abs(lm - lml) < 3 * nse, (lm, lml, nse)
+    assert abs(mom[0, 0] - pmean) < 3 * mom[0, 2]
     ctx.close()
 
 
@@ -140,27 +141,38 @@ def test_one_parameter_egarch_matches_quadrature(S, precision, tempering):
 def test_egarch11_small_run_agrees_with_oracle(S, tempering):
     """EGARCH(1,1), Gaussian shocks, 4 parameters, T = 500, J = 4 x N = 256,
     FP64, 10 Metropolis steps per M phase: GPU and oracle runs agree on log ML
-    and posterior means within combined NSE."""
+    and posterior means within 3 combined NSE.  With J = 4 a single run's NSE
+    rests on 3 degrees of freedom, so each side runs 8 seeds (own prior draws
+    and random numbers) and their averages are compared, with the NSE of an
+    average sqrt(sum NSE_k^2) / 8."""
     w = I.WORKLOADS["egarch11_T500"]
     y = w.data()
     m = S.model_egarch(1, 1, False)
     mean, sd, lo = S.model_prior(m)
-    th0 = I.draw_prior(mean, sd, lo, w.P, seed=w.prior_seed)
-    tmode = S.POWER if tempering == "power" else S.DATA
-    c = S.config_default(J=w.J, N=w.N, precision=S.FP64, rbar=10, kappa=1, seed=7, tempering=tmode)
-    ctx = S.init(m, c, y, th0)
-    ctx.run()
-    lm, nse, _ = ctx.log_ml()
-    mom = ctx.moments()
-    ctx.close()
     spec = O.ModelSpec(K=1, I=1, gamma=False)
-    r = O.smc_run(spec, y, th0, w.J, w.N, rbar=10, kappa=1, seed=7, nthreads=8,
-                  tempering=1 if tempering == "power" else 0)
-    tol = lambda a, b: 4.0 * math.hypot(a, b) + 0.02
-    assert abs(lm - r["log_ml"]) < tol(nse, r["log_ml_nse"]), (lm, r["log_ml"], nse, r["log_ml_nse"])
-    for i in range(4):
-        mo, _, no, _ = O.moment(r["theta"][:, i], w.J, w.N)
-        assert abs(mom[i, 0] - mo) < tol(mom[i, 2], no) + 1e-3, (i, mom[i], mo, no)
+    tmode = S.POWER if tempering == "power" else S.DATA
+    n = 8
+    g_lm, g_n, o_lm, o_n = [], [], [], []
+    g_m, g_mn, o_m, o_mn = [], [], [], []
+    for k in range(n):
+        th0 = I.draw_prior(mean, sd, lo, w.P, seed=w.prior_seed + 100 * k)
+        c = S.config_default(J=w.J, N=w.N, precision=S.FP64, rbar=10, kappa=1, seed=7 + k, tempering=tmode)
+        ctx = S.init(m, c, y, th0)
+        ctx.run()
+        lm, nse, _ = ctx.log_ml()
+        mom = ctx.moments()
+        ctx.close()
+        g_lm.append(lm); g_n.append(nse); g_m.append(mom[:4, 0]); g_mn.append(mom[:4, 2])
+        r = O.smc_run(spec, y, th0, w.J, w.N, rbar=10, kappa=1, seed=1007 + k, nthreads=8,
+                      tempering=1 if tempering == "power" else 0)
+        o_lm.append(r["log_ml"]); o_n.append(r["log_ml_nse"])
+        mo = [O.moment(r["theta"][:, i], w.J, w.N) for i in range(4)]
+        o_m.append([x[0] for x in mo]); o_mn.append([x[2] for x in mo])
+    comb = math.sqrt(np.sum(np.square(g_n)) + np.sum(np.square(o_n))) / n
+    assert abs(np.mean(g_lm) - np.mean(o_lm)) < 3 * comb, (np.mean(g_lm), np.mean(o_lm), comb)
+    combm = np.sqrt(np.sum(np.square(g_mn), axis=0) + np.sum(np.square(o_mn), axis=0)) / n
+    dm = np.abs(np.mean(g_m, axis=0) - np.mean(o_m, axis=0))
+    assert np.all(dm < 3 * combm), (dm, combm)
 
 
 def test_fp32_and_fp64_runs_agree(S):
@@ -168,7 +180,7 @@ def test_fp32_and_fp64_runs_agree(S):
     y = I.simulate_egarch(truth, 1000, seed=8)
     m = S.model_egarch(2, 2, True)
     mean, sd, lo = S.model_prior(m)
-    J, N = 16, 512
+    J, N = 32, 256
     th0 = I.draw_prior(mean, sd, lo, J * N, seed=9)
     res = {}
     for prec in (S.FP64, S.FP32):
@@ -179,9 +191,9 @@ def test_fp32_and_fp64_runs_agree(S):
         ctx.close()
     (l64, n64, _), m64 = res[S.FP64]
     (l32, n32, _), m32 = res[S.FP32]
-    assert abs(l64 - l32) < 4 * math.hypot(n64, n32) + 0.05, (l64, l32, n64, n32)
+    assert abs(l64 - l32) < 3 * math.hypot(n64, n32), (l64, l32, n64, n32)
     for f in range(m64.shape[0]):
-        assert abs(m64[f, 0] - m32[f, 0]) < 4 * math.hypot(m64[f, 2], m32[f, 2]) + 1e-3, f
+        assert abs(m64[f, 0] - m32[f, 0]) < 3 * math.hypot(m64[f, 2], m32[f, 2]), f
 
 
 def test_full_size_run_sampled_parity(S):
@@ -217,8 +229,8 @@ def test_data_tempering_dates_of_interest(S):
     """A forced stop at a date of interest ends a cycle there even with RSS >= D1."""
     X, y, m0, s0, lml, mn, Vn = _linreg()
     m = S.model_linreg(3, 1.0, m0, s0)
-    c = S.config_default(J=8, N=256, precision=S.FP64, tempering=S.DATA, seed=4, force_dates=[37, 45])
-    th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), 8 * 256, seed=6)
+    c = S.config_default(J=32, N=128, precision=S.FP64, tempering=S.DATA, seed=4, force_dates=[37, 45])
+    th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), 32 * 128, seed=6)
     ctx = S.init(m, c, y, th0, X=X)
     ts = []
     while True:
@@ -229,15 +241,15 @@ def test_data_tempering_dates_of_interest(S):
     assert 37 in ts and 45 in ts and ts[-1] == len(y)
     assert all(b > a for a, b in zip(ts, ts[1:]))
     lm, nse, _ = ctx.log_ml()
-    assert abs(lm - lml) < 4 * nse + 0.02
+    assert abs(lm - lml) < 3 * nse
     ctx.close()
 
 
 def test_rne_stopping_rule_run(S):
     X, y, m0, s0, lml, mn, Vn = _linreg()
     m = S.model_linreg(3, 1.0, m0, s0)
-    c = S.config_default(J=8, N=256, precision=S.FP64, stop_rule=S.STOP_RNE, rmax=30, seed=4)
-    th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), 8 * 256, seed=6)
+    c = S.config_default(J=32, N=128, precision=S.FP64, stop_rule=S.STOP_RNE, rmax=30, seed=4)
+    th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), 32 * 128, seed=6)
     ctx = S.init(m, c, y, th0, X=X)
     infos = []
     while True:
@@ -247,7 +259,7 @@ def test_rne_stopping_rule_run(S):
         infos.append(inf)
     assert all(1 <= i["R"] <= 30 for i in infos)
     lm, nse, _ = ctx.log_ml()
-    assert abs(lm - lml) < 4 * nse + 0.02
+    assert abs(lm - lml) < 3 * nse
     ctx.close()
 
 
@@ -377,7 +389,7 @@ def _predictive_cdf(X, y, m0, s0):
 def test_linreg_log_score_and_pit_match_closed_forms(S):
     X, y, m0, s0, lml, mn, Vn = _linreg()
     b = 20
-    J, N = 16, 512
+    J, N = 32, 256
     m = S.model_linreg(3, 1.0, m0, s0)
     c = S.config_default(J=J, N=N, precision=S.FP64, seed=13, tempering=S.DATA, burnin=b, pit=1)
     th0 = I.draw_prior(m0, s0, np.full(3, -np.inf), J * N, seed=7)
@@ -391,9 +403,9 @@ def test_linreg_log_score_and_pit_match_closed_forms(S):
     assert b in ts
     ls, nse = ctx.log_score()
     exact = lml - _prefix_lml(X, y, m0, s0, b)
-    assert abs(ls - exact) < 3.5 * nse + 0.02, (ls, exact, nse)
+    assert abs(ls - exact) < 3 * nse, (ls, exact, nse)
     lm, lnse, _ = ctx.log_ml()
-    assert abs(lm - lml) < 3.5 * lnse + 0.02
+    assert abs(lm - lml) < 3 * lnse
     pit = ctx.pit()
     err = np.abs(pit - _predictive_cdf(X, y, m0, s0))
     assert np.all(np.isfinite(pit)) and err.max() < 0.08 and err.mean() < 0.02, (err.max(), err.mean())
@@ -401,7 +413,8 @@ def test_linreg_log_score_and_pit_match_closed_forms(S):
     # the same prior draws give the oracle's PIT up to rounding through the first cycle
     spec = O.ModelSpec(model=O.LINREG, p=3, sigma=1.0, prior_mean=m0, prior_sd=s0)
     r = O.smc_run(spec, y, th0, J, N, X=X, tempering=0, pit=True, burnin=b, seed=13)
-    t1 = min(ts[0], r["t"][0])
+    t1 = ts[0]
+    assert t1 == r["t"][0], (t1, r["t"][0])   # the first cycle stops where the oracle's does
     np.testing.assert_allclose(pit[:t1], r["pit"][:t1], rtol=0, atol=1e-9)
 
 
@@ -424,7 +437,8 @@ def test_egarch_pit_first_cycle_matches_oracle(S, precision):
     assert np.all(np.isfinite(pit[:tg])) and np.all(np.isnan(pit[tg:]))   # not yet reached
     spec = O.ModelSpec(K=1, I=2, gamma=True)
     r = O.smc_run(spec, y, th0, J, N, tempering=0, pit=True, seed=9, max_cycles=1)
-    t1 = min(tg, r["t"][0])
+    t1 = tg
+    assert t1 == r["t"][0], (t1, r["t"][0])   # the first cycle stops where the oracle's does
     tol = 1e-9 if precision == "fp64" else 2e-3
     np.testing.assert_allclose(pit[:t1], r["pit"][:t1], rtol=0, atol=tol)
 
@@ -528,11 +542,11 @@ def test_run_from_device_prior_draws_matches_closed_form(S):
     """A run started from device prior draws (smc_draw_prior, theta0 on the
     device) reaches the regression's exact log ML."""
     X, y, m0, s0, lml, mn, Vn = _linreg()
-    J, N = 16, 512
+    J, N = 32, 256
     m = S.model_linreg(3, 1.0, m0, s0)
     th0 = S.draw_prior(m, 17, J * N)
     ctx = S.init(m, S.config_default(J=J, N=N, precision=S.FP64, seed=18), y, th0, X=X, theta0_on_device=True)
     ctx.run()
     lm, nse, _ = ctx.log_ml()
-    assert abs(lm - lml) < 3.5 * nse + 0.02, (lm, lml, nse)
+    assert abs(lm - lml) < 3 * nse, (lm, lml, nse)
     ctx.close()
