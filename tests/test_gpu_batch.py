@@ -70,3 +70,138 @@ def test_batch_of_uneven_lengths_and_models_runs_to_the_posterior(S):
         assert np.isfinite(lm) and 0 <= nse < 5
         _, _, _, st = b.member(i).particles()
     b.close()
+
+
+def _replay_snapshot(ctx, th0, seed, design, ell, r):
+    """Particles of a run entering iteration r of cycle ell: a same-seed replay
+    of its recorded design cut there (Algorithm 3; the replay reproduces the
+    adaptive run bit for bit)."""
+    R = np.array(design["R"][:ell], dtype=np.int32)
+    R[ell - 1] = r
+    ctx.reset(th0, seed)
+    ctx.replay_design({"x": design["x"][:ell], "R": R, "L": design["L"][:int(R.sum())]})
+    for _ in range(ell):
+        assert ctx.cycle() is not None
+    return ctx.particles()
+
+
+def test_full_size_batch_members_match_oracle(S):
+    """The 32-dataset batch at full size (T ~ U{500..10000}, K ~ U{1,2,3},
+    I ~ U{1..4}, J = 16 x N = 1024 each, FP32):
+    - every member ends bitwise as its one-at-a-time run;
+    - for four members one Metropolis iteration (cycle 2, iteration 1) from the
+      particles the run held there equals the oracle's random-walk step with the
+      run's own proposal factor and power (Section 3.3, (Mphase_dist)):
+      identical decisions except within rounding of the threshold, identical
+      particles, log likelihoods and log priors elsewhere;
+    - the same members' log ML agrees with an oracle run of the same data
+      (J = 16 x N = 64 particles) within 3 combined NSE (Section 4.2)."""
+    import math
+    import os
+    import oracle as O
+    ws = I.batched_workloads(n=32, seed=40, J=16, N=1024)
+    models, cfgs, ys, ths = [], [], [], []
+    for k, w in enumerate(ws):
+        m = S.model_egarch(w.K, w.I, True)
+        mean, sd, lo = S.model_prior(m)
+        models.append(m)
+        cfgs.append(S.config_default(J=w.J, N=w.N, precision=S.FP32, seed=100 + k))
+        ys.append(w.data())
+        ths.append(I.draw_prior(mean, sd, lo, w.P, seed=w.prior_seed))
+    assert max(len(y) for y in ys) > 9000
+    b = S.Batch(models, cfgs, ys, ths)
+    b.autotune(iters=1)
+    b.run()
+    # one member per (K, I) class, the longest first
+    picks, seen = [], set()
+    for i in sorted(range(32), key=lambda i: -len(ys[i])):
+        key = (ws[i].K, ws[i].I > 1)
+        if key not in seen:
+            seen.add(key)
+            picks.append(i)
+    picks = picks[:4]
+    cores = os.cpu_count() or 4
+    for i in range(32):
+        ctx = S.init(models[i], cfgs[i], ys[i], ths[i])
+        ctx.record_design(8192)
+        ctx.run()
+        mem = b.member(i)
+        lm1, lm2 = ctx.log_ml(), mem.log_ml()
+        assert lm1 == lm2, (i, lm1, lm2)
+        for u, v in zip(ctx.particles(), mem.particles()):
+            np.testing.assert_array_equal(u, v)
+        design = ctx.design()
+        ctx.close()
+        if i not in picks:
+            continue
+        w = ws[i]
+        spec = O.ModelSpec(K=w.K, I=w.I, gamma=True)
+        rep = S.init(models[i], cfgs[i], ys[i], ths[i])
+        th, ll, lp, st = _replay_snapshot(rep, ths[i], cfgs[i].seed, design, 2, 1)
+        th_g, ll_g, lp_g, _ = _replay_snapshot(rep, ths[i], cfgs[i].seed, design, 2, 2)
+        rep.close()
+        Lm = design["L"][int(design["R"][0]) + 1]
+        phi = float(design["x"][1])
+        th_o, ll_o, lp_o, _, acc_o, _ = O.mutate_rw(spec, ys[i], th, ll, lp, st, Lm, phi, cfgs[i].seed, 2, 1,
+                                                    nthreads=cores)
+        acc_g = np.any(th_g != th, axis=1)
+        diff = acc_g != acc_o.astype(bool)
+        for n in np.nonzero(diff)[0]:   # only within the rounding of log alpha
+            z = O.philox_normals(cfgs[i].seed, int(n), 1, 2, spec.d)
+            prop = th[n] + Lm @ z
+            lpn = O.logprior(spec, prop)[0]
+            lln = O.loglik(spec, ys[i], prop)[0] if lpn > -np.inf else -np.inf
+            la = (lpn + phi * lln) - (lp[n] + phi * ll[n])
+            lu = O.philox_log_uniform(cfgs[i].seed, int(n), 1, 2)
+            assert abs(la - lu) < 1e-5 * phi * (abs(ll[n]) + abs(lln)) + 1e-6, (i, n, la, lu)
+        assert diff.sum() <= max(2, w.P // 1000), (i, diff.sum())
+        same = ~diff
+        assert 0.02 < acc_g.mean() < 0.98
+        # The FP32 proposal step L z: FP32 rounding of a d-term sum, each
+        # component within 2e-5 of its proposal scale (the row norm of L).  The
+        # FP32 path draws its normals by Box-Muller in FP32 from the 24-bit
+        # truncation of the same uniforms, so where a uniform is tiny (below
+        # ~1e-5, a few particles in 10^4) its normal differs visibly from the
+        # 53-bit one: such rows (at most 1 in 1000; 5 of 16,384 seen) may
+        # differ by up to 5% of the scale.
+        scale = np.sqrt((Lm ** 2).sum(axis=1))
+        dev = np.abs(th_g - th_o)
+        tight = np.all(dev <= 1e-9 * np.abs(th_o) + 2e-5 * scale, axis=1)
+        loose = same & ~tight
+        assert loose.sum() <= max(2, w.P // 1000), (i, loose.sum())
+        assert np.all(dev[loose] <= 0.05 * scale), i
+        ok = same & tight
+        np.testing.assert_allclose(ll_g[ok], ll_o[ok], rtol=1e-4)
+        np.testing.assert_allclose(lp_g[ok], lp_o[ok], rtol=1e-4, atol=1e-4)
+        # the member's log ML against an oracle run on the same data
+        lm, nse, _ = lm2
+        r = O.smc_run(spec, ys[i], ths[i][:16 * 64], 16, 64, seed=900 + i, nthreads=cores)
+        assert r["status"] == 0
+        comb = math.hypot(nse, r["log_ml_nse"])
+        assert abs(lm - r["log_ml"]) < 3 * comb, (i, lm, r["log_ml"], nse, r["log_ml_nse"])
+    b.close()
+
+
+def test_mala_batch_matches_individual_runs(S):
+    """Batched runs with the MALA mutation (the Langevin proposal from the
+    hand-written adjoint gradient) equal the same runs done one at a time,
+    particle for particle; a batch mixing mutation kinds is refused."""
+    ws, models, cfgs, ys, ths = _members(S, 5, 4, 96, seed=7)
+    cfgs = [S.config_default(J=4, N=96, precision=S.FP32, seed=100 + k, mutation=S.MALA, acc_target=0.5)
+            for k in range(len(models))]
+    b = S.Batch(models, cfgs, ys, ths)
+    b.autotune(iters=1)
+    assert b.tile in (32, 64)
+    assert b.run() >= 1
+    for i in range(len(models)):
+        ctx = S.init(models[i], cfgs[i], ys[i], ths[i])
+        ctx.run()
+        mem = b.member(i)
+        assert ctx.log_ml() == mem.log_ml(), i
+        for u, v in zip(ctx.particles(), mem.particles()):
+            np.testing.assert_array_equal(u, v)
+        ctx.close()
+    b.close()
+    mixed = [cfgs[0], S.config_default(J=4, N=96, precision=S.FP32, seed=1)] + cfgs[2:]
+    with pytest.raises(S.SMCError):
+        S.Batch(models, mixed, ys, ths)
