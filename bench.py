@@ -454,8 +454,8 @@ def main():
         if rank == 0:
             print(json.dumps(precision_report(S, I)), flush=True)
         return
-    if args.workload == "batched32":
-        return run_batched(args, world, rank, local)
+    if args.workload in ("batched32", "batched32_mala"):
+        return run_batched(args, world, rank, local, mala=args.workload == "batched32_mala")
     w = I.WORKLOADS[args.workload]
     if args.particles:
         import dataclasses
@@ -624,10 +624,13 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def run_batched(args, world, rank, local):
+def run_batched(args, world, rank, local, mala=False):
     """32 datasets (T ~ U{500..10000}, K ~ U{1,2,3}, I ~ U{1..4}), J=16 x N=1024
     each, advanced together: one persistent M-phase kernel per Metropolis
-    iteration, replayed from a captured CUDA graph; tile size autotuned."""
+    iteration, replayed from a captured CUDA graph; tile size autotuned.
+    mala=True: the same batch with the MALA mutation (FP32 + adjoint +
+    batched); the metric then counts each likelihood-and-gradient evaluation
+    once."""
     import numpy as np
     import torch
     from paper_1304_4334_gb300 import inputs as I
@@ -639,7 +642,8 @@ def run_batched(args, world, rank, local):
         m = S.model_egarch(w.K, w.I, True)
         mean, sd, lo = S.model_prior(m)
         models.append(m)
-        cfgs.append(S.config_default(J=w.J, N=w.N, precision=S.FP32, seed=100 + k))
+        cfgs.append(S.config_default(J=w.J, N=w.N, precision=S.FP32, seed=100 + k,
+                                     mutation=S.MALA if mala else S.RW, acc_target=0.5 if mala else 0.25))
         ys.append(w.data())
         ths.append(I.draw_prior(mean, sd, lo, w.P, seed=w.prior_seed))
     stream = torch.cuda.Stream()
@@ -680,7 +684,8 @@ def run_batched(args, world, rank, local):
                 "unit": "particle*obs lik evals/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "batched32", "datasets": 32, "J": 16, "N": 1024,
+                "config": {"workload": "batched32_mala" if mala else "batched32", "datasets": 32, "J": 16, "N": 1024,
+                           "sampler": "mala" if mala else "rw",
                            "T": [w.T for w in ws], "KI": [[w.K, w.I] for w in ws],
                            "tile": b.tile, "autotune_ms_per_iteration": tune_ms,
                            "cycles_per_run": cyc, "l2": "flushed between steps (256 MB write)"},

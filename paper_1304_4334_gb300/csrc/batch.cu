@@ -11,7 +11,10 @@
 // that change between cycles live in device descriptors updated once per
 // cycle.  The tile size is chosen at start-up by timing the candidates
 // (autotuner).  The C and S phases of each dataset are enqueued per dataset;
-// all datasets share one control-block read-back per phase.
+// all datasets share one control-block read-back per phase.  Runs whose
+// mutation is MALA use the batched Langevin kernel (batch_mala.cu) in place of
+// the random-walk one; one batch holds runs of one mutation kind.
+#include "batch_mala.cuh"
 #include "ctx.h"
 
 #include <algorithm>
@@ -25,10 +28,6 @@ void count_launch();
 struct BatchMemberDev {
     MutateArgs a;
     int K, I, R;
-};
-
-struct BatchItem {
-    int member, p0;
 };
 
 template <int K, int I>
@@ -92,8 +91,13 @@ struct smc_batch {
     cudaStream_t stream = nullptr;
     std::vector<smc_ctx*> m;
     std::vector<BatchMemberDev> h_mem;
+    std::vector<BatchMalaDev> h_mala;
     std::vector<CovJob> h_jobs;
     BatchMemberDev* d_mem = nullptr;
+    BatchMalaDev* d_mala = nullptr;
+    int mala = 0;                 // every run mutates by MALA
+    int Kmax = 1;
+    size_t mala_smem = 0;
     CovJob* d_jobs = nullptr;
     BatchItem* d_items = nullptr;
     int nitems = 0;
@@ -142,7 +146,12 @@ static smc_status build_items(smc_batch* b)
     BCU(cudaMalloc(&b->d_items, items.size() * sizeof(BatchItem)));
     BCU(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
     int per_sm = 0;
-    BCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mutate_batch, b->tile, 0));
+    if (b->mala) {
+        b->mala_smem = mala_batch_smem(b->Kmax, b->tile);
+        BCU(mala_batch_occupancy(b->tile, b->mala_smem, &per_sm));
+    } else {
+        BCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mutate_batch, b->tile, 0));
+    }
     b->grid = device_sm_count() * (per_sm > 0 ? per_sm : 1);
     return SMC_OK;
 }
@@ -180,6 +189,32 @@ static void fill_descriptors(smc_batch* b, const std::vector<int>& R)
         b->h_mem[i].K = c->model.K;
         b->h_mem[i].I = c->model.I;
         b->h_mem[i].R = R[i];
+        if (b->mala) {
+            MalaArgs& g = b->h_mala[i].a;
+            g.m = c->mdev;
+            g.obs = c->obs;
+            g.T = c->T;
+            g.W = c->W;
+            g.theta = c->theta[c->cur];
+            g.ll = c->ll[c->cur];
+            g.lp = c->lp[c->cur];
+            g.state = c->ns ? c->state[c->cur] : nullptr;
+            g.grad = c->grad[c->cur];
+            g.ckpt = c->ckpt;
+            g.P = c->P;
+            g.ns = c->ns;
+            g.L = c->L;
+            g.phi = c->phi;
+            g.seed = c->cfg.seed;
+            g.cycle = (uint64_t)c->cycle;
+            g.iter = 0;
+            g.acc_count = &c->ctl->acc_count;
+            g.pending = &c->ctl->pending;
+            g.err = &c->ctl->err;
+            b->h_mala[i].K = c->model.K;
+            b->h_mala[i].I = c->model.I;
+            b->h_mala[i].R = R[i];
+        }
         CovJob& j = b->h_jobs[i];
         j.theta = a.theta;
         j.d = c->d;
@@ -204,6 +239,9 @@ static smc_status upload_descriptors(smc_batch* b)
 {
     BCU(cudaMemcpyAsync(b->d_mem, b->h_mem.data(), b->n * sizeof(BatchMemberDev), cudaMemcpyHostToDevice,
                         b->stream));
+    if (b->mala)
+        BCU(cudaMemcpyAsync(b->d_mala, b->h_mala.data(), b->n * sizeof(BatchMalaDev), cudaMemcpyHostToDevice,
+                            b->stream));
     BCU(cudaMemcpyAsync(b->d_jobs, b->h_jobs.data(), b->n * sizeof(CovJob), cudaMemcpyHostToDevice,
                         b->stream));
     return SMC_OK;
@@ -214,8 +252,13 @@ static smc_status enqueue_iteration(smc_batch* b, cudaStream_t s)
 {
     BCU(cudaMemsetAsync(b->d_next, 0, sizeof(unsigned int), s));
     BCU(launch_cov_batch(b->d_jobs, b->n, b->Gmax, b->dmax, b->d_iter, s));
-    k_mutate_batch<<<b->grid, b->tile, 0, s>>>(b->d_mem, b->d_items, b->nitems, b->d_next, b->d_iter);
-    count_launch();
+    if (b->mala) {
+        BCU(launch_mala_batch(b->d_mala, b->d_items, b->nitems, b->d_next, b->d_iter, b->grid, b->tile,
+                              b->mala_smem, s));
+    } else {
+        k_mutate_batch<<<b->grid, b->tile, 0, s>>>(b->d_mem, b->d_items, b->nitems, b->d_next, b->d_iter);
+        count_launch();
+    }
     k_iter_inc<<<1, 32, 0, s>>>(b->d_iter);
     count_launch();
     BCU(cudaGetLastError());
@@ -254,6 +297,9 @@ static smc_status copy_state(smc_batch* b, int to_alternate)
         if (c->ns)
             BCU(cudaMemcpyAsync(c->state[to], c->state[from], Ps * c->ns * sizeof(double),
                                 cudaMemcpyDeviceToDevice, b->stream));
+        if (b->mala)
+            BCU(cudaMemcpyAsync(c->grad[to], c->grad[from], Ps * c->d * sizeof(double), cudaMemcpyDeviceToDevice,
+                                b->stream));
         if (to_alternate) {
             BCU(cudaMemcpyAsync(c->ctl_host, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->stream));
         } else {
@@ -277,13 +323,17 @@ smc_status smc_batch_init(int n, const smc_model* models, const smc_config* cfgs
     if (n < 1 || !models || !cfgs || !ys || !Ts || !theta0s) return bset(b, SMC_EINVAL, "bad batch arguments");
     b->n = n;
     b->stream = (cudaStream_t)stream;
+    b->mala = cfgs[0].mutation == SMC_MALA;
     for (int i = 0; i < n; ++i) {
         const smc_config& c = cfgs[i];
         if (models[i].model != SMC_EGARCH || c.precision != SMC_FP32 || c.tempering != SMC_POWER ||
-            c.mutation != SMC_RW || c.stop_rule != SMC_STOP_DET)
+            (c.mutation != SMC_RW && c.mutation != SMC_MALA) || c.stop_rule != SMC_STOP_DET)
             return bset(b, SMC_EINVAL,
-                        "batched runs take FP32 EGARCH models with power tempering, random-walk "
+                        "batched runs take FP32 EGARCH models with power tempering, random-walk or MALA "
                         "mutation and the deterministic stopping rule");
+        if ((c.mutation == SMC_MALA) != (b->mala != 0))
+            return bset(b, SMC_EINVAL, "the runs of one batch share one mutation kind");
+        b->Kmax = std::max(b->Kmax, models[i].K);
         smc_ctx* ctx = nullptr;
         const smc_status st = smc_init(&models[i], &c, ys[i], nullptr, Ts[i], theta0s[i], 0, stream, &ctx);
         b->m.push_back(ctx);
@@ -293,6 +343,11 @@ smc_status smc_batch_init(int n, const smc_model* models, const smc_config* cfgs
     }
     b->h_mem.resize(n);
     b->h_jobs.resize(n);
+    if (b->mala) {
+        b->h_mala.resize(n);
+        BCU(cudaMalloc(&b->d_mala, n * sizeof(BatchMalaDev)));
+        b->tile = kBatchMalaMaxThreads;
+    }
     BCU(cudaMalloc(&b->d_mem, n * sizeof(BatchMemberDev)));
     BCU(cudaMalloc(&b->d_jobs, n * sizeof(CovJob)));
     BCU(cudaMalloc(&b->d_next, sizeof(unsigned int)));
@@ -319,13 +374,15 @@ smc_status smc_batch_autotune(smc_batch* b, int iters, double* ms_out)
     fill_descriptors(b, R);
     st = upload_descriptors(b);
     if (st != SMC_OK) return st;
-    const int cand[3] = {64, 128, 256};
+    const int cand_rw[3] = {64, 128, 256}, cand_mala[3] = {32, 64, 64};
+    const int* cand = b->mala ? cand_mala : cand_rw;
     double best = 1e30;
     int best_tile = b->tile;
     cudaEvent_t e0, e1;
     BCU(cudaEventCreate(&e0));
     BCU(cudaEventCreate(&e1));
-    for (int t : cand) {
+    for (int ci = 0; ci < 3; ++ci) {
+        const int t = cand[ci];
         b->tile = t;
         st = build_items(b);
         if (st != SMC_OK) return st;
@@ -464,7 +521,7 @@ void smc_batch_free(smc_batch* b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (smc_ctx* c : b->m) smc_free(c);
-    void* ptrs[] = {b->d_mem, b->d_jobs, b->d_items, b->d_next, b->d_iter};
+    void* ptrs[] = {b->d_mem, b->d_mala, b->d_jobs, b->d_items, b->d_next, b->d_iter};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete b;

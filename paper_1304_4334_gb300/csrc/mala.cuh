@@ -156,6 +156,83 @@ __global__ void __launch_bounds__(kMalaThreads) k_loglik_grad(GradArgs a)
         for (int k = 0; k < GP::kNs; ++k) a.state[k * P + p] = st[k];
 }
 
+// One particle's MALA iteration (the body of k_mutate_mala and of the batched
+// persistent kernel): proposal with the drift (1/2) L L' g, log likelihood and
+// gradient of the proposal, the Metropolis-Hastings ratio with the reverse
+// proposal density, and on acceptance the write-back of theta, gradient, log
+// likelihood, log prior and state.  Ls: L in the working precision (shared
+// memory); buf/stride: this thread's segment slab.  Returns the decision.
+template <class GP>
+__device__ __forceinline__ bool mala_particle(const MalaArgs& a, uint64_t iter, int p,
+                                              const typename GP::RealT* Ls, typename GP::RealT* buf, int stride)
+{
+    using Real = typename GP::RealT;
+    const int d = a.m.d;
+    const size_t P = (size_t)a.P;
+    double th[kMaxD], g[kMaxD], prop[kMaxD];
+    Real z[kMaxD], w[kMaxD];
+    for (int i = 0; i < d; ++i) th[i] = a.theta[i * P + p];
+    // gradient of the tempered log target at theta
+    log_prior_grad(a.m, th, g);
+    for (int i = 0; i < d; ++i) g[i] += a.phi * a.grad[i * P + p];
+    // drift (1/2) L (L' g) and proposal
+    for (int k = 0; k < d; ++k) {
+        Real s = 0;
+        for (int i = k; i < d; ++i) s += Ls[i * d + k] * (Real)g[i];
+        w[k] = s;
+    }
+    proposal_normals<Real>(a.seed, (uint64_t)p, iter, a.cycle, d, z);
+    Real zz = 0;
+    for (int i = 0; i < d; ++i) {
+        Real s1 = 0, s2 = 0;
+        for (int k = 0; k <= i; ++k) {
+            s1 += Ls[i * d + k] * w[k];
+            s2 += Ls[i * d + k] * z[k];
+        }
+        prop[i] = th[i] + (double)(Real(0.5) * s1 + s2);
+        zz += z[i] * z[i];
+    }
+    const double lp_new = log_prior(a.m, prop);
+    double gl[kMaxD], st[kMaxState];
+    const double ll_new = GP::eval(a.m, prop, a.obs, a.T, a.W, a.ckpt, P, p, buf, stride, gl, st);
+    double log_alpha = -INFINITY;
+    if (lp_new > -INFINITY && ll_new > -INFINITY) {
+        double g2[kMaxD];
+        log_prior_grad(a.m, prop, g2);
+        for (int i = 0; i < d; ++i) g2[i] += a.phi * gl[i];
+        for (int k = 0; k < d; ++k) {
+            Real s = 0;
+            for (int i = k; i < d; ++i) s += Ls[i * d + k] * (Real)g2[i];
+            w[k] = s;
+        }
+        // u = L^-1 (theta - theta* - (1/2) L L' g*), zero pivots contribute nothing
+        double uu = 0.0;
+        Real u[kMaxD];
+        for (int i = 0; i < d; ++i) {
+            Real s1 = 0;
+            for (int k = 0; k <= i; ++k) s1 += Ls[i * d + k] * w[k];
+            Real r = (Real)(th[i] - prop[i]) - Real(0.5) * s1;
+            for (int k = 0; k < i; ++k) r -= Ls[i * d + k] * u[k];
+            u[i] = Ls[i * d + i] > Real(0) ? r / Ls[i * d + i] : Real(0);
+            uu += (double)u[i] * (double)u[i];
+        }
+        log_alpha = tempered_target(lp_new, ll_new, a.phi) - tempered_target(a.lp[p], a.ll[p], a.phi) -
+                    0.5 * uu + 0.5 * (double)zz;
+    }
+    const bool acc = mh_accept(a.seed, (uint64_t)p, iter, a.cycle, log_alpha);
+    if (acc) {
+        for (int i = 0; i < d; ++i) {
+            a.theta[i * P + p] = prop[i];
+            a.grad[i * P + p] = gl[i];
+        }
+        a.ll[p] = ll_new;
+        a.lp[p] = lp_new;
+        if (a.state)
+            for (int k = 0; k < GP::kNs; ++k) a.state[k * P + p] = st[k];
+    }
+    return acc;
+}
+
 template <class GP>
 __global__ void __launch_bounds__(kMalaThreads) k_mutate_mala(MalaArgs a)
 {
@@ -168,73 +245,9 @@ __global__ void __launch_bounds__(kMalaThreads) k_mutate_mala(MalaArgs a)
     if (threadIdx.x == 0) acc_s = 0;
     __syncthreads();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = p < a.P;
-    const size_t P = (size_t)a.P;
     bool acc = false;
-    if (active) {
-        Real* buf = reinterpret_cast<Real*>(sm_raw) + threadIdx.x;
-        double th[kMaxD], g[kMaxD], prop[kMaxD];
-        Real z[kMaxD], w[kMaxD];
-        for (int i = 0; i < d; ++i) th[i] = a.theta[i * P + p];
-        // gradient of the tempered log target at theta
-        log_prior_grad(a.m, th, g);
-        for (int i = 0; i < d; ++i) g[i] += a.phi * a.grad[i * P + p];
-        // drift (1/2) L (L' g) and proposal
-        for (int k = 0; k < d; ++k) {
-            Real s = 0;
-            for (int i = k; i < d; ++i) s += Ls[i * d + k] * (Real)g[i];
-            w[k] = s;
-        }
-        proposal_normals<Real>(a.seed, (uint64_t)p, a.iter, a.cycle, d, z);
-        Real zz = 0;
-        for (int i = 0; i < d; ++i) {
-            Real s1 = 0, s2 = 0;
-            for (int k = 0; k <= i; ++k) {
-                s1 += Ls[i * d + k] * w[k];
-                s2 += Ls[i * d + k] * z[k];
-            }
-            prop[i] = th[i] + (double)(Real(0.5) * s1 + s2);
-            zz += z[i] * z[i];
-        }
-        const double lp_new = log_prior(a.m, prop);
-        double gl[kMaxD], st[kMaxState];
-        const double ll_new = GP::eval(a.m, prop, a.obs, a.T, a.W, a.ckpt, P, p, buf, blockDim.x, gl, st);
-        double log_alpha = -INFINITY;
-        if (lp_new > -INFINITY && ll_new > -INFINITY) {
-            double g2[kMaxD];
-            log_prior_grad(a.m, prop, g2);
-            for (int i = 0; i < d; ++i) g2[i] += a.phi * gl[i];
-            for (int k = 0; k < d; ++k) {
-                Real s = 0;
-                for (int i = k; i < d; ++i) s += Ls[i * d + k] * (Real)g2[i];
-                w[k] = s;
-            }
-            // u = L^-1 (theta - theta* - (1/2) L L' g*), zero pivots contribute nothing
-            double uu = 0.0;
-            Real u[kMaxD];
-            for (int i = 0; i < d; ++i) {
-                Real s1 = 0;
-                for (int k = 0; k <= i; ++k) s1 += Ls[i * d + k] * w[k];
-                Real r = (Real)(th[i] - prop[i]) - Real(0.5) * s1;
-                for (int k = 0; k < i; ++k) r -= Ls[i * d + k] * u[k];
-                u[i] = Ls[i * d + i] > Real(0) ? r / Ls[i * d + i] : Real(0);
-                uu += (double)u[i] * (double)u[i];
-            }
-            log_alpha = tempered_target(lp_new, ll_new, a.phi) - tempered_target(a.lp[p], a.ll[p], a.phi) -
-                        0.5 * uu + 0.5 * (double)zz;
-        }
-        acc = mh_accept(a.seed, (uint64_t)p, a.iter, a.cycle, log_alpha);
-        if (acc) {
-            for (int i = 0; i < d; ++i) {
-                a.theta[i * P + p] = prop[i];
-                a.grad[i * P + p] = gl[i];
-            }
-            a.ll[p] = ll_new;
-            a.lp[p] = lp_new;
-            if (a.state)
-                for (int k = 0; k < GP::kNs; ++k) a.state[k * P + p] = st[k];
-        }
-    }
+    if (p < a.P) acc = mala_particle<GP>(a, a.iter, p, Ls, reinterpret_cast<Real*>(sm_raw) + threadIdx.x,
+                                         blockDim.x);
     const unsigned int nacc = __popc(__ballot_sync(0xffffffffu, acc));
     if ((threadIdx.x & 31) == 0 && nacc) atomicAdd(&acc_s, nacc);
     __syncthreads();
