@@ -348,13 +348,15 @@ const char* smc_status_str(smc_status s);
 
 /* ---------------------------------------------------------------------------
  * Batched runs: n independent simulator runs (datasets of different length T,
- * EGARCH models of different K and I; FP32, power tempering, random walk,
- * deterministic stopping rule) advanced together cycle by cycle.  Each run is
- * Algorithm 2 as in smc_cycle and keeps its own particles, seed and adaptation;
- * the batch shares the M-phase launches: one persistent kernel per Metropolis
- * iteration processes every run's particles from a work queue ordered by
- * decreasing cost (T x per-observation work), and one iteration (batched
- * covariance + persistent mutation) is a captured CUDA graph.
+ * EGARCH models of different K and I; FP32, power tempering, deterministic
+ * stopping rule; all random walk or all MALA) advanced together cycle by
+ * cycle.  Each run is Algorithm 2 as in smc_cycle and keeps its own particles,
+ * seed and adaptation; the batch shares the M-phase launches: one persistent
+ * kernel per Metropolis iteration processes every run's particles from a work
+ * queue ordered by decreasing cost (T x per-observation work), and one
+ * iteration (batched covariance + persistent mutation) is a captured CUDA
+ * graph.  Results equal those of the same runs done one at a time, bit for
+ * bit.  SMC_EINVAL for other settings or for a batch mixing mutation kinds.
  * ------------------------------------------------------------------------- */
 typedef struct smc_batch smc_batch;
 
@@ -362,9 +364,10 @@ typedef struct smc_batch smc_batch;
  * draws [P_i][d_i].  On error *out is still set (free it with smc_batch_free). */
 smc_status smc_batch_init(int n, const smc_model* models, const smc_config* cfgs, const double* const* ys,
                           const int* Ts, const double* const* theta0s, void* stream, smc_batch** out);
-/* Times `iters` M iterations for each candidate tile (64, 128, 256 particles
- * per work item) on a snapshot of the particles (restored afterwards) and
- * keeps the fastest; ms_per_iteration (host, nullable) gets its time. */
+/* Times `iters` M iterations for each candidate tile (random walk: 64, 128,
+ * 256 particles per work item; MALA: 32, 64) on a snapshot of the particles
+ * (restored afterwards) and keeps the fastest; ms_per_iteration (host,
+ * nullable) gets its time. */
 smc_status smc_batch_autotune(smc_batch* b, int iters, double* ms_per_iteration);
 /* One cycle of every unfinished run; SMC_EDONE when all are done. */
 smc_status smc_batch_cycle(smc_batch* b, int* n_active);
