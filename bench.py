@@ -421,6 +421,102 @@ def precision_report(S, I, P=2048, seeds=2):
                          "max_mean_diff_in_nse": float(dm.max()), "seconds_fp64": t64, "seconds_fp32": t32})
         rec["runs_same_seed_J64_N256"] = runs
         out["shapes"][name] = rec
+    out["log_ml_over_seeds"] = log_ml_bias_over_seeds(S, I)
+    return out
+
+
+def log_ml_bias_over_seeds(S, I, n=10):
+    """FP32 - FP64 log ML over n prior-draw seeds (K=2, I=2, T=5000,
+    J=64 x N=256): FP64 runs, FP32 runs with independent random numbers and
+    FP32 runs with the FP64 runs' seeds; mean difference with its standard
+    error from the seeds, and each form's seed-to-seed s.d. beside its mean
+    NSE."""
+    import numpy as np
+    w = I.WORKLOADS["egarch22_T5000"]
+    y = w.data()
+    m = S.model_egarch(2, 2, True)
+    mean, sd, lo = S.model_prior(m)
+    J, N = 64, 256
+    res = {"f64": [], "f32": [], "f32_same": []}
+    for k in range(n):
+        th0 = I.draw_prior(mean, sd, lo, J * N, seed=900 + k)
+        for prec, key, seed in ((S.FP64, "f64", 11 + k), (S.FP32, "f32", 5011 + k), (S.FP32, "f32_same", 11 + k)):
+            ctx = S.init(m, S.config_default(J=J, N=N, precision=prec, seed=seed), y, th0)
+            ctx.run()
+            res[key].append(ctx.log_ml()[:2])
+            ctx.close()
+    out = {"seeds": n}
+    for key, v in res.items():
+        a = np.array(v)
+        out[key] = {"mean_log_ml": float(a[:, 0].mean()), "sd_over_seeds": float(a[:, 0].std(ddof=1)),
+                    "mean_nse": float(a[:, 1].mean())}
+    for key in ("f32", "f32_same"):
+        dlt = np.array(res[key])[:, 0] - np.array(res["f64"])[:, 0]
+        out[f"{key}_minus_f64"] = {"mean": float(dlt.mean()), "se": float(dlt.std(ddof=1) / np.sqrt(n))}
+    return out
+
+
+def batched_equal_nse(S, I, stream, n=8):
+    """The FP32 + adjoint + batched form against the plain FP64 random walk,
+    at equal log-ML NSE (the precision / time measure of Section 5.2): the
+    first n datasets of the 32-dataset batch (T ~ U{500..10000}, K ~ U{1,2,3},
+    I ~ U{1..4}, J = 16 x N = 1024 each) run (a) as one batch with FP32 MALA,
+    (b) as one batch with the FP32 random walk and (c) one at a time with the
+    FP64 random walk, from the same prior draws.  A batch's time to reach, for
+    every dataset, the NSE of the FP64 run is its run time x the largest ratio
+    NSE_batch^2 / NSE_fp64^2 over the datasets (NSE^2 falls as 1 / particles);
+    'mean' uses the mean ratio instead.  Reported relative to the summed FP64
+    run times."""
+    import numpy as np
+    import torch
+    ws = I.batched_workloads(n=32, seed=40, J=16, N=1024)[:n]
+    models, ys, ths = [], [], []
+    for w in ws:
+        m = S.model_egarch(w.K, w.I, True)
+        mean, sd, lo = S.model_prior(m)
+        models.append(m)
+        ys.append(w.data())
+        ths.append(I.draw_prior(mean, sd, lo, w.P, seed=w.prior_seed))
+    th_dev = [torch.as_tensor(np.ascontiguousarray(t.T), device="cuda") for t in ths]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, r
+
+    out = {"datasets": n, "T": [w.T for w in ws], "KI": [[w.K, w.I] for w in ws]}
+    for name, mut, target in (("fp32_mala_batched", S.MALA, 0.5), ("fp32_rw_batched", S.RW, 0.25)):
+        cfgs = [S.config_default(J=w.J, N=w.N, precision=S.FP32, seed=300 + k, mutation=mut, acc_target=target)
+                for k, w in enumerate(ws)]
+        b = S.Batch(models, cfgs, ys, ths, stream=stream.cuda_stream)
+        b.autotune(iters=1)
+        b.reset(th_dev, 300)
+        b.run()                                   # warm-up run
+        t, _ = timed(lambda: (b.reset(th_dev, 300), b.run()))
+        nse = [b.member(i).log_ml()[1] for i in range(n)]
+        lml = [b.member(i).log_ml()[0] for i in range(n)]
+        b.close()
+        out[name] = {"seconds": t, "nse": nse, "log_ml": lml}
+    t64, n64, l64 = [], [], []
+    for k, w in enumerate(ws):
+        cfg = S.config_default(J=w.J, N=w.N, precision=S.FP64, seed=300 + k)
+        ctx = S.init(models[k], cfg, ys[k], ths[k], stream=stream.cuda_stream)
+        t, _ = timed(lambda: ctx.run())
+        lm, nse, _ = ctx.log_ml()
+        ctx.close()
+        t64.append(t)
+        n64.append(nse)
+        l64.append(lm)
+    ref = sum(t64)
+    out["fp64_rw_one_at_a_time"] = {"seconds": ref, "nse": n64, "log_ml": l64}
+    for name in ("fp32_mala_batched", "fp32_rw_batched"):
+        r = np.square(out[name]["nse"]) / np.square(n64)
+        out[name]["wall_time_at_fp64_nse_rel_worst"] = out[name]["seconds"] * float(r.max()) / ref
+        out[name]["wall_time_at_fp64_nse_rel_mean"] = out[name]["seconds"] * float(r.mean()) / ref
     return out
 
 
@@ -602,6 +698,7 @@ def main():
     eq = None
     if rank == 0 and not args.no_equal_nse and args.cycles == 0 and w.name in ("egarch22_T5000", "egarch34_T20000"):
         eq = equal_nse_comparison(S, w, y, th0, stream, args.equal_nse_seeds)
+        eq["batched"] = batched_equal_nse(S, I, stream)
 
     if rank == 0:
         line = {"metric": "M-phase particle*obs lik evals/s", "value": value,
