@@ -64,7 +64,7 @@ def test_fp32_run_agrees_with_oracle_run(S, shape):
 def test_fp32_loglik_at_the_largest_shape(S):
     """FP32 log likelihood of the K = 3, I = 4 model over all T = 20000
     observations against the FP64 oracle, for posterior-like particles:
-    1e-4 relative (the FP32 tolerance)."""
+    1e-6 relative (7e-8 measured; the FP32 tolerance is 1e-4)."""
     torch = torch_cuda()
     w = I.WORKLOADS["egarch34_T20000"]
     y = w.data()
@@ -79,7 +79,7 @@ def test_fp32_loglik_at_the_largest_shape(S):
     ll = ll.cpu().numpy()
     rel = np.abs(ll - ll_o) / np.abs(ll_o)
     print(f"K=3, I=4, T=20000 FP32 log likelihood: max rel {rel.max():.2e}, median {np.median(rel):.2e}")
-    np.testing.assert_allclose(ll, ll_o, rtol=1e-4)
+    np.testing.assert_allclose(ll, ll_o, rtol=1e-6)
     # the mutation kernel's recursion (alpha v as one FMA): a step with a zero
     # proposal factor from a current log likelihood of -inf accepts theta itself
     # and stores its log likelihood
@@ -94,4 +94,4 @@ def test_fp32_loglik_at_the_largest_shape(S):
     llm = llm.cpu().numpy()
     relm = np.abs(llm - ll_o) / np.abs(ll_o)
     print(f"  mutation kernel: max rel {relm.max():.2e}, median {np.median(relm):.2e}")
-    np.testing.assert_allclose(llm, ll_o, rtol=1e-4)
+    np.testing.assert_allclose(llm, ll_o, rtol=1e-6)

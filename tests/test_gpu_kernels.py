@@ -1,7 +1,8 @@
 """GPU parity of each kernel of the path against the FP64 oracle, through the
 C ABI, on seeded inputs spanning several blocks/chunks with ragged tails.
 
-Tolerances: log likelihood 1e-9 relative in FP64 and 1e-4 relative in FP32;
+Tolerances: log likelihood 1e-9 relative in FP64 and 1e-6 relative in FP32
+(posterior-like particles; the FP32 contract is 1e-4);
 resampling indices bit-exact given identical weights; estimators 1e-12."""
 import math
 
@@ -58,8 +59,10 @@ def test_loglik_fp64_matches_oracle(S, K, I_, gamma, T, P):
 @pytest.mark.parametrize("K,I_,gamma", SHAPES)
 @pytest.mark.parametrize("T,P", [(1, 5), (37, 129), (3089, 300)])
 def test_loglik_fp32_matches_oracle(S, K, I_, gamma, T, P):
+    """FP32 recursion with FP64 accumulation, posterior-like particles: 1e-6
+    relative (1e-7 measured; the stated FP32 tolerance is 1e-4)."""
     ll_o, st_o, lp_o, ll, st, lp = _loglik_case(S, K, I_, gamma, T, P, S.FP32, seed=5 + T)
-    np.testing.assert_allclose(ll, ll_o, rtol=1e-4, atol=1e-4)
+    np.testing.assert_allclose(ll, ll_o, rtol=1e-6, atol=1e-6)
     # end state: eps_T and v_kT carry the FP32 recursion's rounding
     np.testing.assert_allclose(st, st_o, rtol=2e-3, atol=2e-3)
     np.testing.assert_allclose(lp, lp_o, rtol=1e-13, atol=1e-13)

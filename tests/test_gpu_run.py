@@ -216,7 +216,7 @@ def test_full_size_run_sampled_parity(S):
     spec = O.ModelSpec(K=w.K, I=w.I, gamma=w.gamma)
     pick = np.random.default_rng(0).choice(w.P, 48, replace=False)
     ll_o, st_o = O.loglik(spec, y, th[pick], with_state=True, nthreads=8)
-    np.testing.assert_allclose(ll[pick], ll_o, rtol=1e-4)
+    np.testing.assert_allclose(ll[pick], ll_o, rtol=1e-6)
     # the FP32 path evaluates the log prior in FP32 (FP32 mode reading)
     np.testing.assert_allclose(lp[pick], O.logprior(spec, th[pick]), rtol=1e-5)
     np.testing.assert_allclose(st[pick], st_o, rtol=2e-3, atol=2e-3)
