@@ -42,12 +42,12 @@ if ROOT not in sys.path:
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT_GB300 = 152
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the current
-# mutation kernel, by (workload, particles per thread, threads per block).
-# Empty: both kernels changed after their last captures (the paired one's
-# launch bound, the single one's entry wait of a dependent launch), whose
-# figures, 8.72 MB (2 x 64) and 9.06 MB (1 x 224) per launch, are in
-# profiles/; traffic is reported as null until they are captured again.
-MUTATE_TRAFFIC = {}
+# mutation kernel, by (workload, particles per thread, threads per block): the
+# mean of two launches of the second cycle's M phase at the full size, captured
+# with --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass;
+# profiles/k_mutate_x2_egarch34_T20000.md).  Shapes without a capture of the
+# current kernel report null.
+MUTATE_TRAFFIC = {("egarch34_T20000", 2, 128): 1.153083008e9}
 SM_MAX_MHZ_FALLBACK = 2070.0
 L2_FLUSH_BYTES = 256 << 20
 
@@ -674,7 +674,10 @@ def main():
     achieved = w.P * w.T / avg_launch_s if mut_n else float("nan")
     fp32_ops, mufu_ops = (mala_ops_per_eval if mala else alu_ops_per_eval)(w.K, w.I, w.gamma)
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
-            "frac": achieved / peak, "traffic": traffic, "pipe": pipe,
+            "frac": achieved / peak, "traffic": traffic,
+            "traffic_unit": "DRAM bytes read + written per launch (ncu); the kernel is ALU-bound: "
+                            "traffic / launch time is under 1% of the HBM bandwidth",
+            "pipe": pipe,
             "peak_source": (f"pipe rates measured by smc_peaks on this device x {src} SM clock "
                             f"{mhz:.0f} MHz x {SM_COUNT_GB300} SMs"),
             "measured_rates": rates, "peak_nominal": peak_nom / 1e9, "pipe_nominal": pipe_nom,
