@@ -304,7 +304,7 @@ def run_reference(args, world, rank):
 
 
 # ----------------------------------------------------- wall time at equal NSE
-def equal_nse_comparison(S, w, y, th0, stream, seeds):
+def equal_nse_comparison(S, w, y, th0, stream, seeds, shape=None, fp64_seeds=None):
     """The paper's efficiency measure, precision / time = 1 / (NSE^2 t)
     (Section 5.2, Table 3), for the log marginal likelihood: whole runs of
     several forms on the same GPU, same data and prior draws.  At T = 5000 the
@@ -312,7 +312,9 @@ def equal_nse_comparison(S, w, y, th0, stream, seeds):
     and FP32 MALA forms; at 1M particles x T = 20000 (where an FP64 run would
     take hours) the FP32 random walk is the reference for FP32 MALA.  Reported
     per form: mean run time, mean NSE^2, and the wall time it needs to reach
-    the reference form's NSE (t * NSE^2 / NSE_ref^2), relative to that form."""
+    the reference form's NSE (t * NSE^2 / NSE_ref^2), relative to that form.
+    shape: the random-walk runs' mutation launch shape (the benchmark's
+    autotuned one); fp64_seeds: fewer seeds for the slow FP64 form."""
     import torch
     m = S.model_egarch(w.K, w.I, w.gamma)
     forms = [("fp64_rw", S.FP64, S.RW, 0.25), ("fp32_rw", S.FP32, S.RW, 0.25),
@@ -322,10 +324,13 @@ def equal_nse_comparison(S, w, y, th0, stream, seeds):
     out = {}
     for name, prec, mut, target in forms:
         ts, nse2, lml = [], [], []
-        for k in range(seeds):
+        nseeds = fp64_seeds if (prec == S.FP64 and fp64_seeds) else seeds
+        for k in range(nseeds):
             cfg = S.config_default(J=w.J, N=w.N, precision=prec, mutation=mut, acc_target=target,
                                    rbar=w.rbar, kappa=w.kappa, seed=500 + k)
             ctx = S.init(m, cfg, y, th0, stream=stream.cuda_stream)
+            if shape and mut == S.RW and prec == S.FP32:
+                ctx.set_launch_shape(shape[0], shape[1])
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -339,7 +344,7 @@ def equal_nse_comparison(S, w, y, th0, stream, seeds):
             nse2.append(nse * nse)
             lml.append(lm)
         out[name] = {"seconds": statistics.mean(ts), "nse2": statistics.mean(nse2),
-                     "log_ml": statistics.mean(lml), "runs": seeds}
+                     "log_ml": statistics.mean(lml), "runs": nseeds}
     ref = out[forms[0][0]]
     for v in out.values():
         v["wall_time_at_ref_nse_rel"] = (v["seconds"] * v["nse2"] / ref["nse2"]) / ref["seconds"]
@@ -700,8 +705,16 @@ def main():
         cpu = cpu_baseline_leg(w, y)
     eq = None
     if rank == 0 and not args.no_equal_nse and args.cycles == 0 and w.name in ("egarch22_T5000", "egarch34_T20000"):
-        eq = equal_nse_comparison(S, w, y, th0, stream, args.equal_nse_seeds)
+        eq = equal_nse_comparison(S, w, y, th0, stream, args.equal_nse_seeds, shape=shape)
         eq["batched"] = batched_equal_nse(S, I, stream)
+        # MALA at the K=2, I=2, T=5000 shape with J = 64 x N = 4096 particles,
+        # against the FP32 and the (one-seed) FP64 random walk
+        w3 = I.WORKLOADS["egarch22_T5000_mala"]
+        y3 = w3.data()
+        m3 = S.model_egarch(w3.K, w3.I, w3.gamma)
+        th3 = I.draw_prior(*S.model_prior(m3), w3.P, seed=w3.prior_seed)
+        eq["egarch22_T5000_J64xN4096"] = equal_nse_comparison(S, w3, y3, th3, stream, args.equal_nse_seeds,
+                                                              fp64_seeds=1)
 
     if rank == 0:
         line = {"metric": "M-phase particle*obs lik evals/s", "value": value,
