@@ -412,7 +412,11 @@ __device__ void adj_reverse(EgarchNat<Real, K, I> m, const Real* __restrict__ y,
         // checkpoint; only the first observation of the series (t = 0) has no
         // previous shock
         const Real* q = buf + (size_t)(n - 1) * W * stride;
-#pragma unroll 1
+        // unrolled by two: a step's mixture terms (independent of the adjoint
+        // carry vb) overlap the previous step's carry update (measured on
+        // K=2, I=2, T=5000, 262,144 particles: 5.90 ms per MALA launch against
+        // 6.39 ms unrolled once, 5.96 ms by four)
+#pragma unroll 2
         for (int r = n - 1; r >= 1; --r, q -= W * stride) {
             const Real* qp = q - W * stride;
             Real vp[K];
