@@ -49,6 +49,11 @@ SM_COUNT_GB300 = 152
 # current kernel report null.
 MUTATE_TRAFFIC = {("egarch34_T20000", 2, 128): 1.153083008e9}
 SM_MAX_MHZ_FALLBACK = 2070.0
+# Acceptance target of the MALA runs: 0.574, the asymptotically optimal rate of
+# Langevin proposals (Roberts and Rosenthal, 1998); the random walk keeps the
+# paper's 0.25.  Measured on K=2, I=2, T=5000, 262,144 particles (3 seeds):
+# run time x NSE^2 0.000475 against 0.000620 with a target of 0.5.
+MALA_TARGET = 0.574
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -318,7 +323,7 @@ def equal_nse_comparison(S, w, y, th0, stream, seeds, shape=None, fp64_seeds=Non
     import torch
     m = S.model_egarch(w.K, w.I, w.gamma)
     forms = [("fp64_rw", S.FP64, S.RW, 0.25), ("fp32_rw", S.FP32, S.RW, 0.25),
-             ("fp32_mala", S.FP32, S.MALA, 0.5)]
+             ("fp32_mala", S.FP32, S.MALA, MALA_TARGET)]
     if w.T > 10000:
         forms = forms[1:]
     out = {}
@@ -494,7 +499,7 @@ def batched_equal_nse(S, I, stream, n=8):
         return e0.elapsed_time(e1) / 1e3, r
 
     out = {"datasets": n, "T": [w.T for w in ws], "KI": [[w.K, w.I] for w in ws]}
-    for name, mut, target in (("fp32_mala_batched", S.MALA, 0.5), ("fp32_rw_batched", S.RW, 0.25)):
+    for name, mut, target in (("fp32_mala_batched", S.MALA, MALA_TARGET), ("fp32_rw_batched", S.RW, 0.25)):
         cfgs = [S.config_default(J=w.J, N=w.N, precision=S.FP32, seed=300 + k, mutation=mut, acc_target=target)
                 for k, w in enumerate(ws)]
         b = S.Batch(models, cfgs, ys, ths, stream=stream.cuda_stream)
@@ -569,7 +574,7 @@ def main():
     prec = S.FP32 if w.precision == "f32" else S.FP64
     mala = w.mutation == "mala"
     cfg = S.config_default(J=w.J, N=w.N, precision=prec, rbar=w.rbar, kappa=w.kappa, seed=1 + rank,
-                           mutation=S.MALA if mala else S.RW, acc_target=0.5 if mala else 0.25)
+                           mutation=S.MALA if mala else S.RW, acc_target=MALA_TARGET if mala else 0.25)
     stream = torch.cuda.Stream()
     th0_dev = torch.as_tensor(np.ascontiguousarray(th0.T), device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -756,7 +761,7 @@ def run_batched(args, world, rank, local, mala=False):
         mean, sd, lo = S.model_prior(m)
         models.append(m)
         cfgs.append(S.config_default(J=w.J, N=w.N, precision=S.FP32, seed=100 + k,
-                                     mutation=S.MALA if mala else S.RW, acc_target=0.5 if mala else 0.25))
+                                     mutation=S.MALA if mala else S.RW, acc_target=MALA_TARGET if mala else 0.25))
         ys.append(w.data())
         ths.append(I.draw_prior(mean, sd, lo, w.P, seed=w.prior_seed))
     stream = torch.cuda.Stream()
