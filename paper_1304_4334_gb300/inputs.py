@@ -141,13 +141,13 @@ def linreg_data(T: int, beta, sigma: float, seed: int):
 # Workloads.  Shapes follow Section 5 (J = 64 groups of N = 1024, T about 5000
 # daily returns at about 1% volatility) scaled as listed.
 # ---------------------------------------------------------------------------------
-def _cfg2_truth():
+def _truth_k2_i2():
     p, mu, sg = normalized_mixture((0.8, 0.2), (0.0, 0.0), (1.0, 2.5))
     return EgarchTruth(mu_y=0.0003, sigma_y=0.01, alpha=(0.98, 0.85), beta=(0.10, 0.15),
                        gamma=(-0.05, 0.0), p=p, mu=mu, sig=sg)
 
 
-def _cfg5_truth():
+def _truth_k3_heavy_tails():
     p, mu, sg = normalized_mixture((0.9, 0.1), (0.0, 0.0), (1.0, 4.0))
     return EgarchTruth(mu_y=0.0003, sigma_y=0.01, alpha=(0.98, 0.90, 0.60),
                        beta=(0.08, 0.10, 0.12), gamma=(-0.04, -0.02, 0.0), p=p, mu=mu, sig=sg)
@@ -187,11 +187,11 @@ WORKLOADS = {
                               EgarchTruth(0.0, math.exp(-0.1 / (2 * 0.02)), (0.98,), (0.1,), (0.0,)),
                               data_seed=11, prior_seed=12, rbar=10, kappa=1),
     "egarch22_T5000": Workload("egarch22_T5000", 2, 2, True, 5000, 64, 1024, "f32", "rw",
-                               _cfg2_truth(), data_seed=21, prior_seed=22),
+                               _truth_k2_i2(), data_seed=21, prior_seed=22),
     "egarch22_T5000_mala": Workload("egarch22_T5000_mala", 2, 2, True, 5000, 64, 4096, "f32",
-                                    "mala", _cfg2_truth(), data_seed=21, prior_seed=32),
+                                    "mala", _truth_k2_i2(), data_seed=21, prior_seed=32),
     "egarch34_T20000": Workload("egarch34_T20000", 3, 4, True, 20000, 128, 8192, "f32", "rw",
-                                _cfg5_truth(), data_seed=51, prior_seed=52),
+                                _truth_k3_heavy_tails(), data_seed=51, prior_seed=52),
 }
 
 
