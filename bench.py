@@ -191,6 +191,21 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ distributed
+def combine_ranks(seconds, evals, world, device="cpu"):
+    """Whole-job figures of N independent replicas: the slowest rank's timed
+    seconds and the evaluations of all ranks (the process group must be up
+    when world > 1; NCCL on the GPUs, gloo in the CPU test)."""
+    if world <= 1:
+        return seconds, evals
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([seconds], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ee = torch.tensor([evals], device=device, dtype=torch.float64)
+    dist.all_reduce(ee, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(ee.item())
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -633,15 +648,7 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_total = sum(step_ms) / 1e3
     mut_ms, mut_n = ctx.mutate_time(reset=True)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ee = torch.tensor([evals_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(ee, op=dist.ReduceOp.SUM)
-        t_total, evals_all = float(tt.item()), float(ee.item())
-    else:
-        evals_all = evals_total
+    t_total, evals_all = combine_ranks(t_total, evals_total, world, device="cuda")
     value = evals_all / t_total
 
     # ---- end to end through the public API from host buffers ----
