@@ -25,7 +25,6 @@ of cycle l.  A same-seed replay reproduces the adaptive run bit for bit
 adaptive run had at that point; the expected factor, step size and stopping
 decision are then computed from them by the oracle.
 """
-import math
 
 import numpy as np
 import pytest
