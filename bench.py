@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--launch-shape", default="", help="PPT,THREADS: fixed mutation launch shape instead of autotuning")
     ap.add_argument("--equal-nse-seeds", type=int, default=3)
     ap.add_argument("--particles", default="", help="J,N: override the workload's groups x particles (profiling only)")
+    ap.add_argument("--tempering", default="power", choices=["power", "data"],
+                    help="C phase: power tempering (default) or the paper's data tempering")
     return ap.parse_args()
 
 
@@ -589,7 +591,8 @@ def main():
     prec = S.FP32 if w.precision == "f32" else S.FP64
     mala = w.mutation == "mala"
     cfg = S.config_default(J=w.J, N=w.N, precision=prec, rbar=w.rbar, kappa=w.kappa, seed=1 + rank,
-                           mutation=S.MALA if mala else S.RW, acc_target=MALA_TARGET if mala else 0.25)
+                           mutation=S.MALA if mala else S.RW, acc_target=MALA_TARGET if mala else 0.25,
+                           tempering=S.POWER if args.tempering == "power" else S.DATA)
     stream = torch.cuda.Stream()
     th0_dev = torch.as_tensor(np.ascontiguousarray(th0.T), device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -618,7 +621,9 @@ def main():
     # events around the first mutation launch of every M phase only: an event
     # recorded between two kernels linked by programmatic dependent launch
     # serialises them, so timing every launch would slow the step it measures
-    ctx.profile(2)
+    # data tempering: every launch is timed (their lengths t_l differ), which
+    # gives up the programmatic dependent launches' overlap
+    ctx.profile(2 if args.tempering == "power" else 1)
     ctx.mutate_time(reset=True)
     clocks = ClockSampler(local)
     if world > 1:
@@ -688,7 +693,10 @@ def main():
     peak, pipe = alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, mhz, paired, mala, rates=rates)
     peak_nom, pipe_nom = alu_peak_evals(w.K, w.I, w.gamma, SM_COUNT_GB300, mhz, paired, mala)
     avg_launch_s = (mut_ms / mut_n) / 1e3 if mut_n else float("nan")
-    achieved = w.P * w.T / avg_launch_s if mut_n else float("nan")
+    if args.tempering == "power":
+        achieved = w.P * w.T / avg_launch_s if mut_n else float("nan")
+    else:   # every launch timed: all M-phase evaluations over their summed time
+        achieved = evals_total / (mut_ms / 1e3) if mut_n else float("nan")
     fp32_ops, mufu_ops = (mala_ops_per_eval if mala else alu_ops_per_eval)(w.K, w.I, w.gamma)
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
             "frac": achieved / peak, "traffic": traffic,
@@ -704,7 +712,8 @@ def main():
                        else f"k_mutate_x2<{w.K},{w.I}>" if paired
                        else f"k_mutate<PolicyEgarchF32<{w.K},{w.I}>>"), "avg_launch_ms": avg_launch_s * 1e3,
             "launches": int(sum(msteps)), "timed_launches": mut_n,
-            "timed": "first mutation launch of every M phase (CUDA events)",
+            "timed": ("first mutation launch of every M phase (CUDA events)" if args.tempering == "power"
+                      else "every mutation launch (CUDA events)"),
             "share_of_step": avg_launch_s * sum(msteps) / t_total if t_total and mut_n else None,
             "launch_shape": {"particles_per_thread": shape[0], "threads_per_block": shape[1],
                              "autotune_ms_per_iteration": shape[2]}}
@@ -716,7 +725,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline_leg(w, y)
     eq = None
-    if rank == 0 and not args.no_equal_nse and args.cycles == 0 and w.name in ("egarch22_T5000", "egarch34_T20000"):
+    if (rank == 0 and not args.no_equal_nse and args.cycles == 0 and args.tempering == "power"
+            and w.name in ("egarch22_T5000", "egarch34_T20000")):
         eq = equal_nse_comparison(S, w, y, th0, stream, args.equal_nse_seeds, shape=shape)
         eq["batched"] = batched_equal_nse(S, I, stream)
         # MALA at the K=2, I=2, T=5000 shape with J = 64 x N = 4096 particles,
@@ -736,7 +746,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": w.name, "K": w.K, "I": w.I, "T": w.T, "J": w.J, "N": w.N,
                            "precision": ("fp32 recursion, fp64 accumulators" if w.precision == "f32"
-                                         else "fp64 throughout"), "tempering": "power",
+                                         else "fp64 throughout"), "tempering": args.tempering,
                            "sampler": w.mutation, "stop_rule": f"deterministic Rbar={w.rbar} kappa={w.kappa}",
                            "cycles_per_run": cycles, "metropolis_steps_per_run": msteps,
                            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},

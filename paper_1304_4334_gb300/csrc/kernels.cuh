@@ -471,12 +471,12 @@ __global__ void __launch_bounds__(kMutThreads) k_loglik(LoglikArgs a)
 // s = t_l-1 + 1, ..., stopping at the first s with RSS(s) < D1 (Section 3.3),
 // at a date of interest, or at T.  The search runs speculatively over a chunk
 // of up to kCdataChunk observations: each block reduces, for every s of the
-// chunk, (max log w, sum w, sum w^2) over its particles; a one-warp kernel
-// combines the blocks and finds the stopping observation; a commit pass then
+// chunk, (max log w, sum w, sum w^2) over its particles; one block (a warp
+// per observation) combines the blocks and finds the stopping observation; a
+// commit pass then
 // advances every particle's recursion state, log likelihood and log weight to
 // it.  The RSS statistic uses FP32 exponentials of log-weight differences; the
 // log weights themselves are FP64.
-constexpr int kCdataChunk = 32;
 
 struct CdataArgs {
     ModelDev m;

@@ -1149,67 +1149,133 @@ cudaError_t launch_gather(const GatherArgs& a, cudaStream_t s)
     return e;
 }
 
-__global__ void k_cdata_select(const double* part, int G, int B, int s0, int T, int P, double d1,
-                               ForceDates fd, Ctl* ctl)
+// Double-float accumulation on the FP32 pipe (Knuth's TwoSum): x + b and x + y.
+__device__ __forceinline__ Df df_add_f(Df x, float b)
 {
-    const int q = threadIdx.x;
-    double rss = NAN;
-    bool stop = false, forced = false;
-    if (q < B) {
-        double M = -INFINITY;
-        for (int g = 0; g < G; ++g) M = fmax(M, part[((size_t)g * B + q) * 3]);
-        double S1 = 0.0, S2 = 0.0;
-        for (int g = 0; g < G; ++g) {
-            const double* o = part + ((size_t)g * B + q) * 3;
-            if (o[0] == -INFINITY) continue;
-            const double e = exp(o[0] - M);
-            S1 += o[1] * e;
-            S2 += o[2] * e * e;
-        }
-        rss = S1 * S1 / ((double)P * S2);
-        const int sobs = s0 + q + 1;
-        bool date = sobs == T;
-        for (int i = 0; i < fd.n; ++i) date = date || fd.t[i] == sobs;
-        const bool low = !(rss >= d1);   // RSS < D1 (a degenerate NaN also stops)
-        stop = low || date;
-        forced = date && !low;
+    const float s = x.hi + b;
+    const float bv = s - x.hi;
+    const float e = (x.hi - (s - bv)) + (b - bv);
+    return df_quick(s, e + x.lo);
+}
+
+__device__ __forceinline__ Df df_add(Df x, Df y)
+{
+    const float s = x.hi + y.hi;
+    const float bv = s - x.hi;
+    const float e = (x.hi - (s - bv)) + (y.hi - bv);
+    return df_quick(s, e + (x.lo + y.lo));
+}
+
+__device__ __forceinline__ Df warp_sum_df(Df x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const Df y = {__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+        x = df_add(x, y);
     }
-    const unsigned m = __ballot_sync(0xffffffffu, stop);
-    const int at = m ? __ffs(m) - 1 : (B - 1);
-    const double rss_at = __shfl_sync(0xffffffffu, rss, at);
-    const int forced_at = __shfl_sync(0xffffffffu, forced ? 1 : 0, at);
-    if (q == 0) {
-        ctl->cd_stop = m ? at + 1 : B;
-        ctl->cd_found = m ? 1 : 0;
-        ctl->cd_forced = m ? forced_at : 0;
-        ctl->rss = rss_at;
+    return x;
+}
+
+// Data-tempering stop search of one chunk (Section 3.3, "C phase
+// termination"): warp q combines the G blocks' (max log w, sum w, sum w^2) of
+// observation s0 + q + 1 into the pooled RSS, and the first observation with
+// RSS < D1 (or a date of interest, or T) ends the chunk.  The block maxima are
+// compared as order-preserving integer keys; the rescaling weights
+// exp(M_g - M) are FP32 exponentials of the FP64 differences (the blocks' sums
+// are themselves sums of FP32 weights, ~1e-7), accumulated as double-float
+// pairs on the FP32 pipe.  (One warp doing it all in FP64 took ~0.5 ms per
+// chunk at 512 blocks: each FP64 exponential holds this part's FP64 pipe for
+// dozens of instructions of ~64 cycles each.)
+constexpr int kCdSelThreads = 32 * kCdataChunk;
+
+__global__ void __launch_bounds__(kCdSelThreads) k_cdata_select(const double* part, int G, int B, int s0, int T,
+                                                               int P, double d1, ForceDates fd, Ctl* ctl)
+{
+    __shared__ double rss_s[kCdataChunk];
+    __shared__ int flag_s[kCdataChunk];   // bit 0: stop here; bit 1: forced (date of interest, RSS >= D1)
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (q < B) {
+        long long km = kNegInfKey;
+        for (int g = lane; g < G; g += 32) {
+            const long long k = order_key(part[((size_t)g * B + q) * 3]);
+            km = k > km ? k : km;
+        }
+        km = warp_max_key(km);
+        Df s1 = {0.0f, 0.0f}, s2 = {0.0f, 0.0f};
+        if (km != kNegInfKey) {
+            const double M = key_value(km);
+            for (int g = lane; g < G; g += 32) {
+                const double* o = part + ((size_t)g * B + q) * 3;
+                if (order_key(o[0]) == kNegInfKey) continue;
+                const float e = ex2_approx((float)(o[0] - M) * (float)kLog2e);
+                s1 = df_add_f(s1, (float)o[1] * e);
+                s2 = df_add_f(s2, (float)o[2] * (e * e));
+            }
+        }
+        s1 = warp_sum_df(s1);
+        s2 = warp_sum_df(s2);
+        if (lane == 0) {
+            const double S1 = (double)s1.hi + (double)s1.lo, S2 = (double)s2.hi + (double)s2.lo;
+            const double rss = S1 * S1 / ((double)P * S2);
+            const int sobs = s0 + q + 1;
+            bool date = sobs == T;
+            for (int i = 0; i < fd.n; ++i) date = date || fd.t[i] == sobs;
+            const bool low = !(rss >= d1);   // RSS < D1 (a degenerate NaN also stops)
+            rss_s[q] = rss;
+            flag_s[q] = ((low || date) ? 1 : 0) | ((date && !low) ? 2 : 0);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int f = (int)threadIdx.x < B ? flag_s[threadIdx.x] : 0;
+        const unsigned m = __ballot_sync(0xffffffffu, (f & 1) != 0);
+        const int at = m ? __ffs(m) - 1 : (B - 1);
+        if (threadIdx.x == 0) {
+            ctl->cd_stop = m ? at + 1 : B;
+            ctl->cd_found = m ? 1 : 0;
+            ctl->cd_forced = m ? (flag_s[at] >> 1) & 1 : 0;
+            ctl->rss = rss_s[at];
+        }
     }
 }
 
-// PIT of the committed observations s0 + 1 .. s0 + stop (Section 4.1): lane q
+// PIT of the committed observations s0 + 1 .. s0 + stop (Section 4.1): warp q
 // combines the blocks' (max log w(s-1), sum w, sum w I[Y_s <= y_s]) of
-// observation s0 + q + 1 into the weighted share.
-__global__ void k_pit_final(const double* part, int G, int B, int s0, const Ctl* ctl, double* pit)
+// observation s0 + q + 1 into the weighted share (FP64 throughout: the PIT is
+// compared with the oracle's to 1e-9).
+__global__ void __launch_bounds__(kCdSelThreads) k_pit_final(const double* part, int G, int B, int s0,
+                                                            const Ctl* ctl, double* pit)
 {
-    const int q = threadIdx.x;
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (q >= ctl->cd_stop || q >= B) return;
-    double M = -INFINITY;
-    for (int g = 0; g < G; ++g) M = fmax(M, part[((size_t)g * B + q) * 3]);
-    double S1 = 0.0, S2 = 0.0;
-    for (int g = 0; g < G; ++g) {
-        const double* o = part + ((size_t)g * B + q) * 3;
-        if (o[0] == -INFINITY) continue;
-        const double e = exp(o[0] - M);
-        S1 += o[1] * e;
-        S2 += o[2] * e;
+    long long km = kNegInfKey;
+    for (int g = lane; g < G; g += 32) {
+        const long long k = order_key(part[((size_t)g * B + q) * 3]);
+        km = k > km ? k : km;
     }
-    pit[s0 + q] = S2 / S1;
+    km = warp_max_key(km);
+    const double M = key_value(km);
+    double S1 = 0.0, S2 = 0.0;
+    if (km != kNegInfKey)
+        for (int g = lane; g < G; g += 32) {
+            const double* o = part + ((size_t)g * B + q) * 3;
+            if (order_key(o[0]) == kNegInfKey) continue;
+            const double e = exp(o[0] - M);
+            S1 += o[1] * e;
+            S2 += o[2] * e;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+        S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+    }
+    if (lane == 0) pit[s0 + q] = S2 / S1;
 }
 
 cudaError_t launch_pit_final(const double* part, int G, int B, int s0, const Ctl* ctl, double* pit,
                              cudaStream_t s)
 {
-    k_pit_final<<<1, 32, 0, s>>>(part, G, B, s0, ctl, pit);
+    k_pit_final<<<1, kCdSelThreads, 0, s>>>(part, G, B, s0, ctl, pit);
     count_launch();
     return cudaGetLastError();
 }
@@ -1217,7 +1283,7 @@ cudaError_t launch_pit_final(const double* part, int G, int B, int s0, const Ctl
 cudaError_t launch_cdata_select(const double* part, int G, int B, int s0, int T, int P, double d1,
                                 const ForceDates& fd, Ctl* ctl, cudaStream_t s)
 {
-    k_cdata_select<<<1, 32, 0, s>>>(part, G, B, s0, T, P, d1, fd, ctl);
+    k_cdata_select<<<1, kCdSelThreads, 0, s>>>(part, G, B, s0, T, P, d1, fd, ctl);
     count_launch();
     return cudaGetLastError();
 }

@@ -554,6 +554,10 @@ struct ObsPipe {
     }
 };
 
+// Observations per chunk of the data-tempering C phase's speculative stop
+// search (k_cdata, k_cdata_select).
+constexpr int kCdataChunk = 32;
+
 constexpr int kChunkF32 = 1024;   // observations per staged chunk (4 KB)
 constexpr int kChunkF64 = 512;    // elements per staged chunk (4 KB)
 
