@@ -151,6 +151,15 @@ struct PolicyEgarchF32T {
         const Obs y = obs[s - 1];
         return s == 1 ? mdl.template logdens<true>(y) : mdl.template logdens<false>(y);
     }
+    // The data-tempering C phase can keep its per-observation terms in log2
+    // units (l_s = ln2 u_s + kTermConst) and sum them on the FP32 pipe.
+    static constexpr bool kLog2Terms = true;
+    static constexpr double kTermConst = Model::kTermConst;
+    __device__ static float logdens2(Model& mdl, const Obs* obs, int s, int)
+    {
+        const Obs y = obs[s - 1];
+        return s == 1 ? mdl.template logdens2<true>(y) : mdl.template logdens2<false>(y);
+    }
     using Pit = PitMixture<float, I>;
     __device__ static void pit_setup(const ModelDev& m, const double* th, Pit& pm) { pit_setup_egarch<float, K, I>(m, th, pm); }
     // observed standardized shock after logdens of observation s
@@ -185,6 +194,9 @@ struct PolicyEgarchF64 {
         const Obs y = obs[s - 1];
         return s == 1 ? mdl.template logdens<true>(y) : mdl.template logdens<false>(y);
     }
+    static constexpr bool kLog2Terms = false;
+    static constexpr double kTermConst = 0.0;
+    __device__ static float logdens2(Model&, const Obs*, int, int) { return 0.0f; }
     using Pit = PitMixture<double, I>;
     __device__ static void pit_setup(const ModelDev& m, const double* th, Pit& pm) { pit_setup_egarch<double, K, I>(m, th, pm); }
     __device__ static double obs_shock(const Model& mdl, const Obs*, int, int) { return mdl.eps; }
@@ -208,6 +220,9 @@ struct PolicyLinreg {
     {
         return mdl.logdens(obs + (size_t)(s - 1) * W);
     }
+    static constexpr bool kLog2Terms = false;
+    static constexpr double kTermConst = 0.0;
+    __device__ static float logdens2(Model&, const Obs*, int, int) { return 0.0f; }
     using Pit = PitMixture<double, 1>;
     __device__ static void pit_setup(const ModelDev&, const double*, Pit& pm)
     {
@@ -499,6 +514,46 @@ struct CdataArgs {
     uint64_t seed;
 };
 
+// Double-float pair (value = hi + lo) for the data-tempering log weights:
+// Knuth's TwoSum on the FP32 pipe.
+struct Df2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ Df2 df2_norm(float s, float e)
+{
+    const float t = s + e;
+    return {t, e - (t - s)};
+}
+
+__device__ __forceinline__ Df2 df2_add_f(Df2 x, float b)
+{
+    const float s = x.hi + b;
+    const float bv = s - x.hi;
+    const float e = (x.hi - (s - bv)) + (b - bv);
+    return df2_norm(s, e + x.lo);
+}
+
+__device__ __forceinline__ Df2 df2_add(Df2 x, Df2 y)
+{
+    const float s = x.hi + y.hi;
+    const float bv = s - x.hi;
+    const float e = (x.hi - (s - bv)) + (y.hi - bv);
+    return df2_norm(s, e + (x.lo + y.lo));
+}
+
+// Warp maximum of normalised pairs (ordered by hi, then lo).
+__device__ __forceinline__ Df2 warp_max_df2(Df2 x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h = __shfl_xor_sync(0xffffffffu, x.hi, o);
+        const float l = __shfl_xor_sync(0xffffffffu, x.lo, o);
+        if (h > x.hi || (h == x.hi && l > x.lo)) x = {h, l};
+    }
+    return x;
+}
+
 template <class Pol>
 __global__ void __launch_bounds__(kMutThreads) k_cdata(CdataArgs a)
 {
@@ -562,6 +617,12 @@ __global__ void __launch_bounds__(kMutThreads) k_cdata(CdataArgs a)
                 o[1] = S1;
                 o[2] = S2;
             }
+        } else if constexpr (Pol::kLog2Terms) {
+            // the terms in log2 units, summed as a double-float pair on the
+            // FP32 pipe (as in the statistics pass, whose sums these repeat)
+            Df2 d = {0.0f, 0.0f};
+            for (int q = 0; q < n; ++q) d = df2_add_f(d, Pol::logdens2(mdl, obs, a.s0 + q + 1, a.W));
+            add = kLn2 * ((double)d.hi + (double)d.lo) + (double)n * Pol::kTermConst;
         } else {
             for (int q = 0; q < n; ++q) add += Pol::logdens(mdl, obs, a.s0 + q + 1, a.W);
         }
@@ -576,31 +637,63 @@ __global__ void __launch_bounds__(kMutThreads) k_cdata(CdataArgs a)
         }
         return;
     }
-    for (int q = 0; q < a.B; ++q) {
-        double l = Pol::logdens(mdl, obs, a.s0 + q + 1, a.W);
-        lw += isnan(l) ? -INFINITY : l;
-        const double x = active ? lw : -INFINITY;
-        const double mw = warp_max(x);
-        float w = 0.0f;
-        if (x != -INFINITY && mw != -INFINITY) w = ex2_approx((float)((x - mw) * kLog2e));
-        const float s1 = warp_sum(w);
-        const float s2 = warp_sum(w * w);
-        if (lane == 0) {
-            trip[warp][q][0] = mw;
-            trip[warp][q][1] = s1;
-            trip[warp][q][2] = s2;
+    if constexpr (Pol::kLog2Terms) {
+        // FP32 recursion: the log weight log w(s) = log w(s0) + sum of the
+        // chunk's terms is carried in log2 units as a double-float pair (the
+        // per-observation constant, common to every particle, is added back
+        // to the block maxima only), so the warp maxima and the weights need no
+        // FP64 instruction (each holds this part's FP64 pipe for ~64 cycles).
+        const double lw2 = lw * kLog2e;
+        const Df2 x0 = {(float)lw2, (float)(lw2 - (double)(float)lw2)};
+        bool dead = !active || !(lw2 > -INFINITY);
+        Df2 d = {0.0f, 0.0f};
+        for (int q = 0; q < a.B; ++q) {
+            const float u = Pol::logdens2(mdl, obs, a.s0 + q + 1, a.W);
+            dead = dead || !(u > -INFINITY && u < INFINITY);
+            d = df2_add_f(d, u);
+            const Df2 x = dead ? Df2{-INFINITY, 0.0f} : df2_add(x0, d);
+            const Df2 mx = warp_max_df2(x);
+            float w = 0.0f;
+            if (!dead && mx.hi != -INFINITY) w = ex2_approx((x.hi - mx.hi) + (x.lo - mx.lo));
+            const float s1 = warp_sum(w);
+            const float s2 = warp_sum(w * w);
+            if (lane == 0) {
+                trip[warp][q][0] = mx.hi == -INFINITY ? -INFINITY
+                                                      : kLn2 * ((double)mx.hi + (double)mx.lo) +
+                                                            (double)(q + 1) * Pol::kTermConst;
+                trip[warp][q][1] = s1;
+                trip[warp][q][2] = s2;
+            }
+        }
+    } else {
+        for (int q = 0; q < a.B; ++q) {
+            double l = Pol::logdens(mdl, obs, a.s0 + q + 1, a.W);
+            lw += isnan(l) ? -INFINITY : l;
+            const double x = active ? lw : -INFINITY;
+            const double mw = warp_max(x);
+            float w = 0.0f;
+            if (x != -INFINITY && mw != -INFINITY) w = ex2_approx((float)((x - mw) * kLog2e));
+            const float s1 = warp_sum(w);
+            const float s2 = warp_sum(w * w);
+            if (lane == 0) {
+                trip[warp][q][0] = mw;
+                trip[warp][q][1] = s1;
+                trip[warp][q][2] = s2;
+            }
         }
     }
     __syncthreads();
     for (int q = threadIdx.x; q < a.B; q += blockDim.x) {
         double M = -INFINITY;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = fmax(M, trip[w][q][0]);
+        // the warps' sums rescaled by FP32 exponentials of the FP64 differences
+        // (the sums are of FP32 weights already)
         double S1 = 0.0, S2 = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
             if (trip[w][q][0] == -INFINITY) continue;
-            const double e = exp(trip[w][q][0] - M);
-            S1 += trip[w][q][1] * e;
-            S2 += trip[w][q][2] * e * e;
+            const float e = ex2_approx((float)(trip[w][q][0] - M) * (float)kLog2e);
+            S1 += trip[w][q][1] * (double)e;
+            S2 += trip[w][q][2] * (double)(e * e);
         }
         double* o = a.part + ((size_t)blockIdx.x * a.B + q) * 3;
         o[0] = M;

@@ -312,8 +312,10 @@ struct EgarchF32 {
         es = (float)(st[K] * kSfac);
     }
 
+    // One observation's log density less the constant kTermConst, in log2
+    // units: l_t = ln2 u + kTermConst.
     template <bool kFirst>
-    __device__ __forceinline__ double logdens(float y)
+    __device__ __forceinline__ float logdens2(float y)
     {
         if constexpr (kFirst) update_volatility_first();
         else update_volatility();
@@ -337,7 +339,14 @@ struct EgarchF32 {
             for (int i = 0; i < I; ++i) sum += ex2_approx(x[i] - m);
             u = (m - e) + lg2_approx(sum);
         }
-        return kLn2 * (double)u + (-0.5 * kLog2Pi - kLogSfac);
+        return u;
+    }
+    static constexpr double kTermConst = -0.5 * kLog2Pi - kLogSfac;
+
+    template <bool kFirst>
+    __device__ __forceinline__ double logdens(float y)
+    {
+        return kLn2 * (double)logdens2<kFirst>(y) + kTermConst;
     }
 
     // Closes a 32-observation partial (the product of shifted mixture sums
