@@ -480,6 +480,19 @@ smc_status smc_power_search(const double* ll, int P, double phi, double d1, int 
 smc_status smc_resample(const double* w, int J, int N, int resampler, uint64_t seed,
                         uint64_t cycle, int32_t* idx, void* stream);
 
+/* The S phase as a run takes it, from log weights (Section 3.3 for the
+ * resampling, Section 4.2 for the group weight): logw is device [J*N]
+ * (-inf for a particle of weight zero), w_n = exp(logw_n - max_n logw_n),
+ * then exactly smc_resample on those weights.  The quantised weights
+ * floor(2^32 w_n) are those of the FP64 exponential; the kernel evaluates
+ * them in 64-bit fixed point and falls back to the FP64 exponential only
+ * where 2^32 w_n lies within 2^-18 of an integer.  lwbar: host [J] or NULL,
+ * receives log wbar_j = max + log(sum_n w_n / N) with the sums formed
+ * exactly in fixed point.  Returns SMC_EDEGENERATE if every log weight of a
+ * group is -inf (its slots then keep their own particles).  Synchronises. */
+smc_status smc_resample_logw(const double* logw, int J, int N, int resampler, uint64_t seed,
+                             uint64_t cycle, int32_t* idx, double* lwbar, void* stream);
+
 /* Grand mean, s.d., NSE and RNE (Section 2.3) of each of nf functions
  * g (device [nf][J*N], group-major columns).  out: host [nf][4]. */
 smc_status smc_group_moments(const double* g, int nf, int J, int N, double* out, void* stream);

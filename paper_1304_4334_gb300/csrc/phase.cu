@@ -1,6 +1,7 @@
 // C-phase search, S phase, covariance/Cholesky and estimator kernels.
 #include "phase.cuh"
 #include "covtile.cuh"
+#include "exp2_table.h"
 
 #include <cstdio>
 
@@ -520,8 +521,9 @@ cudaError_t launch_adapt_h(Ctl* ctl, int P, double acc_target, int hmin, int hma
 // RSS(dphi) = (sum_n w_n)^2 / (P sum_n w_n^2) with w_n = exp(dphi (l_n - max l))
 // (Section 3.3, pooled over all particles).  One pass evaluates 32 candidate
 // increments spread evenly over (lo, hi]: lane c of every warp owns candidate
-// c and the warp walks its 32-particle tiles with shuffles.  Candidate weights
-// are FP32 hardware exponentials summed in FP32 over one tile; tile sums
+// c and the warp walks its 32-particle tiles in shared memory.  Candidate
+// weights are FP32 hardware exponentials summed in FP32 over one tile (in a
+// fixed order); tile sums
 // (<= 32) enter 64-bit fixed point (2^-36 units), so block and grid totals are
 // exact integer sums whose value does not depend on the order of addition.
 // The whole search (max l, then every pass) is one cooperative launch with at
@@ -530,7 +532,6 @@ cudaError_t launch_adapt_h(Ctl* ctl, int P, double acc_target, int hmin, int hma
 constexpr int kSearchThreads = 512;
 constexpr int kSearchWarps = kSearchThreads / 32;
 constexpr int kCand = 32;
-constexpr int kRegTiles = 4;                      // tiles a warp keeps in registers
 constexpr float kFixScale = 68719476736.0f;       // 2^36
 
 int search_grid(int P)
@@ -542,8 +543,9 @@ int search_grid(int P)
 }
 
 // Scratch (doubles): 8 barrier words, 3 rotating slots of 64 fixed-point
-// totals, one max key per block, then the shifted FP32 log likelihoods of the
-// tiles a warp does not keep in registers.
+// totals, one max key per block, then room for the shifted FP32 log
+// likelihoods of every tile (used when a block's range exceeds its shared
+// memory).
 struct SearchScratch {
     unsigned int* bar;            // [0] arrivals, [1] generation, [2] abort
     unsigned long long* acc;      // [3][2 kCand]
@@ -563,7 +565,7 @@ __host__ __device__ inline SearchScratch search_scratch(double* part, int G)
 
 size_t search_part_len(int P)
 {
-    return 8 + 3 * 2 * kCand + (size_t)search_grid(P) + ((size_t)P + 1) / 2;
+    return 8 + 3 * 2 * kCand + (size_t)search_grid(P) + (size_t)(P + 31) / 32 * 16;
 }
 
 size_t search_bar_bytes() { return 8 * sizeof(double); }
@@ -591,19 +593,28 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p)
     return v;
 }
 
+__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int* p)
+{
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Barrier over the blocks of a cooperative launch.  Arrivals (a release
 // add, ordering the block's earlier writes) count up to the grid size; the
-// last arrival resets the count and advances the generation (release), which
-// the others poll with acquire loads.  The wait is bounded: on time-out (or
-// when another block gave up) the abort word is set and every block returns
-// false.
-__device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks)
+// last arrival resets the count and advances the generation (release).  The
+// others poll the generation with relaxed loads and take an acquire fence
+// once it has moved.  Thread 0 of each block keeps the generation it expects
+// to leave (gen, read once before the block's first arrival: the word moves
+// only after every block has arrived).  The wait is bounded: every 32 polls it
+// checks the abort word and the clock; on time-out (or when another block gave
+// up) it sets the abort word and every block returns false.
+__device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, unsigned int& gen)
 {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
-        const unsigned int gen = ld_acquire_u32(bar + 1);
         unsigned int arrived;
         asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
         if (arrived + 1u == nblocks) {
@@ -611,14 +622,16 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks)
             asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
         } else {
             const uint64_t t0 = global_ns();
-            while (ld_acquire_u32(bar + 1) == gen) {
-                if (ld_acquire_u32(bar + 2) != 0u || global_ns() - t0 > kWaitLimitNs) {
+            for (unsigned int it = 1; ld_relaxed_u32(bar + 1) == gen; ++it) {
+                if ((it & 31u) == 0u && (ld_relaxed_u32(bar + 2) != 0u || global_ns() - t0 > kWaitLimitNs)) {
                     atomicExch(bar + 2, 1u);
                     ok = 0;
                     break;
                 }
             }
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
         }
+        gen += 1u;
     }
     __syncthreads();
     return ok != 0;
@@ -640,10 +653,65 @@ __device__ __forceinline__ long long warp_max_key(long long k)
     return k;
 }
 
+// Conversions on the integer pipes.  On this part the FP64 pipe (about two
+// lanes per clock per SM) also executes the conversions that touch 64-bit
+// values (FP32 <-> 64-bit integer, FP64 <-> FP32), so the search keeps them
+// out of its per-particle and per-tile work.
+//
+// floor(f) for finite f >= 0 (f < 2^64): the 24-bit significand shifted.
+__device__ __forceinline__ uint64_t f32_to_u64_floor(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    if ((u >> 23) == 0u) return 0ull;                 // zero (subnormals are flushed)
+    const int e = (int)(u >> 23) - 150;               // f = m 2^e
+    const uint64_t m = (uint64_t)((u & 0x7fffffu) | 0x800000u);
+    return e >= 0 ? m << e : (e > -24 ? m >> -e : 0ull);
+}
+
+// v to FP32 through its two 32-bit halves (each rounded, then one rounded sum).
+__device__ __forceinline__ float u64_to_f32(uint64_t v)
+{
+    return fmaf(__uint2float_rn((uint32_t)(v >> 32)), 4294967296.0f, __uint2float_rn((uint32_t)v));
+}
+
+// d as hi + lo in FP32 from its bits: hi carries the leading 24 significand
+// bits (truncated), lo the next 29 (rounded to 24).  ok is false outside
+// 2^-126 <= |d| < 2^128 (and for inf or NaN), where the caller converts in FP64.
+__device__ __forceinline__ float2 split_f64(double d, bool& ok)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+    ok = e >= -126 && e <= 127;
+    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+    const float hi = __uint_as_float(sign | ((uint32_t)(e + 127) << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
+    float lo = 0.0f;
+    if (e - 52 >= -126) {
+        const float scale = __uint_as_float((uint32_t)(e - 52 + 127) << 23);   // 2^(e - 52)
+        lo = __uint_as_float(sign | __float_as_uint(__uint2float_rn((uint32_t)(b & 0x1fffffffu)) * scale));
+    }
+    return make_float2(hi, lo);
+}
+
+// Particles split into one contiguous range of 32-particle tiles per block.
+// When a block's range fits (kSearchResident particles) its log likelihoods
+// (FP64, read once from HBM) and then their shifted FP32 values stay in its
+// shared memory for the whole search; otherwise the FP32 values go to global
+// scratch once and every pass stages them, kSearchStage at a time.
+constexpr int kSearchResident = 16 * 1024;   // 12 bytes each: 192 KB
+constexpr int kSearchStage = 48 * 1024;      // 4 bytes each: 192 KB
+
+size_t search_smem(int P, int G)
+{
+    const int tpb = ((P + 31) / 32 + G - 1) / G;
+    return tpb * 32 <= kSearchResident ? (size_t)tpb * 32 * (sizeof(float) + sizeof(double))
+                                       : (size_t)kSearchStage * sizeof(float);
+}
+
 __global__ void __launch_bounds__(kSearchThreads, 1) k_power_search(const double* __restrict__ ll, int P,
                                                                    Ctl* ctl, double* part, double d1,
                                                                    int passes)
 {
+    extern __shared__ __align__(16) float xs[];
     __shared__ long long skey[kSearchWarps];
     __shared__ unsigned long long sacc[2 * kCand];
     __shared__ double scand[kCand];
@@ -652,26 +720,25 @@ __global__ void __launch_bounds__(kSearchThreads, 1) k_power_search(const double
     const SearchScratch sc = search_scratch(part, G);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ntiles = (P + 31) / 32;
-    const int nw = G * kSearchWarps;
-    const int gw = blockIdx.x * kSearchWarps + warp;
+    const int tpb = (ntiles + G - 1) / G;
+    const int t0 = min(ntiles, (int)blockIdx.x * tpb), t1 = min(ntiles, t0 + tpb);
+    const int n0 = t0 * 32, nb = (t1 - t0) * 32;   // the block's particles [n0, n0 + nb), padded to tiles
+    const bool resident = tpb * 32 <= kSearchResident;
+    long long* lraw = reinterpret_cast<long long*>(xs + tpb * 32);   // resident: the FP64 values' bits
     const double phi = ctl->phi;
+    unsigned int gen = 0;
+    if (threadIdx.x == 0) gen = ld_relaxed_u32(sc.bar + 1);
     if (threadIdx.x < 2 * kCand) sacc[threadIdx.x] = 0ull;
     if (blockIdx.x == 0 && threadIdx.x < 2 * kCand) sc.acc[threadIdx.x] = 0ull;   // slot of pass 0
 
     // ---- max l over all particles (integer keys: exact, order-free) ----
-    long long kr[kRegTiles];
     long long km = kNegInfKey;
-#pragma unroll
-    for (int k = 0; k < kRegTiles; ++k) {
-        const int t = gw + k * nw;
-        const int n = t * 32 + lane;
-        kr[k] = (t < ntiles && n < P) ? order_key(ll[n]) : kNegInfKey;
-        km = kr[k] > km ? kr[k] : km;
-    }
-    for (int t = gw + kRegTiles * nw; t < ntiles; t += nw) {
-        const int n = t * 32 + lane;
-        const long long kk = n < P ? order_key(ll[n]) : kNegInfKey;
-        km = kk > km ? kk : km;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < nb; i += kSearchThreads) {
+        const int n = n0 + i;
+        const long long k = n < P ? order_key(ll[n]) : kNegInfKey;
+        if (resident) lraw[i] = k;
+        km = k > km ? k : km;
     }
     km = warp_max_key(km);
     if (lane == 0) skey[warp] = km;
@@ -681,7 +748,7 @@ __global__ void __launch_bounds__(kSearchThreads, 1) k_power_search(const double
         k = warp_max_key(k);
         if (lane == 0) sc.bkey[blockIdx.x] = k;
     }
-    if (!grid_barrier(sc.bar, G)) {
+    if (!grid_barrier(sc.bar, G, gen)) {
         if (threadIdx.x == 0) raise_error(&ctl->err, kErrTimeout);
         return;
     }
@@ -693,20 +760,26 @@ __global__ void __launch_bounds__(kSearchThreads, 1) k_power_search(const double
     kg = warp_max_key(lane < kSearchWarps ? skey[lane] : kNegInfKey);
     const double llmax = key_value(kg);
 
-    // ---- shifted FP32 log likelihoods: registers, then scratch ----
-    float xr[kRegTiles];
-#pragma unroll
-    for (int k = 0; k < kRegTiles; ++k) {
-        xr[k] = -INFINITY;
-        if (gw + k * nw < ntiles && kr[k] != kNegInfKey) xr[k] = (float)(key_value(kr[k]) - llmax);
-    }
-    for (int t = gw + kRegTiles * nw; t < ntiles; t += nw) {
-        const int n = t * 32 + lane;
-        if (n < P) {
-            const long long kk = order_key(ll[n]);
-            sc.xf[n] = kk == kNegInfKey ? -INFINITY : (float)(key_value(kk) - llmax);
+    // ---- shifted FP32 log likelihoods x_n = l_n - max l (-inf past P) ----
+    // (l_hi - max_hi) + (l_lo - max_lo) in FP32: within 2^-23 |x| + 2^-45 |l|.
+    bool mok = true;
+    const float2 mx = kg == kNegInfKey ? make_float2(0.f, 0.f) : split_f64(llmax, mok);
+    // (a resident block converts the keys each thread stored itself)
+    float* xdst = resident ? xs : sc.xf + n0;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < nb; i += kSearchThreads) {
+        const int n = n0 + i;
+        const long long k = resident ? lraw[i] : (n < P ? order_key(ll[n]) : kNegInfKey);
+        float x = -INFINITY;
+        if (k != kNegInfKey) {
+            const double l = key_value(k);
+            bool ok;
+            const float2 lx = split_f64(l, ok);
+            x = (ok && mok) ? (lx.x - mx.x) + (lx.y - mx.y) : (float)(l - llmax);
         }
+        xdst[i] = x;
     }
+    // (the first pass's barrier orders these writes before their reads)
 
     double lo = 0.0, hi = 1.0 - phi, dphi = hi;
     int done = (kg == kNegInfKey) || !(hi > 0.0);
@@ -717,42 +790,48 @@ __global__ void __launch_bounds__(kSearchThreads, 1) k_power_search(const double
     const float cmp = (float)(d1 * (double)P * 16.0);
     for (int p = 0; p < passes && !done; ++p) {
         const int slot = p % 3;
-        // candidates (FP64) and their FP32 exponent scale, once per block
+        // candidates (FP64) and their FP32 exponent scale, once per block;
+        // every candidate is positive (at least (1 - phi) / 32^passes), so
+        // dc x is -inf for a dead particle and its weight ex2(-inf) = 0
         if (warp == 0) {
             const double cv = candidate(lo, hi, lane);
             scand[lane] = cv;
-            sdc[lane] = (float)(cv * kLog2e);
+            sdc[lane] = fmaxf((float)(cv * kLog2e), 1e-30f);
         }
         __syncthreads();
         const float dc = sdc[lane];
+        const float2 dc2 = make_float2(dc, dc);
         unsigned long long q1 = 0ull, q2 = 0ull;
-        auto tile = [&](float x) {
-            // eight shuffles and exponentials issued before their eight
-            // additions (the sums still run j = 0, 1, .., 31)
-            float a1 = 0.0f, a2 = 0.0f;
-#pragma unroll
-            for (int j0 = 0; j0 < 32; j0 += 8) {
-                float w[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float xj = __shfl_sync(0xffffffffu, x, j0 + u);
-                    w[u] = xj == -INFINITY ? 0.0f : ex2_approx(dc * xj);
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    a1 += w[u];
-                    a2 = fmaf(w[u], w[u], a2);
-                }
+        for (int c0 = 0; c0 < nb; c0 += kSearchStage) {
+            const int cn = min(kSearchStage, nb - c0);
+            if (!resident) {
+                __syncthreads();
+                for (int i = threadIdx.x; i < cn; i += kSearchThreads) xs[i] = __ldcg(sc.xf + n0 + c0 + i);
+                __syncthreads();
             }
-            q1 += __float2ull_rn(a1 * kFixScale);
-            q2 += __float2ull_rn(a2 * kFixScale);
-        };
+            // lane c owns candidate c; a warp walks its tiles, reading each
+            // tile's 32 values as eight broadcast 16-byte loads, two particles
+            // per paired FP32 instruction (four partial sums per tile)
+            for (int t = warp; t < cn / 32; t += kSearchWarps) {
+                const float4* xt = reinterpret_cast<const float4*>(xs + t * 32);
+                float2 s1a = make_float2(0.f, 0.f), s1b = s1a, s2a = s1a, s2b = s1a;
 #pragma unroll
-        for (int k = 0; k < kRegTiles; ++k)
-            if (gw + k * nw < ntiles) tile(xr[k]);
-        for (int t = gw + kRegTiles * nw; t < ntiles; t += nw) {
-            const int n = t * 32 + lane;
-            tile(n < P ? sc.xf[n] : -INFINITY);
+                for (int u = 0; u < 8; ++u) {
+                    const float4 v = xt[u];
+                    const float2 ea = __fmul2_rn(dc2, make_float2(v.x, v.y));
+                    const float2 eb = __fmul2_rn(dc2, make_float2(v.z, v.w));
+                    const float2 wa = make_float2(ex2_approx(ea.x), ex2_approx(ea.y));
+                    const float2 wb = make_float2(ex2_approx(eb.x), ex2_approx(eb.y));
+                    s1a = __fadd2_rn(s1a, wa);
+                    s1b = __fadd2_rn(s1b, wb);
+                    s2a = __ffma2_rn(wa, wa, s2a);
+                    s2b = __ffma2_rn(wb, wb, s2b);
+                }
+                const float a1 = (s1a.x + s1a.y) + (s1b.x + s1b.y);
+                const float a2 = (s2a.x + s2a.y) + (s2b.x + s2b.y);
+                q1 += f32_to_u64_floor(a1 * kFixScale);
+                q2 += f32_to_u64_floor(a2 * kFixScale);
+            }
         }
         atomicAdd(&sacc[lane], q1);
         atomicAdd(&sacc[kCand + lane], q2);
@@ -764,13 +843,13 @@ __global__ void __launch_bounds__(kSearchThreads, 1) k_power_search(const double
             // the slot of the next pass was last read before the previous barrier
             sc.acc[((p + 1) % 3) * 2 * kCand + threadIdx.x - 2 * kCand] = 0ull;
         }
-        if (!grid_barrier(sc.bar, G)) {
+        if (!grid_barrier(sc.bar, G, gen)) {
             if (threadIdx.x == 0) raise_error(&ctl->err, kErrTimeout);
             return;
         }
         // every warp takes the same decision from the same totals
-        const float q1s = __ull2float_rn(__ldcg(sc.acc + slot * 2 * kCand + lane)) * 2.3283064365386963e-10f;
-        const float q2s = __ull2float_rn(__ldcg(sc.acc + slot * 2 * kCand + kCand + lane)) * 2.3283064365386963e-10f;
+        const float q1s = u64_to_f32(__ldcg(sc.acc + slot * 2 * kCand + lane)) * 2.3283064365386963e-10f;
+        const float q2s = u64_to_f32(__ldcg(sc.acc + slot * 2 * kCand + kCand + lane)) * 2.3283064365386963e-10f;
         const unsigned below = __ballot_sync(0xffffffffu, q1s * q1s < cmp * q2s);
         if (below == 0u) {
             // RSS stays >= D1 up to hi: in the first pass this takes the whole
@@ -825,9 +904,17 @@ cudaError_t launch_power_search(const double* ll, int P, double d1, int passes, 
                                 Ctl* ctl, cudaStream_t s)
 {
     int G = search_grid(P);
+    const size_t smem = search_smem(P, G);
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t ea = cudaFuncSetAttribute(k_power_search, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)(kSearchStage * sizeof(float)));
+        if (ea != cudaSuccess) return ea;
+        attr = true;
+    }
     void* args[] = {(void*)&ll, (void*)&P, (void*)&ctl, (void*)&part, (void*)&d1, (void*)&passes};
     const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_power_search, dim3(G), dim3(kSearchThreads),
-                                                      args, 0, s);
+                                                      args, smem, s);
     count_launch();
     return e;
 }
@@ -840,14 +927,19 @@ cudaError_t launch_power_search(const double* ll, int P, double d1, int passes, 
 // on summation order or thread count.
 constexpr int kSelThreads = 1024;
 
-size_t select_smem(int N) { return (size_t)N * (sizeof(uint64_t) + sizeof(uint32_t)); }
+// Shared arrays indexed through sp(n) = n + n/8: a thread's eight
+// consecutive entries (the prefix scans give each thread a contiguous range)
+// then fall in distinct banks across a warp, 64- and 32-bit alike.
+__host__ __device__ __forceinline__ int sp(int n) { return n + (n >> 3); }
+
+size_t select_smem(int N) { return (size_t)sp(N) * (sizeof(uint64_t) + sizeof(uint32_t)); }
 
 __device__ int upper_bound_u64(const uint64_t* a, int n, uint64_t u)
 {
-    int lo = 0, hi = n;   // first index with a[idx] > u
+    int lo = 0, hi = n;   // first index with a[sp(idx)] > u
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (a[mid] > u) hi = mid;
+        if (a[sp(mid)] > u) hi = mid;
         else lo = mid + 1;
     }
     return lo < n ? lo : n - 1;
@@ -865,32 +957,133 @@ __device__ __forceinline__ long long block_max_key(long long k, long long* red)
     return k;
 }
 
-// Block sums of a and b (every thread receives them) by a pairwise tree over
-// shared memory, in a fixed order; blockDim.x = kSelThreads.
-__device__ __forceinline__ void block_sum_tree2(double& a, double& b, double* t1, double* t2)
+// ---- exp(x), x <= 0, in 64-bit fixed point on the integer pipes ----
+// The S phase quantises 2^32 exp(x) and sums exp(x) and exp(2x) over the
+// group; an FP64 exponential per particle would hold the FP64 pipe (about
+// two lanes per clock per SM on this part) for most of the kernel.  Here
+// |x| = n ln2/256 + u with 0 <= u < ln2/256, so
+//     exp(x) = 2^-(n >> 8) * 2^-((n & 255)/256) * e^-u,
+// the middle factor from a table of the 256 powers (units 2^-63, the nearest
+// integers) and e^-u from its Taylor polynomial to degree 5, nested as
+// 1 - u(1 - u/2(1 - u/3(1 - u/4(1 - u/5)))) (the first omitted term,
+// u^6/720 < 2^-60, and each truncation are far below the table's 2^-63).
+// |x| enters in units of 2^-57 (exact for |x| >= 2^-5, truncated below);
+// ln2/256 in units of 2^-72, so n ln2/256 is exact to 2^-58 for every n here.
+// The result M 2^-(63 + k) is within 2^-59 relative of exp(x); |x| >= 64
+// (exp(x) < 2^-92, and -inf, NaN) returns false.
+__device__ __forceinline__ uint64_t mulq63(uint64_t a, uint64_t b)   // floor(a b / 2^63)
 {
-    const int tid = threadIdx.x;
-    t1[tid] = a;
-    t2[tid] = b;
-    __syncthreads();
+    return (__umul64hi(a, b) << 1) | ((a * b) >> 63);
+}
+
+__device__ __forceinline__ bool exp_fixed(double x, const uint64_t* tab, uint64_t& M, int& k)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffu);
+    if (e >= 1029) return false;                                   // |x| >= 64, inf, NaN
+    const uint64_t m = (b & 0xfffffffffffffull) | 0x10000000000000ull;
+    const int sh = e - 1018;                                       // X = |x| 2^57 < 2^63
+    const uint64_t X = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> -sh) : 0ull);
+    constexpr uint64_t kOne = 1ull << 63;
+    if (X == 0) {                                                  // |x| < 2^-57: exp(x) rounds to 1
+        M = kOne;
+        k = 0;
+        return true;
+    }
+    // n = floor(|x| 256/ln2), possibly one too small or too large ...
+    long long n = (long long)(__umul64hi(X, kInvLn2x256Q50) >> 43);
+    // ... made exact by the sign of the remainder u = |x| - n ln2/256 (2^-72 units)
+    __int128 D = ((__int128)X << 15) - (__int128)((unsigned __int128)(uint64_t)n * kLn2Q64);
+    if (D < 0) {
+        n -= 1;
+        D += kLn2Q64;
+    } else if (D >= (__int128)kLn2Q64) {
+        n += 1;
+        D -= kLn2Q64;
+    }
+    const uint64_t U = (uint64_t)D >> 9;                           // u 2^63 < 2^55
+    uint64_t p = kOne - U / 5;
+    p = kOne - mulq63(U, p) / 4;
+    p = kOne - mulq63(U, p) / 3;
+    p = kOne - (mulq63(U, p) >> 1);
+    p = kOne - mulq63(U, p);                                       // e^-u 2^63
+    M = mulq63(tab[n & 255], p);
+    k = (int)(n >> 8);
+    return true;
+}
+
+// q = floor(2^32 exp(x)) from the fixed-point value, with the group sums'
+// terms exp(x) 2^62 and exp(2x) 2^62 (truncated).  When 2^32 exp(x) lies
+// within 2^-18 of an integer (the fixed point's error, the FP64 rounding of
+// exp(x) and a last-place difference between exponentials all fit well
+// inside that), q is taken from the FP64 exponential instead, so that the
+// quantised weight is floor(2^32 exp(x)) of the FP64 value exp(x) returns.
+__device__ __forceinline__ uint64_t quantise_exp(double x, const uint64_t* tab, uint64_t& w62, uint64_t& w2_62)
+{
+    uint64_t M;
+    int k;
+    w62 = w2_62 = 0;
+    if (!exp_fixed(x, tab, M, k)) return 0;
+    w62 = k < 63 ? M >> (1 + k) : 0ull;
+    w2_62 = k < 32 ? __umul64hi(M, M) >> (2 * k) : 0ull;
+    const int s = 31 + k;
+    if (s >= 64) return 0;                                         // 2^32 exp(x) < 1/2
+    const uint64_t q = M >> s;
+    const uint64_t rem = M & ((1ull << s) - 1ull);
+    const uint64_t mg = 1ull << (s - 18);
+    const bool near = (q != 0 && rem < mg) || rem >= (1ull << s) - mg;
+    if (M == (1ull << 63) || !near) return q;                        // exp(x) = 1 exactly, or clear of a boundary
+    return (uint64_t)(exp(x) * 4294967296.0);
+}
+
+// Exact block sums of two 128-bit unsigned values (every thread receives
+// them): warp shuffles with carries, then one warp over the warp totals.
+__device__ __forceinline__ void add_u128(uint64_t& lo, uint64_t& hi, uint64_t olo, uint64_t ohi)
+{
+    const uint64_t t = lo + olo;
+    hi += ohi + (t < lo ? 1ull : 0ull);
+    lo = t;
+}
+
+__device__ __forceinline__ void block_sum_u128x2(unsigned __int128& a, unsigned __int128& b, uint64_t* red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t v[4] = {(uint64_t)a, (uint64_t)(a >> 64), (uint64_t)b, (uint64_t)(b >> 64)};
 #pragma unroll
-    for (int h = kSelThreads / 2; h >= 32; h >>= 1) {
-        if (tid < h) {
-            t1[tid] += t1[tid + h];
-            t2[tid] += t2[tid + h];
-        }
-        __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+        uint64_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = __shfl_xor_sync(0xffffffffu, v[i], o);
+        add_u128(v[0], v[1], w[0], w[1]);
+        add_u128(v[2], v[3], w[2], w[3]);
     }
-    if (tid < 32) {
-        double x = warp_sum(t1[tid]), y = warp_sum(t2[tid]);
-        if (tid == 0) {
-            t1[0] = x;
-            t2[0] = y;
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) red[4 * warp + i] = v[i];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = lane < nw ? red[4 * lane + i] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            uint64_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[i] = __shfl_xor_sync(0xffffffffu, v[i], o);
+            add_u128(v[0], v[1], w[0], w[1]);
+            add_u128(v[2], v[3], w[2], w[3]);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) red[i] = v[i];
         }
     }
     __syncthreads();
-    a = t1[0];
-    b = t2[0];
+    a = ((unsigned __int128)red[1] << 64) | red[0];
+    b = ((unsigned __int128)red[3] << 64) | red[2];
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
@@ -900,26 +1093,27 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
     const int N = a.N;
     double* ws = reinterpret_cast<double*>(sm_raw);                        // w, then q, then prefix r
     uint64_t* qs = reinterpret_cast<uint64_t*>(sm_raw);
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(sm_raw + (size_t)N * sizeof(uint64_t));
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(sm_raw + (size_t)sp(N) * sizeof(uint64_t));
     __shared__ long long redk[32];
-    __shared__ double tree1[kSelThreads], tree2[kSelThreads];
-    __shared__ uint64_t redu[32];
+    __shared__ uint64_t redu[4 * 32];
+    __shared__ uint64_t tab[256];
     __shared__ int bad;
     const int j = blockIdx.x;
     const size_t base = (size_t)j * N;
     const int tid = threadIdx.x;
     if (tid == 0) bad = 0;
+    if (a.mode != 2 && tid < 256) tab[tid] = g_exp2_neg256[tid];
 
     // ---- weights ----
-    // Maxima as order-preserving integer keys and the two weight sums by a
-    // shared-memory tree: each FP64 instruction holds its pipe for ~64 cycles
-    // on this part, and a shuffle tree per warp costs every warp five of them.
+    // Maxima as order-preserving integer keys and the two weight sums as
+    // exact integers: each FP64 instruction holds its pipe for ~64 cycles on
+    // this part, so FP64 work per particle is kept to forming log w - max.
     double wmax;
     if (a.mode == 2) {
         long long km = order_key(0.0);
         for (int n = tid; n < N; n += blockDim.x) {
             const double w = a.w[base + n];
-            ws[n] = w;
+            ws[sp(n)] = w;
             const long long k = order_key(w);
             km = k > km ? k : km;
         }
@@ -927,30 +1121,37 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
     } else {
         const double dphi = a.mode == 0 ? a.ctl->dphi : 0.0;
         long long km = kNegInfKey;
+#pragma unroll 4
         for (int n = tid; n < N; n += blockDim.x) {
             double lw;
             if (a.mode == 0) {
                 const double l = a.ll[base + n];
-                lw = l == -INFINITY ? -INFINITY : dphi * l;
+                lw = order_key(l) == kNegInfKey ? -INFINITY : dphi * l;
             } else {
                 lw = a.logw[base + n];
             }
             const long long k = order_key(lw);   // NaN counts as -inf
             if (k == kNegInfKey) lw = -INFINITY;
-            ws[n] = lw;
+            ws[sp(n)] = lw;
             km = k > km ? k : km;
         }
-        const long long kmax = block_max_key(km, redk);
+        const long long kmax = block_max_key(km, redk);   // (its barriers also publish tab)
         const double lmax = key_value(kmax);
-        double s1 = 0.0, s2 = 0.0;
+        // q_n = floor(2^32 exp(log w_n - max)) straight from the fixed-point
+        // exponential, over ws in place; the sums of w and w^2 as exact
+        // 128-bit sums of the 2^62-unit terms (order-free), converted once.
+        unsigned __int128 S1 = 0, S2 = 0;
         for (int n = tid; n < N; n += blockDim.x) {
-            const double w = kmax == kNegInfKey ? 0.0 : exp(ws[n] - lmax);
-            ws[n] = w;
-            s1 += w;
-            s2 += w * w;
+            uint64_t q = 0, t1 = 0, t2 = 0;
+            if (kmax != kNegInfKey) q = quantise_exp(ws[sp(n)] - lmax, tab, t1, t2);
+            qs[sp(n)] = q;
+            S1 += t1;
+            S2 += t2;
         }
-        block_sum_tree2(s1, s2, tree1, tree2);
+        block_sum_u128x2(S1, S2, redu);
         if (tid == 0) {
+            const double s1 = 4.0 * (double)(uint64_t)(S1 >> 64) + 0x1p-62 * (double)(uint64_t)S1;
+            const double s2 = 4.0 * (double)(uint64_t)(S2 >> 64) + 0x1p-62 * (double)(uint64_t)S2;
             const double lwj = lmax + log(s1 / (double)N);
             a.lw[j] = lwj;
             a.a[j] += lwj;
@@ -971,17 +1172,15 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
     const int per = (N + blockDim.x - 1) / blockDim.x;
     const int n0 = min(N, tid * per), n1 = min(N, n0 + per);
     __syncthreads();
-    // (w / max w is w itself when the weights came from log weights, whose
-    // maximum is exp(0) = 1; 2^32 w~ is exact, and truncation is the floor of
-    // a non-negative number.)
+    // (From log weights q_n is already in qs.  Given weights: 2^32 w~ is
+    // exact, and truncation is the floor of a non-negative number.)
     uint64_t qloc = 0;
-    const bool unit_max = wmax == 1.0;
     for (int n = n0; n < n1; ++n) {
-        const double w = ws[n];
-        const double wn = w > 0.0 ? (unit_max ? w : w / wmax) : 0.0;
-        const uint64_t q = (uint64_t)(wn * 4294967296.0);
-        qs[n] = q;
-        qloc += q;
+        if (a.mode == 2) {
+            const double w = ws[sp(n)];
+            qs[sp(n)] = (uint64_t)((w > 0.0 ? w / wmax : 0.0) * 4294967296.0);
+        }
+        qloc += qs[sp(n)];
     }
     const uint64_t Q = block_sum<uint64_t>(qloc, redu);
     if (Q == 0) {
@@ -995,8 +1194,8 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
         const uint64_t incl = block_inclusive_scan_u64(qloc, redu);
         uint64_t run = incl - qloc;
         for (int n = n0; n < n1; ++n) {
-            run += qs[n];
-            qs[n] = run;
+            run += qs[sp(n)];
+            qs[sp(n)] = run;
         }
         __syncthreads();
         const bool systematic = a.scheme == 3;
@@ -1018,16 +1217,24 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
         return;
     }
     // ---- deterministic counts and residuals ----
+    // floor(N q / Q) from the reciprocal floor((2^64 - 1) / Q): the estimate
+    // is the quotient or one less (N q < 2^46), and one step fixes it.
+    const uint64_t rQ = ~0ull / Q;
     uint64_t placed = 0, rloc = 0;
     for (int n = n0; n < n1; ++n) {
-        const uint64_t q = qs[n];
+        const uint64_t q = qs[sp(n)];
         uint64_t c = 0, r = q;
         if (a.scheme == 0) {
-            c = ((uint64_t)N * q) / Q;                 // floor(N w~_n)
-            r = (uint64_t)N * q - Q * c;
+            const uint64_t Nq = (uint64_t)N * q;
+            c = __umul64hi(Nq, rQ);                    // floor(N w~_n)
+            r = Nq - Q * c;
+            if (r >= Q) {
+                c += 1;
+                r -= Q;
+            }
         }
-        cnt[n] = (uint32_t)c;
-        qs[n] = r;
+        cnt[sp(n)] = (uint32_t)c;
+        qs[sp(n)] = r;
         placed += c;
         rloc += r;
     }
@@ -1036,26 +1243,26 @@ __global__ void __launch_bounds__(kSelThreads) k_select(SelectArgs a)
     const uint64_t incl = block_inclusive_scan_u64(rloc, redu);
     uint64_t run = incl - rloc;
     for (int n = n0; n < n1; ++n) {
-        run += qs[n];
-        qs[n] = run;
+        run += qs[sp(n)];
+        qs[sp(n)] = run;
     }
     __syncthreads();
-    const uint64_t R = qs[N - 1];
+    const uint64_t R = qs[sp(N - 1)];
     // ---- residual draws ----
     for (uint64_t m = tid; m < M; m += blockDim.x) {
         const U64x4 x = philox4x64_10((uint64_t)j, m, a.cycle, (uint64_t)kTagResample << 32, a.seed, 0);
         const uint64_t u = __umul64hi(x.v0, R);
         const int n = upper_bound_u64(qs, N, u);
-        atomicAdd(&cnt[n], 1u);
+        atomicAdd(&cnt[sp(n)], 1u);
     }
     __syncthreads();
     // ---- expand counts into indices ----
     uint64_t cl = 0;
-    for (int n = n0; n < n1; ++n) cl += cnt[n];
+    for (int n = n0; n < n1; ++n) cl += cnt[sp(n)];
     const uint64_t cincl = block_inclusive_scan_u64(cl, redu);
     uint64_t off = cincl - cl;
     for (int n = n0; n < n1; ++n) {
-        const uint32_t c = cnt[n];
+        const uint32_t c = cnt[sp(n)];
         for (uint32_t k = 0; k < c; ++k) {
             if (off < (uint64_t)N) a.idx[base + off] = n;
             else bad = 1;

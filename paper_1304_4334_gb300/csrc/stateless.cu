@@ -347,6 +347,44 @@ smc_status smc_resample(const double* w, int J, int N, int resampler, uint64_t s
     return h ? SMC_ECUDA : SMC_OK;
 }
 
+smc_status smc_resample_logw(const double* logw, int J, int N, int resampler, uint64_t seed, uint64_t cycle,
+                             int32_t* idx, double* lwbar, void* stream)
+{
+    if (!logw || !idx || J < 1 || N < 1 || N > SMC_MAX_N || resampler < 0 || resampler > 3) return SMC_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int* err = nullptr;
+    double* buf = nullptr;   // a [J], lw [J], gstat [3 J]
+    CK(cudaMallocAsync((void**)&err, sizeof(int), s));
+    CK(cudaMallocAsync((void**)&buf, (size_t)5 * J * sizeof(double), s));
+    CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(buf, 0, (size_t)J * sizeof(double), s));
+    SelectArgs sa;
+    std::memset(&sa, 0, sizeof sa);
+    sa.mode = 1;
+    sa.logw = logw;
+    sa.J = J;
+    sa.N = N;
+    sa.scheme = resampler;
+    sa.seed = seed;
+    sa.cycle = cycle;
+    sa.a = buf;
+    sa.lw = buf + J;
+    sa.gstat = buf + 2 * J;
+    sa.idx = idx;
+    sa.err = err;
+    cudaError_t e = launch_select(sa, s);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && lwbar)
+        e = cudaMemcpyAsync(lwbar, buf + J, (size_t)J * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(err, s);
+    cudaFreeAsync(buf, s);
+    if (e != cudaSuccess) return SMC_ECUDA;
+    if (h & kErrDegenerate) return SMC_EDEGENERATE;
+    return h ? SMC_ECUDA : SMC_OK;
+}
+
 smc_status smc_group_moments(const double* g, int nf, int J, int N, double* out, void* stream)
 {
     if (!g || !out || nf < 1 || J < 2 || N < 1) return SMC_EINVAL;

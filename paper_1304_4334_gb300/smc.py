@@ -146,6 +146,7 @@ def _declare(L):
     L.smc_cov_chol.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
     L.smc_power_search.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_int, dp, dp, vp]
     L.smc_resample.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, vp, vp]
+    L.smc_resample_logw.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, vp, vp, vp]
     L.smc_group_moments.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp, vp]
     L.smc_ml_from_groups.argtypes = [vp, C.c_int, dp, dp, vp]
 
@@ -603,6 +604,14 @@ def power_search(ll, phi, d1=0.5, passes=6, stream=None):
 
 def resample(w, J, N, idx, resampler=RESIDUAL, seed=0, cycle=0, stream=None):
     _check(lib().smc_resample(_ptr(w), J, N, resampler, seed, cycle, _ptr(idx), _stream(stream)))
+
+
+def resample_logw(logw, J, N, idx, resampler=RESIDUAL, seed=0, cycle=0, stream=None):
+    """S phase from log weights; returns log wbar_j of each group (host [J])."""
+    lwbar = np.zeros(J)
+    _check(lib().smc_resample_logw(_ptr(logw), J, N, resampler, seed, cycle, _ptr(idx), _dptr(lwbar),
+                                   _stream(stream)))
+    return lwbar
 
 
 def group_moments(g, J, N, stream=None):

@@ -59,3 +59,29 @@ def test_scaled_unit_identities():
     ln = -float("0.16331712998914049120")
     assert abs(ln - l2 * math.log(2.0)) < 1e-16
     assert abs(2.0 ** l2 - s) < 1e-16
+
+
+def test_fixed_point_exponential_table():
+    """The S phase's fixed-point exponential: round(ln 2 2^64),
+    round(256/ln 2 2^50) and the 256 powers round(2^(63 - j/256)), checked
+    with exact decimal arithmetic, plus the identities a wrong entry breaks:
+    the table is strictly decreasing, and T[j] T[256 - j] = 2^125 within the
+    rounding of two entries."""
+    from decimal import Decimal, getcontext
+    getcontext().prec = 60
+    src = open(os.path.join(CSRC, "exp2_table.h")).read()
+    ln2 = Decimal(2).ln()
+    l64 = int(re.search(r"kLn2Q64 = (\d+)ull", src).group(1))
+    r50 = int(re.search(r"kInvLn2x256Q50 = (\d+)ull", src).group(1))
+    assert l64 == int((ln2 * 2 ** 64).to_integral_value())
+    assert r50 == int((Decimal(256) / ln2 * 2 ** 50).to_integral_value())
+    body = src[src.index("g_exp2_neg256"):]
+    tab = [int(t) for t in re.findall(r"(\d+)ull", body)]
+    assert len(tab) == 256 and tab[0] == 2 ** 63
+    for j, t in enumerate(tab):
+        exact = Decimal(2) ** (Decimal(63) - Decimal(j) / 256)
+        assert abs(Decimal(t) - exact) <= Decimal("0.5"), j
+    assert all(a > b for a, b in zip(tab, tab[1:]))
+    for j in range(1, 256):
+        prod = Decimal(tab[j]) * Decimal(tab[256 - j]) if j != 128 else Decimal(tab[128]) ** 2
+        assert abs(prod / Decimal(2) ** 125 - 1) < Decimal(2) ** -61, j

@@ -405,6 +405,63 @@ def test_stratified_systematic_bit_exact(S, J, N, scheme):
     assert np.array_equal(host(idx).reshape(J, N), idx_o)
 
 
+def _log_weight_cases(J, N, rng, kind):
+    """Log weights of the shapes the S phase meets: tempered log likelihoods
+    (dphi l_n, wide spread), data-tempering increments (narrow), weights
+    spanning the fixed point's whole range, dead particles and exact ties."""
+    if kind == "power":
+        lw = 1e-3 * (-30000.0 + 4000.0 * rng.standard_normal(J * N))
+    elif kind == "data":
+        lw = 0.3 * rng.standard_normal(J * N) - 2.0
+    else:
+        lw = -rng.uniform(0.0, 70.0, J * N)
+        lw[rng.random(J * N) < 0.05] = -np.inf
+        g = lw.reshape(J, N)
+        g[:, 0] = 0.0
+        if N > 3:
+            g[:, 1] = 0.0                      # ties at the maximum
+            g[:, 2] = -2.0 ** -52              # exp(x) just below one
+            g[:, 3] = -1e-20                   # exp(x) rounds to one
+    return lw
+
+
+@pytest.mark.parametrize("J,N,scheme,kind", [(64, 1024, 0, "power"), (128, 8192, 0, "power"),
+                                              (5, 8192, 1, "data"), (7, 333, 0, "wide"),
+                                              (16, 4096, 2, "wide"), (3, 1000, 3, "data"),
+                                              (2, 1, 0, "wide"), (33, 2048, 0, "wide")])
+def test_resample_from_log_weights_bit_exact(S, J, N, scheme, kind):
+    """The in-run S phase (weights from log weights by the fixed-point
+    exponential) selects exactly the oracle's indices for the FP64 weights
+    exp(lw - max), and its log wbar_j is the group's log mean weight."""
+    torch = torch_cuda()
+    rng = np.random.default_rng(J * N + scheme)
+    lw = _log_weight_cases(J, N, rng, kind)
+    g = lw.reshape(J, N)
+    w = np.exp(g - g.max(axis=1, keepdims=True)).reshape(-1)
+    if scheme <= 1:
+        idx_o = O.resample(w, J, N, resid=scheme == 0, seed=11, cycle=7)
+    else:
+        idx_o = O.resample_scheme(w, J, N, scheme, seed=11, cycle=7)
+    idx = torch.empty(J * N, dtype=torch.int32, device="cuda")
+    lwbar = S.resample_logw(dev(lw), J, N, idx, scheme, seed=11, cycle=7)
+    assert np.array_equal(host(idx).reshape(J, N), idx_o)
+    mx = g.max(axis=1)
+    want = mx + np.log(np.exp(g - mx[:, None]).sum(axis=1) / N)
+    err = np.abs(lwbar - want) / np.maximum(1.0, np.abs(want))
+    assert err.max() <= 1e-13, err.max()
+
+
+def test_resample_from_log_weights_degenerate(S):
+    torch = torch_cuda()
+    lw = np.zeros(2 * 64)
+    lw[64:] = -np.inf
+    idx = torch.empty(128, dtype=torch.int32, device="cuda")
+    with pytest.raises(S.SMCError) as e:
+        S.resample_logw(dev(lw), 2, 64, idx)
+    assert e.value.status == S.EDEGENERATE
+    assert np.array_equal(host(idx)[64:], np.arange(64))
+
+
 def test_resample_dominant_and_degenerate(S):
     torch = torch_cuda()
     N = 8192
