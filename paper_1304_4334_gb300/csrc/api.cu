@@ -836,7 +836,8 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
     CU(dalloc(&ctx->cov_part, (size_t)(ctx->cov_G + 1) * (d + d * (d + 1) / 2)));   // + totals row
     CU(dalloc(&ctx->search_part, search_part_len(P)));
     CU(cudaMemset(ctx->search_part, 0, search_bar_bytes()));
-    CU(dalloc(&ctx->cd_part, (size_t)((P + kMutThreads - 1) / kMutThreads) * kCdataChunk * 3));
+    CU(dalloc(&ctx->cd_part, cdata_part_len((P + kMutThreads - 1) / kMutThreads)));
+    CU(cudaMemset(ctx->cd_part, 0, cdata_part_len((P + kMutThreads - 1) / kMutThreads) * sizeof(double)));
     const int nf_max = d + 3;
     CU(dalloc(&ctx->mom_part, (size_t)nf_max * J * 2));
     CU(dalloc(&ctx->mom_out, (size_t)nf_max * 4));

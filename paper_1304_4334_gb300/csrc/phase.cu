@@ -1383,66 +1383,124 @@ __device__ __forceinline__ Df warp_sum_df(Df x)
     return x;
 }
 
-// Data-tempering stop search of one chunk (Section 3.3, "C phase
-// termination"): warp q combines the G blocks' (max log w, sum w, sum w^2) of
-// observation s0 + q + 1 into the pooled RSS, and the first observation with
-// RSS < D1 (or a date of interest, or T) ends the chunk.  The block maxima are
-// compared as order-preserving integer keys; the rescaling weights
-// exp(M_g - M) are FP32 exponentials of the FP64 differences (the blocks' sums
-// are themselves sums of FP32 weights, ~1e-7), accumulated as double-float
-// pairs on the FP32 pipe.  (One warp doing it all in FP64 took ~0.5 ms per
-// chunk at 512 blocks: each FP64 exponential holds this part's FP64 pipe for
-// dozens of instructions of ~64 cycles each.)
-constexpr int kCdSelThreads = 32 * kCdataChunk;
-
-__global__ void __launch_bounds__(kCdSelThreads) k_cdata_select(const double* part, int G, int B, int s0, int T,
-                                                               int P, double d1, ForceDates fd, Ctl* ctl)
+// FP64 -> FP32, round to nearest even, from the bits (the conversion
+// instruction for values outside the normal FP32 range).
+__device__ __forceinline__ float f64_to_f32(double d)
 {
-    __shared__ double rss_s[kCdataChunk];
-    __shared__ int flag_s[kCdataChunk];   // bit 0: stop here; bit 1: forced (date of interest, RSS >= D1)
-    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (q < B) {
-        long long km = kNegInfKey;
-        for (int g = lane; g < G; g += 32) {
-            const long long k = order_key(part[((size_t)g * B + q) * 3]);
-            km = k > km ? k : km;
-        }
-        km = warp_max_key(km);
-        Df s1 = {0.0f, 0.0f}, s2 = {0.0f, 0.0f};
-        if (km != kNegInfKey) {
-            const double M = key_value(km);
-            for (int g = lane; g < G; g += 32) {
-                const double* o = part + ((size_t)g * B + q) * 3;
-                if (order_key(o[0]) == kNegInfKey) continue;
-                const float e = ex2_approx((float)(o[0] - M) * (float)kLog2e);
-                s1 = df_add_f(s1, (float)o[1] * e);
-                s2 = df_add_f(s2, (float)o[2] * (e * e));
-            }
-        }
-        s1 = warp_sum_df(s1);
-        s2 = warp_sum_df(s2);
-        if (lane == 0) {
-            const double S1 = (double)s1.hi + (double)s1.lo, S2 = (double)s2.hi + (double)s2.lo;
-            const double rss = S1 * S1 / ((double)P * S2);
-            const int sobs = s0 + q + 1;
-            bool date = sobs == T;
-            for (int i = 0; i < fd.n; ++i) date = date || fd.t[i] == sobs;
-            const bool low = !(rss >= d1);   // RSS < D1 (a degenerate NaN also stops)
-            rss_s[q] = rss;
-            flag_s[q] = ((low || date) ? 1 : 0) | ((date && !low) ? 2 : 0);
+    const uint64_t b = (uint64_t)__double_as_longlong(d);
+    const uint32_t e = (uint32_t)(b >> 52) & 0x7ffu;
+    if (e - 897u >= 254u) return __double2float_rn(d);        // FP32 exponent outside 1..254
+    const uint64_t mant = b & 0xfffffffffffffull;
+    uint32_t f = ((uint32_t)(b >> 32) & 0x80000000u) | ((e - 896u) << 23) | (uint32_t)(mant >> 29);
+    const uint32_t rest = (uint32_t)mant & 0x1fffffffu;          // the 29 bits rounded away
+    f += (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) ? 1u : 0u;   // carries into the exponent
+    return __uint_as_float(f);
+}
+
+// Data-tempering stop search of one chunk (Section 3.3, "C phase
+// termination"): block q combines the G blocks' (max log w, sum w, sum w^2)
+// of observation s0 + q + 1 into the pooled RSS; the last block to finish
+// takes the first observation with RSS < D1 (or a date of interest, or T) as
+// the end of the chunk.  The block maxima are compared as order-preserving
+// integer keys; the rescaling weights exp(M_g - M) are FP32 exponentials of
+// the differences formed from the FP32 hi/lo splits of the FP64 values (the
+// blocks' sums are themselves sums of FP32 weights, ~1e-7), accumulated as
+// double-float pairs on the FP32 pipe, with no FP64 instruction per block
+// and observation.  (One warp doing it all in FP64 took ~0.5 ms per chunk at
+// 512 blocks: each FP64 instruction holds this part's FP64 pipe for ~64
+// cycles; one warp per observation in a single block, 39 us per chunk at
+// 293 blocks.)  The per-observation results and the arrival count sit in a
+// tail of the chunk scratch (cdata_part_len); the count returns to zero.
+constexpr int kCdSelThreads = 32 * kCdataChunk;   // k_pit_final: one warp per observation
+constexpr int kCdStopThreads = 256;
+
+size_t cdata_part_len(int G) { return (size_t)G * kCdataChunk * 3 + 2 * kCdataChunk + 8; }
+
+struct CdStopTail {
+    double* rss;           // [kCdataChunk]
+    int* flag;             // [kCdataChunk]
+    unsigned int* count;   // arrivals of the current launch
+};
+
+__device__ __forceinline__ CdStopTail cdstop_tail(double* part, int G)
+{
+    double* t = part + (size_t)G * kCdataChunk * 3;
+    return {t, reinterpret_cast<int*>(t + kCdataChunk), reinterpret_cast<unsigned int*>(t + 2 * kCdataChunk)};
+}
+
+__global__ void __launch_bounds__(kCdStopThreads) k_cdata_select(double* part, int G, int B, int s0, int T, int P,
+                                                                double d1, ForceDates fd, Ctl* ctl)
+{
+    constexpr int kW = kCdStopThreads / 32;
+    __shared__ long long sk[kW];
+    __shared__ float sd[4][kW];
+    __shared__ int last;
+    const int q = blockIdx.x;   // gridDim.x = B
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const CdStopTail tl = cdstop_tail(part, G);
+    long long km = kNegInfKey;
+    for (int g = tid; g < G; g += kCdStopThreads) {
+        const long long k = order_key(part[((size_t)g * B + q) * 3]);
+        km = k > km ? k : km;
+    }
+    km = warp_max_key(km);
+    if (lane == 0) sk[w] = km;
+    __syncthreads();
+    km = warp_max_key(lane < kW ? sk[lane] : kNegInfKey);
+    Df s1 = {0.0f, 0.0f}, s2 = {0.0f, 0.0f};
+    if (km != kNegInfKey) {
+        bool mok;
+        const float2 mx = split_f64(key_value(km), mok);
+        const double M = key_value(km);
+        for (int g = tid; g < G; g += kCdStopThreads) {
+            const double* o = part + ((size_t)g * B + q) * 3;
+            if (order_key(o[0]) == kNegInfKey) continue;
+            bool ok;
+            const float2 ox = split_f64(o[0], ok);
+            const float x = (ok && mok) ? (ox.x - mx.x) + (ox.y - mx.y) : (float)(o[0] - M);
+            const float e = ex2_approx(x * (float)kLog2e);
+            s1 = df_add_f(s1, f64_to_f32(o[1]) * e);
+            s2 = df_add_f(s2, f64_to_f32(o[2]) * (e * e));
         }
     }
+    s1 = warp_sum_df(s1);
+    s2 = warp_sum_df(s2);
+    if (lane == 0) {
+        sd[0][w] = s1.hi;
+        sd[1][w] = s1.lo;
+        sd[2][w] = s2.hi;
+        sd[3][w] = s2.lo;
+    }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        const int f = (int)threadIdx.x < B ? flag_s[threadIdx.x] : 0;
-        const unsigned m = __ballot_sync(0xffffffffu, (f & 1) != 0);
-        const int at = m ? __ffs(m) - 1 : (B - 1);
-        if (threadIdx.x == 0) {
-            ctl->cd_stop = m ? at + 1 : B;
-            ctl->cd_found = m ? 1 : 0;
-            ctl->cd_forced = m ? (flag_s[at] >> 1) & 1 : 0;
-            ctl->rss = rss_s[at];
+    if (tid == 0) {
+        Df a = {0.0f, 0.0f}, b = {0.0f, 0.0f};
+        for (int i = 0; i < kW; ++i) {   // fixed order
+            a = df_add(a, Df{sd[0][i], sd[1][i]});
+            b = df_add(b, Df{sd[2][i], sd[3][i]});
         }
+        const double S1 = (double)a.hi + (double)a.lo, S2 = (double)b.hi + (double)b.lo;
+        const double rss = S1 * S1 / ((double)P * S2);
+        const int sobs = s0 + q + 1;
+        bool date = sobs == T;
+        for (int i = 0; i < fd.n; ++i) date = date || fd.t[i] == sobs;
+        const bool low = !(rss >= d1);   // RSS < D1 (a degenerate NaN also stops)
+        tl.rss[q] = rss;
+        tl.flag[q] = ((low || date) ? 1 : 0) | ((date && !low) ? 2 : 0);
+        __threadfence();
+        last = atomicAdd(tl.count, 1u) == (unsigned int)B - 1u;
+    }
+    __syncthreads();
+    if (!last || tid >= 32) return;
+    __threadfence();
+    const int f = tid < B ? __ldcg(tl.flag + tid) : 0;
+    const unsigned m = __ballot_sync(0xffffffffu, (f & 1) != 0);
+    const int at = m ? __ffs(m) - 1 : (B - 1);
+    if (tid == 0) {
+        ctl->cd_stop = m ? at + 1 : B;
+        ctl->cd_found = m ? 1 : 0;
+        ctl->cd_forced = m ? (__ldcg(tl.flag + at) >> 1) & 1 : 0;
+        ctl->rss = __ldcg(tl.rss + at);
+        *tl.count = 0u;
     }
 }
 
@@ -1487,10 +1545,10 @@ cudaError_t launch_pit_final(const double* part, int G, int B, int s0, const Ctl
     return cudaGetLastError();
 }
 
-cudaError_t launch_cdata_select(const double* part, int G, int B, int s0, int T, int P, double d1,
+cudaError_t launch_cdata_select(double* part, int G, int B, int s0, int T, int P, double d1,
                                 const ForceDates& fd, Ctl* ctl, cudaStream_t s)
 {
-    k_cdata_select<<<1, kCdSelThreads, 0, s>>>(part, G, B, s0, T, P, d1, fd, ctl);
+    k_cdata_select<<<B, kCdStopThreads, 0, s>>>(part, G, B, s0, T, P, d1, fd, ctl);
     count_launch();
     return cudaGetLastError();
 }

@@ -124,7 +124,10 @@ struct ForceDates {
     int n;
     int t[65];   // dates of interest and the burn-in date
 };
-cudaError_t launch_cdata_select(const double* part, int G, int B, int s0, int T, int P, double d1,
+// Chunk scratch of the data-tempering C phase: per block and observation
+// (max log w, sum w, sum w^2), then the stop search's tail (zeroed once).
+size_t cdata_part_len(int G);
+cudaError_t launch_cdata_select(double* part, int G, int B, int s0, int T, int P, double d1,
                                 const ForceDates& fd, Ctl* ctl, cudaStream_t s);
 cudaError_t launch_pit_final(const double* part, int G, int B, int s0, const Ctl* ctl, double* pit,
                              cudaStream_t s);

@@ -348,11 +348,14 @@ def test_cov_chol_rank_deficient(S):
 
 
 # ------------------------------------------------------------------ C phase
-# 400,037 particles exceed the four tiles per warp kept in registers (152 blocks
-# x 16 warps x 4 x 32 = 311,296 on 152 SMs), so the rest go through scratch;
-# 33 leave most warps of the only block empty.
+# Each block keeps its range of particles in shared memory up to 16,384 of
+# them (2,490,368 particles on 152 SMs); 3,000,017 go through global scratch
+# staged once per pass, 7,500,001 in two stages per pass (49,344 per block
+# against 49,152 staged at a time).  33 leave most warps of the only block
+# empty.
 @pytest.mark.parametrize("P,phi,spread", [(65536, 0.0, 30.0), (1024, 0.3, 5.0), (4096, 0.9, 200.0),
-                                          (400037, 0.2, 50.0), (33, 0.0, 3.0)])
+                                          (400037, 0.2, 50.0), (33, 0.0, 3.0), (3000017, 0.1, 40.0),
+                                          (7500001, 0.0, 60.0)])
 def test_power_search_matches_oracle(S, P, phi, spread):
     rng = np.random.default_rng(P)
     ll = -16000 + spread * rng.standard_normal(P)
