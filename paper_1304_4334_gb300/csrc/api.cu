@@ -373,7 +373,7 @@ static void release(smc_ctx* c)
     void* ptrs[] = {c->obs, c->theta[0], c->theta[1], c->ll[0], c->ll[1], c->lp[0], c->lp[1],
                     c->grad[0], c->grad[1], c->ckpt, c->design_L,
                     c->state[0], c->state[1], c->thp, c->logw, c->g, c->a, c->lw, c->gstat,
-                    c->idx, c->cov_part, c->search_part, c->cd_part, c->mom_part, c->mom_out, c->ml_out,
+                    c->idx, c->cov_part, c->search_part, c->cd_part, c->cd_end, c->mom_part, c->mom_out, c->ml_out,
                     c->L, c->qmean, c->covtile, c->covshift_f, c->cov_tot, c->cov_counter, c->lq, c->a_score, c->pit, c->gather_ptrs, c->ctl};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -838,6 +838,7 @@ smc_status smc_init(const smc_model* m, const smc_config* c, const double* y, co
     CU(cudaMemset(ctx->search_part, 0, search_bar_bytes()));
     CU(dalloc(&ctx->cd_part, cdata_part_len((P + kMutThreads - 1) / kMutThreads)));
     CU(cudaMemset(ctx->cd_part, 0, cdata_part_len((P + kMutThreads - 1) / kMutThreads) * sizeof(double)));
+    if (c->tempering != SMC_POWER) CU(dalloc(&ctx->cd_end, Ps * (size_t)(1 + ctx->ns)));
     const int nf_max = d + 3;
     CU(dalloc(&ctx->mom_part, (size_t)nf_max * J * 2));
     CU(dalloc(&ctx->mom_out, (size_t)nf_max * 4));
@@ -1269,6 +1270,7 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
             ca.s0 = s0;
             ca.B = ctx->T - s0 < kCdataChunk ? ctx->T - s0 : kCdataChunk;
             ca.part = ctx->cd_part;
+            ca.end = ctx->cd_end;
             ca.stop = &ctx->ctl->cd_stop;
             ca.commit = 0;
             ca.pit = 0;

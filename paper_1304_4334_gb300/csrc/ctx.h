@@ -43,6 +43,7 @@ struct smc_ctx {
     int cov_G = 0;
     double* search_part = nullptr;
     double* cd_part = nullptr;       // [G][kCdataChunk][3] data-tempering statistics
+    double* cd_end = nullptr;        // [1 + ns][P] data tempering: the chunk's sum and end state (statistics pass)
     double* mom_part = nullptr;      // [nf][J][2]
     double* mom_out = nullptr;       // [nf][4]
     double* ml_out = nullptr;        // [3]

@@ -505,6 +505,10 @@ struct CdataArgs {
     int s0;                // observations already absorbed
     int B;                 // observations in this chunk (<= kCdataChunk, s0 + B <= T)
     double* part;          // [gridDim][B][3] statistics pass output
+    // [1 + ns][P] (nullable): the statistics pass leaves each particle's sum
+    // of the chunk's B terms and its recursion state after them, which a
+    // commit of all B observations (no PIT) then takes instead of recomputing
+    double* end;
     const int* stop;       // commit pass: observations to absorb (device)
     int commit;
     // Commit pass, probability integral transform (Section 4.1; nullable):
@@ -560,11 +564,23 @@ __global__ void __launch_bounds__(kMutThreads) k_cdata(CdataArgs a)
     using Real = typename Pol::Real;
     using Obs = typename Pol::Obs;
     __shared__ double trip[kMutThreads / 32][kCdataChunk][3];
+    __shared__ float tripf[kMutThreads / 32][kCdataChunk][4];   // log2 path: warp max (hi, lo), sums
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < a.P;
     const int pp = active ? p : a.P - 1;
     const size_t P = (size_t)a.P;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (a.commit && a.end && !a.pit && *a.stop == a.B) {
+        // every observation of the chunk is absorbed: the statistics pass's
+        // sum and end state are exactly what the recursion below would give
+        if (active) {
+            const double add = a.end[p];
+            a.ll[p] += add;
+            a.logw[p] += add;
+            for (int k = 0; k < Pol::kNs; ++k) a.state[k * P + p] = a.end[(size_t)(1 + k) * P + p];
+        }
+        return;
+    }
     double th[kMaxD];
     for (int i = 0; i < a.m.d; ++i) th[i] = a.theta[i * P + pp];
     typename Pol::Model mdl;
@@ -658,16 +674,22 @@ __global__ void __launch_bounds__(kMutThreads) k_cdata(CdataArgs a)
             const float s1 = warp_sum(w);
             const float s2 = warp_sum(w * w);
             if (lane == 0) {
-                trip[warp][q][0] = mx.hi == -INFINITY ? -INFINITY
-                                                      : kLn2 * ((double)mx.hi + (double)mx.lo) +
-                                                            (double)(q + 1) * Pol::kTermConst;
-                trip[warp][q][1] = s1;
-                trip[warp][q][2] = s2;
+                tripf[warp][q][0] = mx.hi;
+                tripf[warp][q][1] = mx.lo;
+                tripf[warp][q][2] = s1;
+                tripf[warp][q][3] = s2;
             }
         }
+        if (a.end && active) {   // the commit pass's sum over all B terms
+            double add = kLn2 * ((double)d.hi + (double)d.lo) + (double)a.B * Pol::kTermConst;
+            if (isnan(add)) add = -INFINITY;
+            a.end[p] = add;
+        }
     } else {
+        double add = 0.0;   // the commit pass's sum, in its order
         for (int q = 0; q < a.B; ++q) {
             double l = Pol::logdens(mdl, obs, a.s0 + q + 1, a.W);
+            add += l;
             lw += isnan(l) ? -INFINITY : l;
             const double x = active ? lw : -INFINITY;
             const double mw = warp_max(x);
@@ -681,24 +703,55 @@ __global__ void __launch_bounds__(kMutThreads) k_cdata(CdataArgs a)
                 trip[warp][q][2] = s2;
             }
         }
+        if (a.end && active) a.end[p] = isnan(add) ? -INFINITY : add;
+    }
+    if (a.end && active && Pol::kNs) {
+        Pol::state_out(mdl, st);
+        for (int k = 0; k < Pol::kNs; ++k) a.end[(size_t)(1 + k) * P + p] = st[k];
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < a.B; q += blockDim.x) {
-        double M = -INFINITY;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = fmax(M, trip[w][q][0]);
-        // the warps' sums rescaled by FP32 exponentials of the FP64 differences
-        // (the sums are of FP32 weights already)
-        double S1 = 0.0, S2 = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            if (trip[w][q][0] == -INFINITY) continue;
-            const float e = ex2_approx((float)(trip[w][q][0] - M) * (float)kLog2e);
-            S1 += trip[w][q][1] * (double)e;
-            S2 += trip[w][q][2] * (double)(e * e);
+    if constexpr (Pol::kLog2Terms) {
+        // the warps' (max, sums) in log2 units combined on the FP32 pipe; one
+        // conversion to natural units (with the per-observation constant) per
+        // observation
+        for (int q = threadIdx.x; q < a.B; q += blockDim.x) {
+            Df2 M = {-INFINITY, 0.0f};
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                const float h = tripf[w][q][0], l = tripf[w][q][1];
+                if (h > M.hi || (h == M.hi && l > M.lo)) M = {h, l};
+            }
+            Df2 S1 = {0.0f, 0.0f}, S2 = {0.0f, 0.0f};
+            if (M.hi != -INFINITY)
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                    if (tripf[w][q][0] == -INFINITY) continue;
+                    const float e = ex2_approx((tripf[w][q][0] - M.hi) + (tripf[w][q][1] - M.lo));
+                    S1 = df2_add_f(S1, tripf[w][q][2] * e);
+                    S2 = df2_add_f(S2, tripf[w][q][3] * (e * e));
+                }
+            double* o = a.part + ((size_t)blockIdx.x * a.B + q) * 3;
+            o[0] = M.hi == -INFINITY ? -INFINITY
+                                     : kLn2 * ((double)M.hi + (double)M.lo) + (double)(q + 1) * Pol::kTermConst;
+            o[1] = (double)S1.hi + (double)S1.lo;
+            o[2] = (double)S2.hi + (double)S2.lo;
         }
-        double* o = a.part + ((size_t)blockIdx.x * a.B + q) * 3;
-        o[0] = M;
-        o[1] = S1;
-        o[2] = S2;
+    } else {
+        for (int q = threadIdx.x; q < a.B; q += blockDim.x) {
+            double M = -INFINITY;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = fmax(M, trip[w][q][0]);
+            // the warps' sums rescaled by FP32 exponentials of the FP64 differences
+            // (the sums are of FP32 weights already)
+            double S1 = 0.0, S2 = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                if (trip[w][q][0] == -INFINITY) continue;
+                const float e = ex2_approx((float)(trip[w][q][0] - M) * (float)kLog2e);
+                S1 += trip[w][q][1] * (double)e;
+                S2 += trip[w][q][2] * (double)(e * e);
+            }
+            double* o = a.part + ((size_t)blockIdx.x * a.B + q) * 3;
+            o[0] = M;
+            o[1] = S1;
+            o[2] = S2;
+        }
     }
 }
 
