@@ -1254,37 +1254,59 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
             if (c.burnin > 0) fd.t[fd.n++] = c.burnin;   // the log score starts a cycle at b
         }
         const int G = (P + kMutThreads - 1) / kMutThreads;
+        // Chunks are queued in batches without waiting for the stop: each
+        // chunk's kernels do nothing once an earlier chunk of the cycle has
+        // found it (Ctl::cd_found), so a batch that overshoots costs only
+        // empty launches.  A cycle's first batch is as long as the previous
+        // cycle was; later batches take two chunks.
+        CU(cudaMemsetAsync(&ctx->ctl->cd_found, 0, sizeof(int), ctx->stream));
+        std::vector<int> start(1, 0);   // start[seq]: observations absorbed before chunk seq
+        int s_next = ctx->t_prev;
+        int batch = ctx->cd_chunks > 0 ? ctx->cd_chunks : 1;
         int s0 = ctx->t_prev;
         for (;;) {
-            CdataArgs ca;
-            ca.m = ctx->mdev;
-            ca.obs = ctx->obs;
-            ca.T = ctx->T;
-            ca.W = ctx->W;
-            ca.theta = ctx->theta[ctx->cur];
-            ca.state = ctx->state[ctx->cur];
-            ca.ll = ctx->ll[ctx->cur];
-            ca.logw = ctx->logw;
-            ca.P = P;
-            ca.ns = ctx->ns;
-            ca.s0 = s0;
-            ca.B = ctx->T - s0 < kCdataChunk ? ctx->T - s0 : kCdataChunk;
-            ca.part = ctx->cd_part;
-            ca.end = ctx->cd_end;
-            ca.stop = &ctx->ctl->cd_stop;
-            ca.commit = 0;
-            ca.pit = 0;
-            ca.seed = c.seed;
-            CU(launch_cdata(ca, c.precision, ctx->stream));
-            CU(launch_cdata_select(ctx->cd_part, G, ca.B, s0, ctx->T, P, d1, fd, ctx->ctl, ctx->stream));
-            ca.commit = 1;
-            ca.pit = ctx->pit != nullptr;
-            CU(launch_cdata(ca, c.precision, ctx->stream));
-            if (ctx->pit) CU(launch_pit_final(ctx->cd_part, G, ca.B, s0, ctx->ctl, ctx->pit, ctx->stream));
+            for (int b = 0; b < batch && s_next < ctx->T; ++b) {
+                const int seq = (int)start.size();
+                start.push_back(s_next);
+                CdataArgs ca;
+                ca.m = ctx->mdev;
+                ca.obs = ctx->obs;
+                ca.T = ctx->T;
+                ca.W = ctx->W;
+                ca.theta = ctx->theta[ctx->cur];
+                ca.state = ctx->state[ctx->cur];
+                ca.ll = ctx->ll[ctx->cur];
+                ca.logw = ctx->logw;
+                ca.P = P;
+                ca.ns = ctx->ns;
+                ca.s0 = s_next;
+                ca.B = ctx->T - s_next < kCdataChunk ? ctx->T - s_next : kCdataChunk;
+                ca.part = ctx->cd_part;
+                ca.end = ctx->cd_end;
+                ca.stop = &ctx->ctl->cd_stop;
+                ca.found = &ctx->ctl->cd_found;
+                ca.seq = seq;
+                ca.commit = 0;
+                ca.pit = 0;
+                ca.seed = c.seed;
+                CU(launch_cdata(ca, c.precision, ctx->stream));
+                CU(launch_cdata_select(ctx->cd_part, G, ca.B, s_next, ctx->T, P, d1, fd, ctx->ctl, seq, ctx->stream));
+                ca.commit = 1;
+                ca.pit = ctx->pit != nullptr;
+                CU(launch_cdata(ca, c.precision, ctx->stream));
+                if (ctx->pit) CU(launch_pit_final(ctx->cd_part, G, ca.B, s_next, ctx->ctl, ctx->pit, seq, ctx->stream));
+                s_next += ca.B;
+            }
             st = sync_ctl(ctx);
             if (st != SMC_OK) return st;
-            s0 += ctx->ctl_host->cd_stop;
-            if (ctx->ctl_host->cd_found) break;
+            const int f = ctx->ctl_host->cd_found;
+            if (f > 0 && f < (int)start.size()) {
+                s0 = start[f] + ctx->ctl_host->cd_stop;
+                ctx->cd_chunks = f;
+                break;
+            }
+            if (f != 0 || s_next >= ctx->T) return set_err(ctx, SMC_ECUDA, "data tempering: no stop found by observation %d", s_next);
+            batch = 2;
         }
         t_l = s0;
         rss = ctx->ctl_host->rss;

@@ -64,6 +64,7 @@ struct smc_ctx {
     Ctl* ctl_host = nullptr;         // pinned, two blocks: [0] the latest read-back, [1] the M phase's (pipelined runs)
     // run state
     int cycle = 0, t_prev = 0, done = 0;
+    int cd_chunks = 0;   // data tempering: chunks the last cycle's C phase took (batch size only)
     double phi = 0.0;
     int64_t msteps = 0;
     double evals = 0.0;

@@ -510,6 +510,11 @@ struct CdataArgs {
     // commit of all B observations (no PIT) then takes instead of recomputing
     double* end;
     const int* stop;       // commit pass: observations to absorb (device)
+    // The chunk's number within the cycle (1-based) and the device word naming
+    // the chunk that holds the stop (0: none yet); a chunk numbered after it
+    // does nothing, so that chunks can be queued before the stop is known.
+    const int* found;
+    int seq;
     int commit;
     // Commit pass, probability integral transform (Section 4.1; nullable):
     // part[block][q] gets (max log w(s-1), sum w(s-1), sum w(s-1) I[Y_s <= y_s])
@@ -570,6 +575,10 @@ __global__ void __launch_bounds__(kMutThreads) k_cdata(CdataArgs a)
     const int pp = active ? p : a.P - 1;
     const size_t P = (size_t)a.P;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (a.found) {
+        const int f = *a.found;
+        if (f != 0 && f < a.seq) return;
+    }
     if (a.commit && a.end && !a.pit && *a.stop == a.B) {
         // every observation of the chunk is absorbed: the statistics pass's
         // sum and end state are exactly what the recursion below would give

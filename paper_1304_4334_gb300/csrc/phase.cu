@@ -1429,12 +1429,13 @@ __device__ __forceinline__ CdStopTail cdstop_tail(double* part, int G)
 }
 
 __global__ void __launch_bounds__(kCdStopThreads) k_cdata_select(double* part, int G, int B, int s0, int T, int P,
-                                                                double d1, ForceDates fd, Ctl* ctl)
+                                                                double d1, ForceDates fd, Ctl* ctl, int seq)
 {
     constexpr int kW = kCdStopThreads / 32;
     __shared__ long long sk[kW];
     __shared__ float sd[4][kW];
     __shared__ int last;
+    if (ctl->cd_found != 0) return;   // an earlier chunk of this cycle holds the stop
     const int q = blockIdx.x;   // gridDim.x = B
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const CdStopTail tl = cdstop_tail(part, G);
@@ -1497,7 +1498,7 @@ __global__ void __launch_bounds__(kCdStopThreads) k_cdata_select(double* part, i
     const int at = m ? __ffs(m) - 1 : (B - 1);
     if (tid == 0) {
         ctl->cd_stop = m ? at + 1 : B;
-        ctl->cd_found = m ? 1 : 0;
+        ctl->cd_found = m ? seq : 0;
         ctl->cd_forced = m ? (__ldcg(tl.flag + at) >> 1) & 1 : 0;
         ctl->rss = __ldcg(tl.rss + at);
         *tl.count = 0u;
@@ -1509,10 +1510,11 @@ __global__ void __launch_bounds__(kCdStopThreads) k_cdata_select(double* part, i
 // observation s0 + q + 1 into the weighted share (FP64 throughout: the PIT is
 // compared with the oracle's to 1e-9).
 __global__ void __launch_bounds__(kCdSelThreads) k_pit_final(const double* part, int G, int B, int s0,
-                                                            const Ctl* ctl, double* pit)
+                                                            const Ctl* ctl, double* pit, int seq)
 {
     const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (q >= ctl->cd_stop || q >= B) return;
+    const int found = ctl->cd_found;
+    if ((found != 0 && found < seq) || q >= ctl->cd_stop || q >= B) return;
     long long km = kNegInfKey;
     for (int g = lane; g < G; g += 32) {
         const long long k = order_key(part[((size_t)g * B + q) * 3]);
@@ -1537,18 +1539,18 @@ __global__ void __launch_bounds__(kCdSelThreads) k_pit_final(const double* part,
     if (lane == 0) pit[s0 + q] = S2 / S1;
 }
 
-cudaError_t launch_pit_final(const double* part, int G, int B, int s0, const Ctl* ctl, double* pit,
+cudaError_t launch_pit_final(const double* part, int G, int B, int s0, const Ctl* ctl, double* pit, int seq,
                              cudaStream_t s)
 {
-    k_pit_final<<<1, kCdSelThreads, 0, s>>>(part, G, B, s0, ctl, pit);
+    k_pit_final<<<1, kCdSelThreads, 0, s>>>(part, G, B, s0, ctl, pit, seq);
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_cdata_select(double* part, int G, int B, int s0, int T, int P, double d1,
-                                const ForceDates& fd, Ctl* ctl, cudaStream_t s)
+                                const ForceDates& fd, Ctl* ctl, int seq, cudaStream_t s)
 {
-    k_cdata_select<<<B, kCdStopThreads, 0, s>>>(part, G, B, s0, T, P, d1, fd, ctl);
+    k_cdata_select<<<B, kCdStopThreads, 0, s>>>(part, G, B, s0, T, P, d1, fd, ctl, seq);
     count_launch();
     return cudaGetLastError();
 }

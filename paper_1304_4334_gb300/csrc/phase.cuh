@@ -19,8 +19,9 @@ struct Ctl {
     double llmax, lo, hi, dphi, rss, phi;
     int pass, done, last;
     // C phase, data tempering: observations to absorb from the current chunk,
-    // whether the chunk contains the stopping observation, and whether the
-    // stop was forced (date of interest or T with RSS >= D1).
+    // the chunk (1-based number within the cycle) that contains the stopping
+    // observation or 0, and whether the stop was forced (date of interest or
+    // T with RSS >= D1).  Chunks numbered after cd_found do nothing.
     int cd_stop, cd_found, cd_forced;
     // RNE stopping rule.
     double mean_rne;
@@ -128,8 +129,8 @@ struct ForceDates {
 // (max log w, sum w, sum w^2), then the stop search's tail (zeroed once).
 size_t cdata_part_len(int G);
 cudaError_t launch_cdata_select(double* part, int G, int B, int s0, int T, int P, double d1,
-                                const ForceDates& fd, Ctl* ctl, cudaStream_t s);
-cudaError_t launch_pit_final(const double* part, int G, int B, int s0, const Ctl* ctl, double* pit,
+                                const ForceDates& fd, Ctl* ctl, int seq, cudaStream_t s);
+cudaError_t launch_pit_final(const double* part, int G, int B, int s0, const Ctl* ctl, double* pit, int seq,
                              cudaStream_t s);
 
 // After the S phase: pooled RSS at the chosen power, log wtilde, phi update.
