@@ -174,10 +174,11 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info);
 
 /* Cycles until the full posterior is reached (at most max_cycles, 0 = no cap).
  * info (nullable) receives the last cycle's report; ncycles (nullable) the
- * number of cycles run by this call.  With power tempering the next cycle's C
- * and S phases are enqueued behind each M phase, so that one host
- * synchronisation per cycle serves both; the kernels, their order and the
- * results are those of repeated smc_cycle calls, bit for bit. */
+ * number of cycles run by this call.  The next cycle's C phase (power
+ * tempering: with its S phase; data tempering: its first batch of 32-
+ * observation chunks) is enqueued behind each M phase, so that one host
+ * synchronisation serves both; the kernels, their order and the results are
+ * those of repeated smc_cycle calls, bit for bit. */
 smc_status smc_run(smc_ctx* ctx, int max_cycles, smc_cycle_info* info, int* ncycles);
 
 /* Restarts the run from new prior draws (same layout rules as smc_init),

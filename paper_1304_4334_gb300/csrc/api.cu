@@ -1219,12 +1219,118 @@ static smc_status m_phase(smc_ctx* ctx, int Tm, double phim, double rss, int for
     return smc_internal_enqueue_adapt(ctx);
 }
 
+// One cycle's data-tempering C phase in progress (Algorithm 1, 2(a)):
+// observations are absorbed in chunks of kCdataChunk until RSS < D1, a date
+// of interest or T.  Chunks are queued in batches without waiting for the
+// stop: each chunk's kernels do nothing once an earlier chunk of the cycle
+// has found it (Ctl::cd_found), so a batch that overshoots costs only empty
+// launches.  A cycle's first batch is as long as the previous cycle's C
+// phase was; later batches take two chunks.
+struct DataC {
+    ForceDates fd;
+    double d1 = 0.0;
+    std::vector<int> start;   // start[seq]: observations absorbed before chunk seq (1-based)
+    int s_next = 0;
+    int batch = 1;
+};
+
+static smc_status data_c_enqueue(smc_ctx* ctx, DataC& dc)
+{
+    const smc_config& c = ctx->cfg;
+    const int P = ctx->P;
+    const int G = (P + kMutThreads - 1) / kMutThreads;
+    for (int b = 0; b < dc.batch && dc.s_next < ctx->T; ++b) {
+        const int seq = (int)dc.start.size();
+        dc.start.push_back(dc.s_next);
+        CdataArgs ca;
+        ca.m = ctx->mdev;
+        ca.obs = ctx->obs;
+        ca.T = ctx->T;
+        ca.W = ctx->W;
+        ca.theta = ctx->theta[ctx->cur];
+        ca.state = ctx->state[ctx->cur];
+        ca.ll = ctx->ll[ctx->cur];
+        ca.logw = ctx->logw;
+        ca.P = P;
+        ca.ns = ctx->ns;
+        ca.s0 = dc.s_next;
+        ca.B = ctx->T - dc.s_next < kCdataChunk ? ctx->T - dc.s_next : kCdataChunk;
+        ca.part = ctx->cd_part;
+        ca.end = ctx->cd_end;
+        ca.stop = &ctx->ctl->cd_stop;
+        ca.found = &ctx->ctl->cd_found;
+        ca.seq = seq;
+        ca.commit = 0;
+        ca.pit = 0;
+        ca.seed = c.seed;
+        CU(launch_cdata(ca, c.precision, ctx->stream));
+        CU(launch_cdata_select(ctx->cd_part, G, ca.B, dc.s_next, ctx->T, P, dc.d1, dc.fd, ctx->ctl, seq,
+                               ctx->stream));
+        ca.commit = 1;
+        ca.pit = ctx->pit != nullptr;
+        CU(launch_cdata(ca, c.precision, ctx->stream));
+        if (ctx->pit) CU(launch_pit_final(ctx->cd_part, G, ca.B, dc.s_next, ctx->ctl, ctx->pit, seq, ctx->stream));
+        dc.s_next += ca.B;
+    }
+    return SMC_OK;
+}
+
+// Enqueues the start of cycle `cycle`'s C phase from t_prev observations
+// (weights reset, the first batch of chunks, the control block's read-back
+// left to the caller).
+static smc_status data_c_begin(smc_ctx* ctx, DataC& dc, int t_prev, int cycle)
+{
+    const smc_config& c = ctx->cfg;
+    std::memset(&dc.fd, 0, sizeof dc.fd);
+    dc.d1 = c.d1;
+    if (ctx->replay) {
+        if (cycle > (int)ctx->design_x.size())
+            return set_err(ctx, SMC_EINVAL, "the replayed design has only %d cycles", (int)ctx->design_x.size());
+        dc.fd.n = 1;
+        dc.fd.t[0] = (int)ctx->design_x[cycle - 1];
+        dc.d1 = -1.0;   // the recorded end, not RSS, closes the cycle
+    } else {
+        dc.fd.n = c.n_force;
+        for (int i = 0; i < c.n_force; ++i) dc.fd.t[i] = c.force_dates[i];
+        if (c.burnin > 0) dc.fd.t[dc.fd.n++] = c.burnin;   // the log score starts a cycle at b
+    }
+    dc.start.assign(1, 0);
+    dc.s_next = t_prev;
+    dc.batch = ctx->cd_chunks > 0 ? ctx->cd_chunks : 1;
+    CU(cudaMemsetAsync(ctx->logw, 0, (size_t)ctx->P * sizeof(double), ctx->stream));
+    CU(cudaMemsetAsync(&ctx->ctl->cd_found, 0, sizeof(int), ctx->stream));
+    return data_c_enqueue(ctx, dc);
+}
+
+// With the control block of the latest batch read back: more batches until
+// a chunk holds the stop, then the cycle's end t_l, its RSS and whether the
+// end was forced.
+static smc_status data_c_finish(smc_ctx* ctx, DataC& dc, int* t_l, double* rss, int* forced)
+{
+    for (;;) {
+        const int f = ctx->ctl_host->cd_found;
+        if (f > 0 && f < (int)dc.start.size()) {
+            *t_l = dc.start[f] + ctx->ctl_host->cd_stop;
+            *rss = ctx->ctl_host->rss;
+            *forced = ctx->ctl_host->cd_forced || *t_l == ctx->T;
+            ctx->cd_chunks = f;
+            return SMC_OK;
+        }
+        if (f != 0 || dc.s_next >= ctx->T)
+            return set_err(ctx, SMC_ECUDA, "data tempering: no stop found by observation %d", dc.s_next);
+        dc.batch = 2;
+        smc_status st = data_c_enqueue(ctx, dc);
+        if (st != SMC_OK) return st;
+        st = sync_ctl(ctx);
+        if (st != SMC_OK) return st;
+    }
+}
+
 smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
 {
     if (!ctx) return SMC_EINVAL;
     if (ctx->done) return set_err(ctx, SMC_EDONE, "the run has reached the full posterior");
     const smc_config& c = ctx->cfg;
-    const int P = ctx->P;
     if (c.tempering != SMC_POWER) ctx->cycle += 1;
     int t_l = ctx->T;
     double rss = 1.0;
@@ -1238,79 +1344,13 @@ smc_status smc_cycle(smc_ctx* ctx, smc_cycle_info* info)
         smc_internal_after_cs(ctx, &rss, &forced);
     } else {
         // ---- C phase: add observations until RSS < D1 (Algorithm 1, 2(a)) ----
-        CU(cudaMemsetAsync(ctx->logw, 0, (size_t)P * sizeof(double), ctx->stream));
-        ForceDates fd;
-        std::memset(&fd, 0, sizeof fd);
-        double d1 = c.d1;
-        if (ctx->replay) {
-            if (ctx->cycle > (int)ctx->design_x.size())
-                return set_err(ctx, SMC_EINVAL, "the replayed design has only %d cycles", (int)ctx->design_x.size());
-            fd.n = 1;
-            fd.t[0] = (int)ctx->design_x[ctx->cycle - 1];
-            d1 = -1.0;   // the recorded end, not RSS, closes the cycle
-        } else {
-            fd.n = c.n_force;
-            for (int i = 0; i < c.n_force; ++i) fd.t[i] = c.force_dates[i];
-            if (c.burnin > 0) fd.t[fd.n++] = c.burnin;   // the log score starts a cycle at b
-        }
-        const int G = (P + kMutThreads - 1) / kMutThreads;
-        // Chunks are queued in batches without waiting for the stop: each
-        // chunk's kernels do nothing once an earlier chunk of the cycle has
-        // found it (Ctl::cd_found), so a batch that overshoots costs only
-        // empty launches.  A cycle's first batch is as long as the previous
-        // cycle was; later batches take two chunks.
-        CU(cudaMemsetAsync(&ctx->ctl->cd_found, 0, sizeof(int), ctx->stream));
-        std::vector<int> start(1, 0);   // start[seq]: observations absorbed before chunk seq
-        int s_next = ctx->t_prev;
-        int batch = ctx->cd_chunks > 0 ? ctx->cd_chunks : 1;
-        int s0 = ctx->t_prev;
-        for (;;) {
-            for (int b = 0; b < batch && s_next < ctx->T; ++b) {
-                const int seq = (int)start.size();
-                start.push_back(s_next);
-                CdataArgs ca;
-                ca.m = ctx->mdev;
-                ca.obs = ctx->obs;
-                ca.T = ctx->T;
-                ca.W = ctx->W;
-                ca.theta = ctx->theta[ctx->cur];
-                ca.state = ctx->state[ctx->cur];
-                ca.ll = ctx->ll[ctx->cur];
-                ca.logw = ctx->logw;
-                ca.P = P;
-                ca.ns = ctx->ns;
-                ca.s0 = s_next;
-                ca.B = ctx->T - s_next < kCdataChunk ? ctx->T - s_next : kCdataChunk;
-                ca.part = ctx->cd_part;
-                ca.end = ctx->cd_end;
-                ca.stop = &ctx->ctl->cd_stop;
-                ca.found = &ctx->ctl->cd_found;
-                ca.seq = seq;
-                ca.commit = 0;
-                ca.pit = 0;
-                ca.seed = c.seed;
-                CU(launch_cdata(ca, c.precision, ctx->stream));
-                CU(launch_cdata_select(ctx->cd_part, G, ca.B, s_next, ctx->T, P, d1, fd, ctx->ctl, seq, ctx->stream));
-                ca.commit = 1;
-                ca.pit = ctx->pit != nullptr;
-                CU(launch_cdata(ca, c.precision, ctx->stream));
-                if (ctx->pit) CU(launch_pit_final(ctx->cd_part, G, ca.B, s_next, ctx->ctl, ctx->pit, seq, ctx->stream));
-                s_next += ca.B;
-            }
-            st = sync_ctl(ctx);
-            if (st != SMC_OK) return st;
-            const int f = ctx->ctl_host->cd_found;
-            if (f > 0 && f < (int)start.size()) {
-                s0 = start[f] + ctx->ctl_host->cd_stop;
-                ctx->cd_chunks = f;
-                break;
-            }
-            if (f != 0 || s_next >= ctx->T) return set_err(ctx, SMC_ECUDA, "data tempering: no stop found by observation %d", s_next);
-            batch = 2;
-        }
-        t_l = s0;
-        rss = ctx->ctl_host->rss;
-        forced = ctx->ctl_host->cd_forced || t_l == ctx->T;
+        DataC dc;
+        st = data_c_begin(ctx, dc, ctx->t_prev, ctx->cycle);
+        if (st != SMC_OK) return st;
+        st = sync_ctl(ctx);
+        if (st != SMC_OK) return st;
+        st = data_c_finish(ctx, dc, &t_l, &rss, &forced);
+        if (st != SMC_OK) return st;
         // ---- S phase (weights from the accumulated log weights) ----
         st = s_phase(ctx, 1);
         if (st != SMC_OK) return st;
@@ -1381,10 +1421,69 @@ static smc_status run_power_pipelined(smc_ctx* ctx, int max_cycles, smc_cycle_in
     return st;
 }
 
+// Data tempering, likewise: the next cycle's C phase starts (its first batch
+// of chunks) right behind this cycle's M phase, and one synchronisation
+// returns the M phase's control block (ctl_host[1]) and the batch's
+// (ctl_host[0]).  The kernels and their order are those of smc_cycle.
+static smc_status run_data_pipelined(smc_ctx* ctx, int max_cycles, smc_cycle_info* info, int* ncycles)
+{
+    const smc_config& c = ctx->cfg;
+    int n = 0;
+    smc_cycle_info ci;
+    std::memset(&ci, 0, sizeof ci);
+    Ctl* hm = ctx->ctl_host + 1;
+    bool have_c = false;   // this cycle's first batch is enqueued and read back
+    DataC dc;
+    smc_status st = SMC_OK;
+    while (!ctx->done && (max_cycles <= 0 || n < max_cycles)) {
+        if (!have_c) {
+            ctx->cycle += 1;
+            st = data_c_begin(ctx, dc, ctx->t_prev, ctx->cycle);
+            if (st != SMC_OK) break;
+            st = sync_ctl(ctx);
+            if (st != SMC_OK) break;
+        }
+        int t_l = ctx->T, forced = 0;
+        double rss = 1.0;
+        st = data_c_finish(ctx, dc, &t_l, &rss, &forced);
+        if (st != SMC_OK) break;
+        st = s_phase(ctx, 1);
+        if (st != SMC_OK) break;
+        CU(launch_cycle_close(ctx->gstat, ctx->lw, c.J, c.N, 0, ctx->ctl, ctx->stream));
+        ctx->phi = 1.0;
+        const int cycle = ctx->cycle;
+        int r = 0;
+        st = m_phase(ctx, t_l, 1.0, rss, forced, &r);
+        if (st != SMC_OK) break;
+        CU(cudaMemcpyAsync(hm, ctx->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+        ctx->d2h += sizeof(Ctl);
+        have_c = t_l < ctx->T && (max_cycles <= 0 || n + 1 < max_cycles) &&
+                 (!ctx->replay || cycle < (int)ctx->design_x.size());
+        if (have_c) {
+            ctx->cycle += 1;
+            st = data_c_begin(ctx, dc, t_l, ctx->cycle);
+            if (st != SMC_OK) break;
+            st = smc_internal_enqueue_ctl_readback(ctx);
+            if (st != SMC_OK) break;
+        }
+        CU(cudaStreamSynchronize(ctx->stream));
+        // the error word is sticky: the later read-back carries every error
+        st = check_device_error(ctx, have_c ? *ctx->ctl_host : *hm);
+        if (st != SMC_OK) break;
+        st = after_m_from(ctx, *hm, cycle, t_l, r, t_l, 1.0, rss, &ci);
+        if (st != SMC_OK) break;
+        ++n;
+    }
+    if (info) *info = ci;
+    if (ncycles) *ncycles = n;
+    return st;
+}
+
 smc_status smc_run(smc_ctx* ctx, int max_cycles, smc_cycle_info* info, int* ncycles)
 {
     if (!ctx) return SMC_EINVAL;
     if (ctx->cfg.tempering == SMC_POWER && !ctx->done) return run_power_pipelined(ctx, max_cycles, info, ncycles);
+    if (ctx->cfg.tempering == SMC_DATA && !ctx->done) return run_data_pipelined(ctx, max_cycles, info, ncycles);
     int n = 0;
     smc_cycle_info ci;
     std::memset(&ci, 0, sizeof ci);

@@ -293,13 +293,15 @@ def test_launch_shapes_give_identical_runs(S):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision,record", [("fp32", False), ("fp64", True)])
-def test_pipelined_run_equals_cycle_by_cycle(S, precision, record):
-    """smc_run with power tempering enqueues the next cycle's C and S phases
-    behind each M phase (one host round trip per cycle); the same context
-    stepped with smc_cycle synchronises twice per cycle.  Both must produce
-    the same cycles, designs and particles bitwise, also when the run is
-    split by max_cycles."""
+@pytest.mark.parametrize("precision,record,tempering", [("fp32", False, "power"), ("fp64", True, "power"),
+                                                        ("fp32", False, "data"), ("fp64", True, "data")])
+def test_pipelined_run_equals_cycle_by_cycle(S, precision, record, tempering):
+    """smc_run enqueues the next cycle's C phase (power tempering: with its S
+    phase; data tempering: its first batch of chunks) behind each M phase, so
+    one host round trip serves both; the same context stepped with smc_cycle
+    synchronises after each phase.  Both must produce the same cycles,
+    designs and particles bitwise, also when the run is split by
+    max_cycles."""
     truth = I.WORKLOADS["egarch22_T5000"].truth
     y = I.simulate_egarch(truth, 600, seed=11)
     m = S.model_egarch(2, 2, True)
@@ -308,18 +310,19 @@ def test_pipelined_run_equals_cycle_by_cycle(S, precision, record):
     th0 = I.draw_prior(mean, sd, lo, J * N, seed=12)
     prec = S.FP32 if precision == "fp32" else S.FP64
     out = []
+    tmp = S.POWER if tempering == "power" else S.DATA
     for mode in ("run", "split", "cycle"):
-        ctx = S.init(m, S.config_default(J=J, N=N, precision=prec, seed=7), y, th0)
+        ctx = S.init(m, S.config_default(J=J, N=N, precision=prec, seed=7, tempering=tmp), y, th0)
         if record:
             ctx.record_design()
         infos = []
         if mode == "run":
             n, last = ctx.run()
-            infos = [n, last["cycle"], last["phi"], last["R"], last["h_tenths"], last["acc_rate"]]
+            infos = [n, last["cycle"], last["phi"], last["t"], last["R"], last["h_tenths"], last["acc_rate"]]
         elif mode == "split":
             n1, _ = ctx.run(3)
             n2, last = ctx.run()
-            infos = [n1 + n2, last["cycle"], last["phi"], last["R"], last["h_tenths"], last["acc_rate"]]
+            infos = [n1 + n2, last["cycle"], last["phi"], last["t"], last["R"], last["h_tenths"], last["acc_rate"]]
         else:
             n, last = 0, None
             while True:
@@ -329,7 +332,7 @@ def test_pipelined_run_equals_cycle_by_cycle(S, precision, record):
                 n, last = n + 1, info
                 if info["done"]:
                     break
-            infos = [n, last["cycle"], last["phi"], last["R"], last["h_tenths"], last["acc_rate"]]
+            infos = [n, last["cycle"], last["phi"], last["t"], last["R"], last["h_tenths"], last["acc_rate"]]
         design = ctx.design() if record else None
         out.append((infos, ctx.log_ml(), ctx.particles(), design))
         ctx.close()
