@@ -255,7 +255,8 @@ template <int K, int I, int kSeg>
 __device__ double adj_forward_fast(const float* th, int has_gamma, int eps0_zero, const float* __restrict__ y,
                                    int T, float* ckpt, size_t P, int p)
 {
-    static_assert(kSeg == 32, "one 32-observation partial per segment");
+    static_assert(32 % kSeg == 0, "FP32 partials of 32 observations cover whole segments");
+    constexpr int kPerPartial = 32 / kSeg;
     EgarchF32<K, I> f;
     f.setup(th, has_gamma, eps0_zero);
     const int nseg = (T + kSeg - 1) / kSeg;
@@ -278,8 +279,10 @@ __device__ double adj_forward_fast(const float* th, int has_gamma, int eps0_zero
                 else f.template step<false>(y[t0 + r]);
             }
         }
-        f.flush();
-        if ((sg & 7) == 7) f.flush_fp64();
+        if (sg % kPerPartial == kPerPartial - 1 || sg == nseg - 1) {
+            f.flush();
+            if (sg % (8 * kPerPartial) == 8 * kPerPartial - 1) f.flush_fp64();
+        }
     }
     return f.finish(T);
 }

@@ -9,7 +9,7 @@ namespace smc {
 
 constexpr int kMalaThreads = 128;
 // Launch width of the gradient kernels: each thread holds a shared-memory slab
-// for one segment's recomputed states (32 x (K + 2) values), so narrower blocks
+// for one segment's recomputed states (mala_seg x (K + 2) values), so narrower blocks
 // pack more resident blocks per SM and leave a smaller last wave.
 constexpr int kMalaLaunch = 64;
 
@@ -48,10 +48,18 @@ struct MalaArgs {
     int* err;
 };
 
+// Observations per checkpoint segment of the EGARCH adjoint (the reverse
+// sweep's shared-memory slab holds one segment per thread); the checkpoint
+// buffers are sized from the same value.  (16 in FP32 as well, for more
+// resident blocks, was measured and not kept: 5.81 against 5.90 ms per launch
+// at K=2, I=2, T=5000, 262,144 particles, for twice the checkpoint memory.)
+template <typename Real>
+constexpr int mala_seg() { return sizeof(Real) == 4 ? 32 : 16; }
+
 template <typename Real, int K, int I>
 struct GradEgarch {
     using RealT = Real;
-    static constexpr int kSeg = sizeof(Real) == 4 ? 32 : 16;
+    static constexpr int kSeg = mala_seg<Real>();
     static constexpr int kNs = K + 1;
     static size_t smem_bytes(int threads) { return (size_t)kSeg * (K + 2) * threads * sizeof(Real); }
     static size_t ckpt_bytes(int T, int P)
@@ -310,8 +318,8 @@ cudaError_t launch_mala(const MalaArgs& a, int precision, cudaStream_t s);
 inline size_t mala_ckpt_bytes(const ModelDev& m, int precision, int T, int P)
 {
     if (m.kind == 1) return GradLinreg::ckpt_bytes(T, P);
-    const int seg = precision == 1 ? 32 : 16;
     const size_t real = precision == 1 ? 4 : 8;
+    const int seg = precision == 1 ? mala_seg<float>() : mala_seg<double>();
     const int nseg = (T + seg - 1) / seg;
     return (size_t)(nseg > 1 ? nseg - 1 : 1) * (m.K + 1) * (size_t)P * real;
 }
