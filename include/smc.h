@@ -320,13 +320,16 @@ smc_status smc_wait_selftest(uint64_t limit_ns, int complete, void* stream);
  * ex2 and lg2 (ex2/lg2.approx.ftz.f32, each with one FP32 operand fix-up on
  * another pipe) and dfma (fma.rn.f64); issue = warp instructions per SM and
  * clock with an FFMA and a logic operation on its result in turn; sm_mhz = the SM clock during
- * the tests (cycle counter over the global nanosecond timer); sms = SM count.
+ * the tests (cycle counter over the global nanosecond timer); sms = SM count;
+ * ffma_mix = FP32 lane operations per SM and clock with an FFMA2 and an FFMA
+ * on independent chains in turn.
  * Takes about 10 ms; allocates and frees a few bytes of device memory;
  * synchronises `stream`.  SMC_ECUDA without a usable GPU. */
 typedef struct {
     int sms;
     double ffma, ffma2, ex2, lg2, dfma, issue;
     double sm_mhz;
+    double ffma_mix;
 } smc_peak_rates;
 smc_status smc_peaks(smc_peak_rates* out, void* stream);
 

@@ -19,6 +19,9 @@
 //   ISSUE  an FFMA and a logic operation on its result in turn (two
 //          instructions on different pipes): warp instructions issued per SM
 //          and clock
+//   MIX    an FFMA2 and an FFMA on independent chains in turn: FP32 lane
+//          operations per SM and clock when paired and single instructions
+//          share the FP32 pipes
 // The loop body holds kReps x kChains operations, so that the loop's own
 // counter and branch take about 1% of the issue slots.
 #include "../../include/smc.h"
@@ -33,7 +36,7 @@ constexpr int kPeakSmem = 150 * 1024;   // > half of an SM's shared memory
 constexpr int kChains = 8;
 constexpr int kReps = 32;
 
-enum { kOpFfma = 0, kOpFfma2, kOpEx2, kOpLg2, kOpDfma, kOpIssue, kNumOps };
+enum { kOpFfma = 0, kOpFfma2, kOpEx2, kOpLg2, kOpDfma, kOpIssue, kOpMix, kNumOps };
 
 struct PeakClock {
     unsigned long long cycles, ns;
@@ -72,6 +75,10 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak(int iters, float a, float
                 if constexpr (OP == kOpIssue) {
                     x[c] = fmaf(x[c], a, b);
                     u[c] ^= __float_as_uint(x[c]);
+                }
+                if constexpr (OP == kOpMix) {
+                    x2[c] = __ffma2_rn(x2[c], a2, b2);
+                    x[c] = fmaf(x[c], a, b);
                 }
             }
         }
@@ -128,9 +135,9 @@ extern "C" smc_status smc_peaks(smc_peak_rates* out, void* stream)
     // lane operations per thread per loop iteration, and iteration counts that
     // keep each launch near a millisecond at the nominal rates
     const int per_iter = kReps * kChains;
-    const int iters[kNumOps] = {1024, 512, 128, 64, 16, 512};
-    const double lanes_per_instr[kNumOps] = {1, 2, 1, 1, 1, 1};
-    const double instr_per_op[kNumOps] = {1, 1, 1, 1, 1, 2};
+    const int iters[kNumOps] = {1024, 512, 128, 64, 16, 512, 384};
+    const double lanes_per_instr[kNumOps] = {1, 2, 1, 1, 1, 1, 3};   // MIX: per FFMA2 + FFMA pair
+    const double instr_per_op[kNumOps] = {1, 1, 1, 1, 1, 2, 2};
     double rate[kNumOps], mhz[kNumOps];
     smc_status st = SMC_OK;
     for (int op = 0; op < kNumOps && st == SMC_OK; ++op) {
@@ -142,7 +149,8 @@ extern "C" smc_status smc_peaks(smc_peak_rates* out, void* stream)
             case kOpEx2: e = run_peak<kOpEx2>(blocks, iters[op], sink, clk, s); break;
             case kOpLg2: e = run_peak<kOpLg2>(blocks, iters[op], sink, clk, s); break;
             case kOpDfma: e = run_peak<kOpDfma>(blocks, iters[op], sink, clk, s); break;
-            default: e = run_peak<kOpIssue>(blocks, iters[op], sink, clk, s); break;
+            case kOpIssue: e = run_peak<kOpIssue>(blocks, iters[op], sink, clk, s); break;
+            default: e = run_peak<kOpMix>(blocks, iters[op], sink, clk, s); break;
             }
             if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), clk, (size_t)blocks * sizeof(PeakClock),
                                                       cudaMemcpyDeviceToHost, s);
@@ -174,6 +182,7 @@ extern "C" smc_status smc_peaks(smc_peak_rates* out, void* stream)
     out->lg2 = rate[kOpLg2];
     out->dfma = rate[kOpDfma];
     out->issue = rate[kOpIssue];
+    out->ffma_mix = rate[kOpMix];
     double m = 0.0;
     for (int op = 0; op < kNumOps; ++op) m += mhz[op];
     out->sm_mhz = m / kNumOps;

@@ -61,7 +61,8 @@ class smc_config(C.Structure):
 
 class smc_peak_rates(C.Structure):
     _fields_ = [("sms", C.c_int), ("ffma", C.c_double), ("ffma2", C.c_double), ("ex2", C.c_double),
-                ("lg2", C.c_double), ("dfma", C.c_double), ("issue", C.c_double), ("sm_mhz", C.c_double)]
+                ("lg2", C.c_double), ("dfma", C.c_double), ("issue", C.c_double), ("sm_mhz", C.c_double),
+                ("ffma_mix", C.c_double)]
 
 
 class smc_cycle_info(C.Structure):
