@@ -47,6 +47,36 @@ def _loglik_case(S, K, I_, gamma, T, P, precision, seed, frac_prior=0.0):
     return ll_o, st_o, lp_o, host(ll), host(st).T, host(lp)
 
 
+@pytest.mark.parametrize("K,I_", [(3, 4), (2, 3), (1, 4)])
+def test_loglik_fp32_tail_observations_match_oracle(S, K, I_):
+    """Outlying observations push every mixture component of many particles
+    far into its tail: every 13th shock scaled by 10 to 60 and a run of 40
+    shocks scaled by 5 (mixture sums far below their peak, observation after
+    observation).  For posterior-like particles the FP32 recursion's log
+    likelihood still matches the FP64 oracle; a mishandled tail would move it
+    by tens of nats.  (Prior draws are left out here: with such shocks some of
+    them reach volatilities of 2^1000 and beyond, where FP32 and FP64
+    underflow at different points.)"""
+    torch = torch_cuda()
+    truth = egarch_truth(K, I_)
+    T, P = 777, 400
+    y = I.simulate_egarch(truth, T, seed=41)
+    y[::13] *= np.linspace(10.0, 60.0, len(y[::13]))
+    y[300:340] *= 5.0
+    spec = O.ModelSpec(K=K, I=I_, gamma=True)
+    prior = O.table1_prior(K, I_, True)
+    th = particles(spec.d, truth, K, I_, True, P, 43, prior=prior, frac_prior=0.0)
+    ll_o = O.loglik(spec, y, th, nthreads=4)
+    m = S.model_egarch(K, I_, True)
+    ll = torch.empty(P, dtype=torch.float64, device="cuda")
+    S.loglik(m, S.FP32, dev(y, torch.float32), soa(th), ll, None, None)
+    ll = host(ll)
+    fin = np.isfinite(ll_o) & (ll_o > -1e7)
+    assert fin.sum() >= P - 2 and np.all(np.isfinite(ll[fin]))
+    err = np.abs(ll[fin] - ll_o[fin]) / np.abs(ll_o[fin])
+    assert np.quantile(err, 0.99) <= 1e-5 and err.max() <= 1e-4, (np.quantile(err, 0.99), err.max())
+
+
 @pytest.mark.parametrize("K,I_,gamma", SHAPES)
 @pytest.mark.parametrize("T,P", [(1, 5), (37, 129), (1037, 300)])
 def test_loglik_fp64_matches_oracle(S, K, I_, gamma, T, P):

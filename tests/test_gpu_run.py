@@ -263,13 +263,19 @@ def test_rne_stopping_rule_run(S):
     ctx.close()
 
 
-def test_launch_shapes_give_identical_runs(S):
+@pytest.mark.parametrize("workload", ["egarch22_T5000", "egarch34_T20000"])
+def test_launch_shapes_give_identical_runs(S, workload):
     """Every launch shape (blocks of any multiple of 32 threads up to 224, one
     or two particles per thread) computes each particle's proposal, recursion
-    and decision exactly as one particle per thread in 128-thread blocks."""
-    truth = I.WORKLOADS["egarch22_T5000"].truth
+    and decision exactly as one particle per thread in 128-thread blocks.  The
+    K=3, I=4 case adds outlying observations, so that the mixture sums' tail
+    fallback and rescaling run in both kernels."""
+    w = I.WORKLOADS[workload]
+    truth = w.truth
     y = I.simulate_egarch(truth, 700, seed=8)
-    m = S.model_egarch(2, 2, True)
+    if w.I >= 3:
+        y[::37] *= 12.0
+    m = S.model_egarch(w.K, w.I, True)
     mean, sd, lo = S.model_prior(m)
     J, N = 16, 300   # P = 4800: ragged against 64/128/256-particle tiles
     th0 = I.draw_prior(mean, sd, lo, J * N, seed=9)
