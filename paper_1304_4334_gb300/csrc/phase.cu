@@ -920,11 +920,12 @@ cudaError_t launch_power_search(const double* ll, int P, double d1, int passes, 
 }
 
 // ================================================================= S phase
-// One block per group.  Weights (FP64): w_n = exp(log w_n - max_n log w_n);
-// log wbar_j(l-1) = max + log(sum_n w_n / N) (Section 4.2).  Resampling in
-// integer fixed point (the reading stated in smc.h): everything after the
-// quantisation is integer arithmetic, so the selected indices do not depend
-// on summation order or thread count.
+// One block per group.  Weights w_n = exp(log w_n - max_n log w_n), the
+// difference formed in FP64 and the exponential in 64-bit fixed point
+// (exp_fixed below); log wbar_j(l-1) = max + log(sum_n w_n / N) (Section
+// 4.2).  Resampling in integer fixed point (the reading stated in smc.h):
+// everything after the quantisation is integer arithmetic, so the selected
+// indices do not depend on summation order or thread count.
 constexpr int kSelThreads = 1024;
 
 // Shared arrays indexed through sp(n) = n + n/8: a thread's eight
