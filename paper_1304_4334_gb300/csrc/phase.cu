@@ -677,6 +677,11 @@ __device__ __forceinline__ float u64_to_f32(uint64_t v)
 // d as hi + lo in FP32 from its bits: hi carries the leading 24 significand
 // bits (truncated), lo the next 29 (rounded to 24).  ok is false outside
 // 2^-126 <= |d| < 2^128 (and for inf or NaN), where the caller converts in FP64.
+// The rare FP64 paths of the conversions below, kept out of line so that the
+// compiler does not evaluate them speculatively beside the integer path.
+__device__ __noinline__ float diff_f64_to_f32(double a, double b) { return __double2float_rn(a - b); }
+__device__ __noinline__ float cvt_f64_to_f32(double d) { return __double2float_rn(d); }
+
 __device__ __forceinline__ float2 split_f64(double d, bool& ok)
 {
     const uint64_t b = (uint64_t)__double_as_longlong(d);
@@ -775,7 +780,7 @@ __global__ void __launch_bounds__(kSearchThreads, 1) k_power_search(const double
             const double l = key_value(k);
             bool ok;
             const float2 lx = split_f64(l, ok);
-            x = (ok && mok) ? (lx.x - mx.x) + (lx.y - mx.y) : (float)(l - llmax);
+            x = (ok && mok) ? (lx.x - mx.x) + (lx.y - mx.y) : diff_f64_to_f32(l, llmax);
         }
         xdst[i] = x;
     }
@@ -1013,6 +1018,10 @@ __device__ __forceinline__ bool exp_fixed(double x, const uint64_t* tab, uint64_
     return true;
 }
 
+// floor(2^32 exp(x)) from the FP64 exponential: out of line, so that the
+// compiler does not evaluate it speculatively for every particle.
+__device__ __noinline__ uint64_t quantise_fp64_exp(double x) { return (uint64_t)(exp(x) * 4294967296.0); }
+
 // q = floor(2^32 exp(x)) from the fixed-point value, with the group sums'
 // terms exp(x) 2^62 and exp(2x) 2^62 (truncated).  When 2^32 exp(x) lies
 // within 2^-18 of an integer (the fixed point's error, the FP64 rounding of
@@ -1034,7 +1043,7 @@ __device__ __forceinline__ uint64_t quantise_exp(double x, const uint64_t* tab, 
     const uint64_t mg = 1ull << (s - 18);
     const bool near = (q != 0 && rem < mg) || rem >= (1ull << s) - mg;
     if (M == (1ull << 63) || !near) return q;                        // exp(x) = 1 exactly, or clear of a boundary
-    return (uint64_t)(exp(x) * 4294967296.0);
+    return quantise_fp64_exp(x);
 }
 
 // Exact block sums of two 128-bit unsigned values (every thread receives
@@ -1390,7 +1399,7 @@ __device__ __forceinline__ float f64_to_f32(double d)
 {
     const uint64_t b = (uint64_t)__double_as_longlong(d);
     const uint32_t e = (uint32_t)(b >> 52) & 0x7ffu;
-    if (e - 897u >= 254u) return __double2float_rn(d);        // FP32 exponent outside 1..254
+    if (e - 897u >= 254u) return cvt_f64_to_f32(d);          // FP32 exponent outside 1..254
     const uint64_t mant = b & 0xfffffffffffffull;
     uint32_t f = ((uint32_t)(b >> 32) & 0x80000000u) | ((e - 896u) << 23) | (uint32_t)(mant >> 29);
     const uint32_t rest = (uint32_t)mant & 0x1fffffffu;          // the 29 bits rounded away
@@ -1459,7 +1468,7 @@ __global__ void __launch_bounds__(kCdStopThreads) k_cdata_select(double* part, i
             if (order_key(o[0]) == kNegInfKey) continue;
             bool ok;
             const float2 ox = split_f64(o[0], ok);
-            const float x = (ok && mok) ? (ox.x - mx.x) + (ox.y - mx.y) : (float)(o[0] - M);
+            const float x = (ok && mok) ? (ox.x - mx.x) + (ox.y - mx.y) : diff_f64_to_f32(o[0], M);
             const float e = ex2_approx(x * (float)kLog2e);
             s1 = df_add_f(s1, f64_to_f32(o[1]) * e);
             s2 = df_add_f(s2, f64_to_f32(o[2]) * (e * e));
