@@ -47,7 +47,7 @@ SM_COUNT_GB300 = 152
 # with --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass;
 # profiles/k_mutate_x2_egarch34_T20000.md).  Shapes without a capture of the
 # current kernel report null.
-MUTATE_TRAFFIC = {("egarch34_T20000", 2, 128): 1.153083008e9}
+MUTATE_TRAFFIC = {("egarch34_T20000", 2, 128): 1.153083008e9, ("egarch22_T5000", 1, 224): 8.935808e6}
 SM_MAX_MHZ_FALLBACK = 2070.0
 # Acceptance target of the MALA runs: 0.574, the asymptotically optimal rate of
 # Langevin proposals (Roberts and Rosenthal, 1998); the random walk keeps the
